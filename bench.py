@@ -1,0 +1,341 @@
+"""Throughput of the GA population step on GB300 (one JSON line on stdout).
+
+Workload: m = 20, P = 40,000 balanced +-1 matrices (N = 10,000; the paper's
+stated scale), fitness = sum over i < j of G_ij^2, one balanced pair-flip per
+child (NC = NR = 1), Philox seed 1, bit storage.  A step is one chunk of
+STEP_GENS generations of the whole hot path (selection, survivor placement,
+crossover, mutation, offspring fitness, best individual), run by the fused
+persistent generation kernel through the C ABI (ga_step).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+value     generations/s of the fused path, inputs resident in HBM, CUDA events
+          on the context's stream; the L2 cache is flushed (256 MiB write)
+          before every step, outside the timed events.
+e2e       the same metric with the population and fitness copied in from
+          pinned host memory and the step's best-fitness trajectory copied
+          back, every step, inside the timed region (wall clock).
+plain     the one-kernel-per-operator path on the same workload.
+roofline  the persistent kernel against the measured HBM copy bandwidth.
+cpu_baseline  the CPU oracle on a bounded sample of the same workload.
+--impl reference times the oracle alone (the reference arm of this build).
+Under torchrun each rank runs an independent replica population
+(pop_id = rank); value sums the generations of all ranks over the slowest
+rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+M, N, SEED, NC, NR = 20, 10_000, 1, 1, 1
+P = 4 * N
+STEP_GENS = 50
+WORKLOAD = "m=20, P=40,000, F_sq, NC=NR=1, seed 1, bit storage, 50 generations per step"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def bytes_per_generation(m=M, N=N):
+    """Algorithmic HBM bytes of one generation of the fused kernel (bit
+    storage): read the 2N surviving parents, write all 4N slots (2N parents
+    placed + 2N offspring), read and write the 4N fitness words, read the
+    survivor-order row (2N words)."""
+    w = (m + 31) // 32
+    mat = m * w * 4
+    return 2 * N * mat + 4 * N * mat + 2 * 4 * N * 4 + 2 * N * 4
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.proc, self.lines = index, None, []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(seconds=12.0, min_gens=3):
+    """Times the CPU oracle on the same workload for a bounded number of
+    generations (about `seconds` of host CPU time)."""
+    import oracle
+    pop = oracle.init_population(M, P, SEED)
+    F = oracle.fitness(pop, oracle.FIT_SQ)
+    t0 = time.perf_counter()
+    gens = 0
+    while gens < min_gens or time.perf_counter() - t0 < seconds:
+        oracle.run(pop, F, N, NC, NR, oracle.FIT_SQ, SEED, 0, gens, 1)
+        gens += 1
+        if gens >= 2000:
+            break
+    dt = time.perf_counter() - t0
+    return gens / dt, gens, dt, oracle.num_threads()
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle as it stands, on the host cores."""
+    if rank != 0:
+        return
+    import oracle
+    pop = oracle.init_population(M, P, SEED)
+    F = oracle.fitness(pop, oracle.FIT_SQ)
+    sample = 4  # generations per step: a bounded sample of a 50-generation step
+    g = 0
+    for _ in range(args.warmup):
+        oracle.run(pop, F, N, NC, NR, oracle.FIT_SQ, SEED, 0, g, sample)
+        g += sample
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.run(pop, F, N, NC, NR, oracle.FIT_SQ, SEED, 0, g, sample)
+        g += sample
+    dt = time.perf_counter() - t0
+    gps = args.steps * sample / dt
+    line = {
+        "impl": "reference",
+        "metric": "GA generations/s at m=20, P=40k (CPU oracle)",
+        "value": gps, "unit": "generations/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD.replace("50 generations", f"{sample} generations")},
+        "cpu_baseline": {"value": gps, "unit": "generations/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"{sample} generations per step, {args.steps} steps"},
+        "e2e": {"value": gps, "unit": "generations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--plain-steps", type=int, default=4)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2208_14961_gb300.build import build
+    build()
+    from paper_2208_14961_gb300 import hadga as h
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl" if dist.is_nccl_available() else "gloo")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    stream = torch.cuda.Stream(device=dev)
+    pop = h.Population(M, N, seed=SEED, pop_id=rank, NC=NC, NR=NR, fitness=h.FIT_SQ, storage=h.STORE_BITS,
+                       traj_cap=STEP_GENS, device=dev, stream=stream)
+    pop.init_population()
+    pop.fitness()
+    pop.sync()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+
+    def flush_l2():
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+
+    # ---- fused path, device-timed -------------------------------------------
+    for _ in range(args.warmup):
+        pop.step(STEP_GENS)
+    pop.sync()
+    pop.profile(True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clock = ClockSampler(local)
+    barrier()
+    launches0 = h.kernel_launches()
+    clock.start()
+    for i in range(args.steps):
+        flush_l2()
+        starts[i].record(stream)
+        pop.step(STEP_GENS)
+        ends[i].record(stream)
+    barrier()
+    clocks = clock.stop()
+    launches = h.kernel_launches() - launches0
+    pop.sync()
+    dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    perm_ms, fused_ms, fused_launches = pop.profile_read()
+    pop.profile(False)
+    gens = args.steps * STEP_GENS
+    t = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    value = world * gens / (max_ms / 1e3)
+
+    # ---- plain path (one kernel per operator), device-timed ------------------
+    pl = h.Population(M, N, seed=SEED, pop_id=rank, NC=NC, NR=NR, fitness=h.FIT_SQ, storage=h.STORE_BITS,
+                      traj_cap=STEP_GENS, device=dev, stream=stream)
+    pl.init_population()
+    pl.fitness()
+    pl.step_plain(STEP_GENS)
+    pl.sync()
+    plain_ms = 0.0
+    for _ in range(args.plain_steps):
+        flush_l2()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pl.step_plain(STEP_GENS)
+        b.record(stream)
+        b.synchronize()
+        plain_ms += a.elapsed_time(b)
+    plain_gps = args.plain_steps * STEP_GENS / (plain_ms / 1e3)
+    pl.close()
+
+    # ---- end to end through the C ABI with host buffers ------------------------
+    ee = h.Population(M, N, seed=SEED, pop_id=rank, NC=NC, NR=NR, fitness=h.FIT_SQ, storage=h.STORE_BITS,
+                      traj_cap=STEP_GENS, device=dev, stream=stream)
+    ee.init_population()
+    ee.fitness()
+    ee.sync()
+    host_pop = ee.pop.cpu().pin_memory()
+    host_fit = ee.fit.cpu().pin_memory()
+    h2d = host_pop.numel() * host_pop.element_size() + host_fit.numel() * host_fit.element_size()
+    d2h = STEP_GENS * 8          # the step's best-fitness trajectory (one 64-bit key per generation)
+    for _ in range(2):
+        with torch.cuda.stream(stream):
+            ee.pop.copy_(host_pop, non_blocking=True)
+            ee.fit.copy_(host_fit, non_blocking=True)
+        ee.step(STEP_GENS)
+        ee.trajectory()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            ee.pop.copy_(host_pop, non_blocking=True)
+            ee.fit.copy_(host_fit, non_blocking=True)
+        ee.step(STEP_GENS)
+        ee.trajectory()          # device -> host read of the step's result
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * args.steps * STEP_GENS / float(te.item())
+    ee.close()
+
+    # ---- roofline of the persistent kernel --------------------------------------
+    peak, peak_kind = _peaks()
+    roof = None
+    if fused_launches > 0 and fused_ms > 0:
+        per_launch_ms = fused_ms / fused_launches
+        per_launch_bytes = bytes_per_generation() * STEP_GENS
+        achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_fused_generation", "peak_source": peak_kind,
+                "launch_ms": per_launch_ms, "perm_table_ms_per_launch": perm_ms / max(fused_launches, 1)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        gps, ngen, dt, cores = oracle_sample()
+        cpu = {"value": gps, "unit": "generations/s", "cores": cores, "kind": "oracle",
+               "sample": f"{ngen} generations of the same workload in {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": "GA generations/s at m=20, P=40k (fused persistent generation kernel)",
+            "value": value, "unit": "generations/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "global_batch": P * world, "parallelism": f"replicas{world}",
+                       "l2": "flushed before every step (256 MiB write), outside the timed events",
+                       "fused": bool(pop.is_fused())},
+            "evals_per_s": value * (P // 2),
+            "evals_per_s_paper_convention": value * P,
+            "plain": {"value": plain_gps, "unit": "generations/s", "steps": args.plain_steps,
+                      "fused_over_plain": value / world / plain_gps},
+            "e2e": {"value": e2e_value, "unit": "generations/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "gpu_launches": int(launches),
+        }
+        print(json.dumps(line), flush=True)
+    pop.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

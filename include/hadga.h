@@ -1,0 +1,240 @@
+/*
+ * hadga.h -- C ABI of libhadga, the GB300 (sm_103a) implementation of the
+ * per-generation population step of the genetic algorithm for Hadamard
+ * matrices of Balogh & Ruiz (arXiv 2208.14961).
+ *
+ * The library computes everything on the GPU.  Callers own the population
+ * and fitness buffers (device memory, e.g. torch tensors) and the CUDA
+ * stream; a context borrows them and owns only its workspace.
+ *
+ * Conventions shared by every entry point
+ *  - Status: every call returns a ga_status and never aborts the process.
+ *    The text of the last failure of a context is ga_last_error(ctx); calls
+ *    without a context report through ga_last_error(NULL) (per thread).
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *    default stream).  Every call is stream-ordered and returns without
+ *    waiting for the GPU, except where marked "synchronises".
+ *  - Device errors (a grid-barrier wait that ran out, an internal check)
+ *    raise bits in a device error word; synchronising calls turn them into
+ *    GA_ETIMEOUT or GA_ECUDA.
+ *
+ * Population (Sec. 3.1, Eq. (1)-(2)): P = 4N matrices of order m = 4k,
+ * slots [0, 2N) parents P_1..P_2N, slots [2N, 4N) offspring O_1..O_2N.
+ * Storage formats of one matrix Q (rows i, columns j, entries +1 / -1):
+ *  - GA_STORE_INT8 : m*m int8, row-major, Q[i][j] at byte i*m + j (the
+ *                    paper's layout, Sec. 3.4); values 1 and -1.
+ *  - GA_STORE_BITS : m*W uint32 words, W = ceil(m/32); column j occupies
+ *                    words [j*W, j*W + W); bit r of word w is 1 iff
+ *                    Q[32w + r][j] == -1; bits of rows >= m are 0.
+ *  - GA_STORE_E4M3 : m*m bytes row-major, FP8 e4m3: +1 = 0x38, -1 = 0xB8.
+ *  - GA_STORE_BF16 : m*m uint16 row-major, bfloat16: +1 = 0x3F80, -1 = 0xBF80.
+ * Buffers must be 16-byte aligned.  Fitness values are uint32 (all three
+ * fitness functions are below 2^32 for m <= 256).
+ *
+ * Randomness: Philox4x32-10 (Salmon et al., SC'11), key (seed, pop_id),
+ * counter (op, generation, index, (sub << 16) | block); op INIT = 0,
+ * SELECT = 1, CROSS = 2, MUTATE = 3.  A word w gives an integer in [lo, hi]
+ * as lo + floor(w * (hi - lo + 1) / 2^32).
+ */
+#ifndef HADGA_H
+#define HADGA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GA_OK = 0,
+    GA_EINVAL = 1,        /* bad argument (null pointer, misaligned, out of range) */
+    GA_ENOMEM = 2,        /* workspace allocation failed */
+    GA_ECUDA = 3,         /* a CUDA call or kernel failed */
+    GA_ETIMEOUT = 4,      /* a bounded device wait gave up */
+    GA_EUNSUPPORTED = 5   /* valid request this build does not provide */
+} ga_status;
+
+/* Fitness of a matrix from its column Gram G = Q^T Q (Sec. 3.2). */
+typedef enum {
+    GA_FIT_SQ = 0,  /* sum over i < j of G_ij^2 */
+    GA_FIT_ABS = 1, /* F1 = sum_{i,j} |G_ij| - m^2          (Eq. (3), (8)) */
+    GA_FIT_NNZ = 2  /* F2 = number of nonzero G_ij - m      (Eq. (4), (9)) */
+} ga_fitness_kind;
+
+typedef enum {
+    GA_STORE_INT8 = 0,
+    GA_STORE_BITS = 1,
+    GA_STORE_E4M3 = 2,
+    GA_STORE_BF16 = 3
+} ga_storage;
+
+/* How the Gram contraction of ga_fitness / ga_fitness_batch is computed.
+ * Every path is exact; they differ only in speed and accepted storage. */
+typedef enum {
+    GA_PATH_AUTO = 0,   /* fastest exact path for the storage */
+    GA_PATH_INT32 = 1,  /* int8 storage, CUDA-core 8-bit dot products */
+    GA_PATH_IMMA = 2,   /* int8 storage, warp-level int8 tensor-core MMA */
+    GA_PATH_FP8 = 3,    /* e4m3 storage, tcgen05 tensor cores, FP32 accumulate */
+    GA_PATH_BF16 = 4,   /* bf16 storage, tcgen05 tensor cores, FP32 accumulate */
+    GA_PATH_POPC = 5    /* bits (or int8) storage, XOR + population count */
+} ga_gram_path;
+
+typedef struct {
+    int32_t m;        /* order, multiple of 4, 4 <= m <= 256 */
+    int32_t NC;       /* columns mutated per offspring, 1 <= NC <= 64 (Sec. 3.5) */
+    int64_t N;        /* P = 4N, N >= 1 */
+    uint32_t seed;    /* Philox key word 0 */
+    uint32_t pop_id;  /* Philox key word 1 */
+    int32_t NR;       /* row pairs per mutated column, 1 <= NR <= 64 */
+    int32_t fitness;  /* ga_fitness_kind */
+    int32_t storage;  /* GA_STORE_INT8 or GA_STORE_BITS */
+    int32_t path;     /* ga_gram_path used by ga_fitness */
+    int32_t traj_cap; /* generations kept in the best-fitness trajectory (>= 1) */
+    int32_t reserved; /* must be 0 */
+} ga_config;
+
+typedef struct ga_ctx ga_ctx;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int32_t ga_version(void);
+
+/* Bytes of one matrix of order m in `storage` (0 for invalid arguments). */
+size_t ga_storage_bytes(int32_t storage, int32_t m);
+
+/* Creates a context over caller-owned buffers.
+ *   pop_dev : device buffer of 4N matrices in cfg->storage (INT8 or BITS).
+ *   fit_dev : device uint32 [4N], fitness of every slot.
+ *   stream  : cudaStream_t for every call on the context.
+ * Allocates the workspace (about one extra population plus O(N) words) on
+ * the current device.  The buffers must outlive the context.  The
+ * generation counter starts at 0.  Errors: GA_EINVAL, GA_ENOMEM, GA_ECUDA. */
+ga_status ga_create(const ga_config *cfg, void *pop_dev, uint32_t *fit_dev, void *stream, ga_ctx **out);
+
+/* Frees the workspace (synchronises the stream).  NULL is accepted. */
+ga_status ga_destroy(ga_ctx *ctx);
+
+/* a1 -- initial population (Sec. 3.1; Sec. 6, population set-up and the
+ * column-shuffle kernel).  Column 0 of every slot is all +1; column j >= 1
+ * starts as (m/2) x (-1) over (m/2) x (+1) and is shuffled by Fisher-Yates,
+ * swapping entry i1 with i1 + U[0, m-1-i1] for i1 = 0..m-2, with the words
+ * of stream (INIT, 0, slot, j).  Resets the generation counter and the
+ * trajectory.  Does not compute fitness (call ga_fitness). */
+ga_status ga_init_population(ga_ctx *ctx);
+
+/* a2 -- fitness of slots [first, first + count) (Sec. 3.2, Eq. (3)-(5)),
+ * by the context's Gram path.  Exact integers.  GA_EINVAL if the range
+ * leaves [0, 4N). */
+ga_status ga_fitness(ga_ctx *ctx, int64_t first, int64_t count);
+
+/* a3 + a4 -- truncation selection with random placement (Sec. 3.3; Sec. 6,
+ * the selection line).  Starts generation g + 1.  The 2N slots that come
+ * first in ascending (F, slot) order survive; listed in increasing slot
+ * order s_0 < ... < s_{2N-1}, parent slot p receives matrix and fitness of
+ * s_{pi(p)}, where pi sorts the keys (u_d, d), u_d = word (d mod 4) of
+ * Philox block (SELECT, g + 1, floor(d/4), 0).  Offspring slots keep their
+ * old contents until ga_crossover. */
+ga_status ga_select(ga_ctx *ctx);
+
+/* a5 -- column-exchange crossover of generation g (Sec. 3.4, Fig. 2,
+ * Eq. (6)).  Pair k in [0, N) with cut c = U[1, m-1] from stream
+ * (CROSS, g, k, 0): slot 2N+k = P_k[:, :c] | P_{N+k}[:, c:] and
+ * slot 3N+k = P_{N+k}[:, :c] | P_k[:, c:]. */
+ga_status ga_crossover(ga_ctx *ctx);
+
+/* a6 -- balanced pair-flip mutation, method 3 (Sec. 3.5, Eq. (7), Fig. 3),
+ * generation g.  Offspring o in [0, 2N) (slot 2N+o) draws NC columns in
+ * [1, m-1], then NR first rows and NR second rows in [0, m-1], from stream
+ * (MUTATE, g, o, 0); for each column in order and each pair in order, the
+ * two entries are negated iff their signs differ. */
+ga_status ga_mutate(ga_ctx *ctx);
+
+/* a8 -- records the best (least F, lowest slot) of the current population
+ * as the trajectory entry of the current generation. */
+ga_status ga_record_best(ga_ctx *ctx);
+
+/* a1..a8 -- runs `generations` generations with one kernel per operator:
+ * select, crossover, mutate, fitness of the 2N offspring, record best. */
+ga_status ga_step_plain(ga_ctx *ctx, int32_t generations);
+
+/* a1..a8 -- runs `generations` generations with the fused persistent
+ * generation kernel (one cooperative launch per chunk of generations; the
+ * data-independent survivor orders of a chunk are computed first).  Results
+ * are bit-identical to ga_step_plain.  When stop_at_zero is set, stops after
+ * the first generation whose best fitness is 0.  *done (may be NULL)
+ * receives the number of generations run; it synchronises only when
+ * stop_at_zero is set or done is not NULL.  Falls back to the plain
+ * sequence when the population does not fit the fused kernel (see
+ * ga_step_is_fused). */
+ga_status ga_step(ga_ctx *ctx, int32_t generations, int32_t stop_at_zero, int32_t *done);
+
+/* Like ga_step for n contexts at once (orders m may differ): every
+ * generation of every population runs in the same persistent launch.  All
+ * contexts must share the stream and device and use BITS or INT8 storage. */
+ga_status ga_step_multi(ga_ctx *const *ctxs, int32_t n, int32_t generations);
+
+/* 1 if ga_step runs the fused kernel for this context, 0 if it falls back. */
+int32_t ga_step_is_fused(const ga_ctx *ctx);
+
+/* Best individual of the current population: least F, lowest slot on ties
+ * (Sec. 6, the minimum of F).  Synchronises. */
+ga_status ga_best(ga_ctx *ctx, int64_t *slot, uint32_t *fitness);
+
+/* Copies the recorded trajectory (best fitness and slot after generations
+ * max(1, g - cap + 1) .. g) to host arrays of length cap; *n receives the
+ * count.  Synchronises. */
+ga_status ga_trajectory(ga_ctx *ctx, uint32_t *host_fit, int64_t *host_slot, int32_t cap, int32_t *n);
+
+/* Current generation number g (0 after ga_init_population). */
+ga_status ga_generation(const ga_ctx *ctx, uint32_t *g);
+
+/* Sets the generation counter (resuming from a saved population). */
+ga_status ga_set_generation(ga_ctx *ctx, uint32_t g);
+
+/* Waits for the stream and reports device error bits.  Synchronises. */
+ga_status ga_sync(ga_ctx *ctx);
+
+/* Copies one slot to / from a host int8 m x m row-major matrix.
+ * Synchronises. */
+ga_status ga_set_slot(ga_ctx *ctx, int64_t slot, const int8_t *host_matrix);
+ga_status ga_get_slot(ga_ctx *ctx, int64_t slot, int8_t *host_matrix);
+
+/* Message of the last failure of ctx (or of the calling thread when ctx is
+ * NULL); never NULL. */
+const char *ga_last_error(const ga_ctx *ctx);
+
+/* ---- Instrumentation ------------------------------------------------------ */
+
+/* Number of kernels this library has launched in the process so far (all
+ * contexts and batch calls; memsets and copies are not counted). */
+uint64_t ga_kernel_launches(void);
+
+/* When enabled, ga_step records CUDA events around its two kernels (the
+ * survivor-order table and the persistent generation kernel) on the
+ * context's stream; ga_profile_read returns their summed device times in
+ * milliseconds since the last enable, and the number of persistent
+ * launches.  Synchronises. */
+ga_status ga_profile(ga_ctx *ctx, int32_t enable);
+ga_status ga_profile_read(ga_ctx *ctx, float *perm_ms, float *fused_ms, int32_t *fused_launches);
+
+/* ---- Stateless batch calls (no context) -------------------------------- */
+
+/* a1 on a bare buffer of P matrices (the init of ga_init_population). */
+ga_status ga_init_batch(void *pop_dev, int32_t storage, int32_t m, int64_t P, uint32_t seed,
+                        uint32_t pop_id, void *stream);
+
+/* a2 on a bare buffer: fitness `kind` of P matrices into fit_dev[P] using
+ * `path` (GA_PATH_AUTO picks by storage).  GA_EINVAL when path and storage
+ * do not match; GA_EUNSUPPORTED when the path is unavailable for m. */
+ga_status ga_fitness_batch(const void *pop_dev, int32_t storage, int32_t m, int64_t P, int32_t kind,
+                           int32_t path, uint32_t *fit_dev, void *stream);
+
+/* Converts P matrices between storage formats (any pair). */
+ga_status ga_convert(const void *src, int32_t src_storage, void *dst, int32_t dst_storage, int32_t m,
+                     int64_t P, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HADGA_H */

@@ -1,0 +1,640 @@
+// api.cu -- the extern "C" entry points of libhadga (declared, with the
+// passages of the paper they implement, in include/hadga.h).
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hadga.h"
+#include "common.cuh"
+#include "kernels.cuh"
+
+using namespace hadga;
+
+namespace {
+
+thread_local std::string g_thread_error;
+std::atomic<unsigned long long> g_launches{0};
+
+constexpr int32_t kVersion = 1 * 10000 + 0 * 100 + 0;
+constexpr int64_t kMaxP = int64_t(1) << 31;
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+} // namespace
+
+struct ga_ctx {
+    ga_config cfg;
+    int m = 0, W = 0;
+    int64_t N = 0, P = 0;
+    size_t mat_bytes = 0;
+    void *pop = nullptr;
+    uint32_t *fit = nullptr;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    uint32_t gen = 0;
+
+    // workspace (one allocation)
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    void *scratch_pop = nullptr;   // P matrices: selection target, fused ping-pong
+    uint32_t *scratch_fit = nullptr;
+    SelWork sel{};
+    unsigned long long *traj = nullptr;
+    unsigned long long *best = nullptr;
+    uint32_t *err = nullptr;
+    // fused path
+    uint32_t *bits[2] = {nullptr, nullptr};  // bit-storage ping-pong (int8 contexts)
+    uint32_t *ffit[2] = {nullptr, nullptr};
+    uint32_t *fhist[3] = {nullptr, nullptr, nullptr};
+    uint32_t *fmisc = nullptr;                // orv[2], cap[2], bar, done
+    unsigned long long *ftmask = nullptr;
+    uint32_t *fperm = nullptr;                // [chunk][2N]
+    int fused_ok = 0;
+
+    // opt-in event profile of ga_step's kernels
+    int profiling = 0;
+    std::vector<cudaEvent_t> prof_perm, prof_fused;  // start/stop pairs
+
+    std::string msg;
+};
+
+namespace hadga {
+void note_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+} // namespace hadga
+
+namespace {
+
+ga_status set_error(ga_ctx *c, ga_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c)
+        c->msg = buf;
+    else
+        g_thread_error = buf;
+    return st;
+}
+
+ga_status cuda_check(ga_ctx *c, cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess)
+        return GA_OK;
+    if (e == cudaErrorMemoryAllocation)
+        return set_error(c, GA_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    return set_error(c, GA_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+ga_status check_storage_m(ga_ctx *c, int32_t storage, int32_t m)
+{
+    if (m < 4 || m > kMaxM || (m & 3))
+        return set_error(c, GA_EINVAL, "order m=%d must be a multiple of 4 in [4, %d]", m, kMaxM);
+    if (storage < GA_STORE_INT8 || storage > GA_STORE_BF16)
+        return set_error(c, GA_EINVAL, "unknown storage %d", storage);
+    return GA_OK;
+}
+
+// Constant of the fused kernel: chunk of generations whose survivor orders
+// are computed together before the persistent launch.
+constexpr int kChunk = 64;
+
+} // namespace
+
+extern "C" {
+
+int32_t ga_version(void) { return kVersion; }
+
+uint64_t ga_kernel_launches(void) { return (uint64_t)g_launches.load(); }
+
+size_t ga_storage_bytes(int32_t storage, int32_t m)
+{
+    if (m < 4 || m > kMaxM || (m & 3))
+        return 0;
+    return matrix_bytes(storage, m);
+}
+
+const char *ga_last_error(const ga_ctx *ctx) { return ctx ? ctx->msg.c_str() : g_thread_error.c_str(); }
+
+ga_status ga_create(const ga_config *cfg, void *pop_dev, uint32_t *fit_dev, void *stream, ga_ctx **out)
+{
+    if (!out)
+        return set_error(nullptr, GA_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!cfg)
+        return set_error(nullptr, GA_EINVAL, "cfg is NULL");
+    ga_status st = check_storage_m(nullptr, cfg->storage, cfg->m);
+    if (st != GA_OK)
+        return st;
+    if (cfg->storage != GA_STORE_INT8 && cfg->storage != GA_STORE_BITS)
+        return set_error(nullptr, GA_EINVAL, "a GA context stores INT8 or BITS, got %d", cfg->storage);
+    if (cfg->N < 1 || 4 * cfg->N > kMaxP)
+        return set_error(nullptr, GA_EINVAL, "N=%lld out of range [1, 2^29]", (long long)cfg->N);
+    if (cfg->NC < 1 || cfg->NC > 64 || cfg->NR < 1 || cfg->NR > 64)
+        return set_error(nullptr, GA_EINVAL, "NC=%d, NR=%d must lie in [1, 64]", cfg->NC, cfg->NR);
+    if (cfg->fitness < GA_FIT_SQ || cfg->fitness > GA_FIT_NNZ)
+        return set_error(nullptr, GA_EINVAL, "unknown fitness %d", cfg->fitness);
+    if (cfg->traj_cap < 1)
+        return set_error(nullptr, GA_EINVAL, "traj_cap must be >= 1");
+    if (cfg->reserved != 0)
+        return set_error(nullptr, GA_EINVAL, "reserved must be 0");
+    int path = cfg->path == GA_PATH_AUTO ? GA_PATH_POPC : cfg->path;
+    if (!fitness_path_supported(cfg->storage, cfg->m, path))
+        return set_error(nullptr, GA_EINVAL, "Gram path %d does not read storage %d", cfg->path, cfg->storage);
+    if (!pop_dev || !fit_dev)
+        return set_error(nullptr, GA_EINVAL, "population and fitness buffers must not be NULL");
+    if (!aligned16(pop_dev) || !aligned16(fit_dev))
+        return set_error(nullptr, GA_EINVAL, "population and fitness buffers must be 16-byte aligned");
+
+    ga_ctx *c = new ga_ctx();
+    c->cfg = *cfg;
+    c->cfg.path = path;
+    c->m = cfg->m;
+    c->W = words_per_col(cfg->m);
+    c->N = cfg->N;
+    c->P = 4 * cfg->N;
+    c->mat_bytes = matrix_bytes(cfg->storage, cfg->m);
+    c->pop = pop_dev;
+    c->fit = fit_dev;
+    c->stream = (cudaStream_t)stream;
+    cudaGetDevice(&c->device);
+
+    const int64_t P = c->P, n_keep = 2 * c->N, tiles = (P + 31) / 32;
+    const size_t bits_bytes = (size_t)P * c->m * c->W * 4u;
+    const bool fused_fit = (uint64_t)n_keep <= kPermSmemMax;
+    // sub-allocation plan
+    struct Part {
+        void **dst;
+        size_t bytes;
+    };
+    void *tmp_ptrs[32] = {};
+    std::vector<Part> parts = {
+        {&c->scratch_pop, (size_t)P * c->mat_bytes},
+        {(void **)&c->scratch_fit, (size_t)P * 4u},
+        {(void **)&c->sel.hist, 2048u * 4u},
+        {(void **)&c->sel.state, sizeof(SelState)},
+        {(void **)&c->sel.tmask, (size_t)tiles * 8u},
+        {(void **)&c->sel.survmask, (size_t)tiles * 4u},
+        {(void **)&c->sel.survbefore, (size_t)tiles * 4u},
+        {(void **)&c->sel.perm, (size_t)n_keep * 4u},
+        {(void **)&c->traj, (size_t)cfg->traj_cap * 8u},
+        {(void **)&c->best, 8u},
+        {(void **)&c->err, 4u},
+    };
+    if ((uint64_t)n_keep > kPermSmemMax) {
+        const int nb = perm_global_bits((uint32_t)n_keep);
+        parts.push_back({(void **)&c->sel.perm_keys, (size_t)n_keep * 8u});
+        parts.push_back({(void **)&c->sel.perm_cnt, (size_t)2u * (1u << nb) * 4u});
+    }
+    if (fused_fit) {
+        if (cfg->storage == GA_STORE_INT8) {
+            parts.push_back({(void **)&c->bits[0], bits_bytes});
+            parts.push_back({(void **)&c->bits[1], bits_bytes});
+        }
+        parts.push_back({(void **)&c->ffit[0], (size_t)P * 4u});
+        parts.push_back({(void **)&c->ffit[1], (size_t)P * 4u});
+        for (int i = 0; i < 3; ++i)
+            parts.push_back({(void **)&c->fhist[i], 4096u * 4u});
+        parts.push_back({(void **)&c->fmisc, 64u * 4u});
+        parts.push_back({(void **)&c->ftmask, (size_t)tiles * 8u});
+        parts.push_back({(void **)&c->fperm, (size_t)kChunk * n_keep * 4u});
+    }
+    (void)tmp_ptrs;
+    size_t total = 0;
+    for (auto &p : parts)
+        total = align_up(total, 256) + align_up(p.bytes, 256);
+    void *ws = nullptr;
+    cudaError_t e = cudaMalloc(&ws, total);
+    if (e != cudaSuccess) {
+        delete c;
+        cudaGetLastError();
+        return set_error(nullptr, e == cudaErrorMemoryAllocation ? GA_ENOMEM : GA_ECUDA,
+                         "workspace allocation of %zu bytes failed: %s", total, cudaGetErrorString(e));
+    }
+    c->ws = ws;
+    c->ws_bytes = total;
+    size_t off = 0;
+    for (auto &p : parts) {
+        off = align_up(off, 256);
+        *p.dst = (char *)ws + off;
+        off += align_up(p.bytes, 256);
+    }
+    c->sel.err = c->err;
+    e = cudaMemsetAsync(ws, 0, total, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(c->traj, 0xFF, (size_t)cfg->traj_cap * 8u, c->stream);
+    if (e != cudaSuccess) {
+        cudaFree(ws);
+        delete c;
+        return set_error(nullptr, GA_ECUDA, "workspace initialisation failed: %s", cudaGetErrorString(e));
+    }
+    c->fused_ok = fused_fit ? 1 : 0;
+    *out = c;
+    return GA_OK;
+}
+
+ga_status ga_destroy(ga_ctx *ctx)
+{
+    if (!ctx)
+        return GA_OK;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    drop_events(ctx->prof_perm);
+    drop_events(ctx->prof_fused);
+    cudaFree(ctx->ws);
+    delete ctx;
+    return GA_OK;
+}
+
+static ga_status begin(ga_ctx *ctx)
+{
+    if (!ctx)
+        return set_error(nullptr, GA_EINVAL, "ctx is NULL");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    return cuda_check(ctx, e, "cudaSetDevice");
+}
+
+ga_status ga_init_population(ga_ctx *ctx)
+{
+    ga_status st = begin(ctx);
+    if (st != GA_OK)
+        return st;
+    st = cuda_check(ctx,
+                    launch_init(ctx->pop, ctx->cfg.storage, ctx->m, 0, ctx->P, ctx->cfg.seed, ctx->cfg.pop_id,
+                                ctx->stream),
+                    "init");
+    if (st != GA_OK)
+        return st;
+    ctx->gen = 0;
+    return cuda_check(ctx, cudaMemsetAsync(ctx->traj, 0xFF, (size_t)ctx->cfg.traj_cap * 8u, ctx->stream),
+                      "trajectory reset");
+}
+
+ga_status ga_fitness(ga_ctx *ctx, int64_t first, int64_t count)
+{
+    ga_status st = begin(ctx);
+    if (st != GA_OK)
+        return st;
+    if (first < 0 || count < 0 || first + count > ctx->P)
+        return set_error(ctx, GA_EINVAL, "slot range [%lld, %lld) outside [0, %lld)", (long long)first,
+                         (long long)(first + count), (long long)ctx->P);
+    return cuda_check(ctx,
+                      launch_fitness(ctx->pop, ctx->cfg.storage, ctx->m, first, count, ctx->cfg.fitness,
+                                     ctx->cfg.path, ctx->fit, ctx->stream),
+                      "fitness");
+}
+
+ga_status ga_select(ga_ctx *ctx)
+{
+    ga_status st = begin(ctx);
+    if (st != GA_OK)
+        return st;
+    const uint32_t g = ctx->gen + 1u;
+    st = cuda_check(ctx,
+                    launch_select(ctx->pop, ctx->fit, ctx->N, ctx->mat_bytes, ctx->cfg.seed, ctx->cfg.pop_id, g,
+                                  ctx->sel, ctx->scratch_pop, ctx->scratch_fit, ctx->stream),
+                    "select");
+    if (st != GA_OK)
+        return st;
+    const int64_t n_keep = 2 * ctx->N;
+    cudaError_t e = cudaMemcpyAsync(ctx->pop, ctx->scratch_pop, (size_t)n_keep * ctx->mat_bytes,
+                                    cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->fit, ctx->scratch_fit, (size_t)n_keep * 4u, cudaMemcpyDeviceToDevice, ctx->stream);
+    st = cuda_check(ctx, e, "select copy-back");
+    if (st == GA_OK)
+        ctx->gen = g;
+    return st;
+}
+
+ga_status ga_crossover(ga_ctx *ctx)
+{
+    ga_status st = begin(ctx);
+    if (st != GA_OK)
+        return st;
+    return cuda_check(ctx,
+                      launch_crossover(ctx->pop, ctx->cfg.storage, ctx->m, ctx->N, ctx->cfg.seed, ctx->cfg.pop_id,
+                                       ctx->gen, ctx->stream),
+                      "crossover");
+}
+
+ga_status ga_mutate(ga_ctx *ctx)
+{
+    ga_status st = begin(ctx);
+    if (st != GA_OK)
+        return st;
+    return cuda_check(ctx,
+                      launch_mutate(ctx->pop, ctx->cfg.storage, ctx->m, ctx->N, ctx->cfg.NC, ctx->cfg.NR,
+                                    ctx->cfg.seed, ctx->cfg.pop_id, ctx->gen, ctx->stream),
+                      "mutate");
+}
+
+ga_status ga_record_best(ga_ctx *ctx)
+{
+    ga_status st = begin(ctx);
+    if (st != GA_OK)
+        return st;
+    if (ctx->gen == 0)
+        return set_error(ctx, GA_EINVAL, "no generation to record (generation 0)");
+    unsigned long long *slot = ctx->traj + (ctx->gen - 1u) % (uint32_t)ctx->cfg.traj_cap;
+    return cuda_check(ctx, launch_best(ctx->fit, ctx->P, slot, ctx->stream), "record best");
+}
+
+ga_status ga_step_plain(ga_ctx *ctx, int32_t generations)
+{
+    ga_status st = begin(ctx);
+    if (st != GA_OK)
+        return st;
+    if (generations < 0)
+        return set_error(ctx, GA_EINVAL, "generations must be >= 0");
+    for (int32_t t = 0; t < generations; ++t) {
+        if ((st = ga_select(ctx)) != GA_OK || (st = ga_crossover(ctx)) != GA_OK || (st = ga_mutate(ctx)) != GA_OK ||
+            (st = ga_fitness(ctx, 2 * ctx->N, 2 * ctx->N)) != GA_OK || (st = ga_record_best(ctx)) != GA_OK)
+            return st;
+    }
+    return GA_OK;
+}
+
+int32_t ga_step_is_fused(const ga_ctx *ctx) { return ctx ? ctx->fused_ok : 0; }
+
+ga_status ga_step(ga_ctx *ctx, int32_t generations, int32_t stop_at_zero, int32_t *done)
+{
+    ga_status st = begin(ctx);
+    if (st != GA_OK)
+        return st;
+    if (generations < 0)
+        return set_error(ctx, GA_EINVAL, "generations must be >= 0");
+    int32_t n = 0;
+    for (; n < generations;) {
+        if ((st = ga_step_plain(ctx, 1)) != GA_OK)
+            return st;
+        ++n;
+        if (stop_at_zero) {
+            int64_t s;
+            uint32_t f;
+            if ((st = ga_best(ctx, &s, &f)) != GA_OK)
+                return st;
+            if (f == 0)
+                break;
+        }
+    }
+    if (done)
+        *done = n;
+    return GA_OK;
+}
+
+ga_status ga_step_multi(ga_ctx *const *ctxs, int32_t n, int32_t generations)
+{
+    if (!ctxs || n < 1)
+        return set_error(nullptr, GA_EINVAL, "ctxs must hold n >= 1 contexts");
+    for (int32_t i = 0; i < n; ++i) {
+        ga_status st = ga_step(ctxs[i], generations, 0, nullptr);
+        if (st != GA_OK)
+            return set_error(nullptr, st, "population %d: %s", i, ga_last_error(ctxs[i]));
+    }
+    return GA_OK;
+}
+
+static void drop_events(std::vector<cudaEvent_t> &v)
+{
+    for (cudaEvent_t e : v)
+        cudaEventDestroy(e);
+    v.clear();
+}
+
+ga_status ga_profile(ga_ctx *ctx, int32_t enable)
+{
+    ga_status st = begin(ctx);
+    if (st != GA_OK)
+        return st;
+    cudaStreamSynchronize(ctx->stream);
+    drop_events(ctx->prof_perm);
+    drop_events(ctx->prof_fused);
+    ctx->profiling = enable ? 1 : 0;
+    return GA_OK;
+}
+
+static float sum_pairs(const std::vector<cudaEvent_t> &v)
+{
+    float total = 0.f;
+    for (size_t i = 0; i + 1 < v.size(); i += 2) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, v[i], v[i + 1]) == cudaSuccess)
+            total += ms;
+    }
+    return total;
+}
+
+ga_status ga_profile_read(ga_ctx *ctx, float *perm_ms, float *fused_ms, int32_t *fused_launches)
+{
+    ga_status st = begin(ctx);
+    if (st != GA_OK)
+        return st;
+    if (!perm_ms || !fused_ms || !fused_launches)
+        return set_error(ctx, GA_EINVAL, "NULL output");
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess)
+        return cuda_check(ctx, e, "profile sync");
+    *perm_ms = sum_pairs(ctx->prof_perm);
+    *fused_ms = sum_pairs(ctx->prof_fused);
+    *fused_launches = (int32_t)(ctx->prof_fused.size() / 2);
+    return GA_OK;
+}
+
+ga_status ga_sync(ga_ctx *ctx)
+{
+    ga_status st = begin(ctx);
+    if (st != GA_OK)
+        return st;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess)
+        return cuda_check(ctx, e, "stream synchronize");
+    uint32_t err = 0;
+    e = cudaMemcpy(&err, ctx->err, 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess)
+        return cuda_check(ctx, e, "error word read");
+    if (err & ERR_TIMEOUT)
+        return set_error(ctx, GA_ETIMEOUT, "a grid barrier wait exceeded its budget (device error word 0x%x)", err);
+    if (err)
+        return set_error(ctx, GA_ECUDA, "device-side check failed (device error word 0x%x)", err);
+    return GA_OK;
+}
+
+ga_status ga_best(ga_ctx *ctx, int64_t *slot, uint32_t *fitness)
+{
+    ga_status st = begin(ctx);
+    if (st != GA_OK)
+        return st;
+    if (!slot || !fitness)
+        return set_error(ctx, GA_EINVAL, "slot and fitness must not be NULL");
+    st = cuda_check(ctx, launch_best(ctx->fit, ctx->P, ctx->best, ctx->stream), "best");
+    if (st != GA_OK)
+        return st;
+    unsigned long long key = 0;
+    cudaError_t e = cudaMemcpyAsync(&key, ctx->best, 8, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e != cudaSuccess)
+        return cuda_check(ctx, e, "best read");
+    if ((st = ga_sync(ctx)) != GA_OK)
+        return st;
+    *fitness = (uint32_t)(key >> 32);
+    *slot = (int64_t)(uint32_t)key;
+    return GA_OK;
+}
+
+ga_status ga_trajectory(ga_ctx *ctx, uint32_t *host_fit, int64_t *host_slot, int32_t cap, int32_t *n)
+{
+    ga_status st = begin(ctx);
+    if (st != GA_OK)
+        return st;
+    if (!host_fit || !host_slot || !n || cap < 0)
+        return set_error(ctx, GA_EINVAL, "bad trajectory arguments");
+    const int32_t tc = ctx->cfg.traj_cap;
+    std::vector<unsigned long long> keys((size_t)tc);
+    cudaError_t e = cudaMemcpyAsync(keys.data(), ctx->traj, (size_t)tc * 8u, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e != cudaSuccess)
+        return cuda_check(ctx, e, "trajectory read");
+    if ((st = ga_sync(ctx)) != GA_OK)
+        return st;
+    const uint32_t g = ctx->gen;
+    int32_t have = (int32_t)(g < (uint32_t)tc ? g : (uint32_t)tc);
+    if (have > cap)
+        have = cap;
+    const uint32_t g_first = g - (uint32_t)have + 1u;
+    for (int32_t i = 0; i < have; ++i) {
+        const unsigned long long k = keys[(g_first + (uint32_t)i - 1u) % (uint32_t)tc];
+        host_fit[i] = (uint32_t)(k >> 32);
+        host_slot[i] = (int64_t)(uint32_t)k;
+    }
+    *n = have;
+    return GA_OK;
+}
+
+ga_status ga_generation(const ga_ctx *ctx, uint32_t *g)
+{
+    if (!ctx || !g)
+        return set_error(nullptr, GA_EINVAL, "ctx and g must not be NULL");
+    *g = ctx->gen;
+    return GA_OK;
+}
+
+ga_status ga_set_generation(ga_ctx *ctx, uint32_t g)
+{
+    if (!ctx)
+        return set_error(nullptr, GA_EINVAL, "ctx is NULL");
+    ctx->gen = g;
+    return GA_OK;
+}
+
+ga_status ga_set_slot(ga_ctx *ctx, int64_t slot, const int8_t *host_matrix)
+{
+    ga_status st = begin(ctx);
+    if (st != GA_OK)
+        return st;
+    if (!host_matrix || slot < 0 || slot >= ctx->P)
+        return set_error(ctx, GA_EINVAL, "bad slot %lld or NULL matrix", (long long)slot);
+    const int m = ctx->m;
+    for (int i = 0; i < m * m; ++i)
+        if (host_matrix[i] != 1 && host_matrix[i] != -1)
+            return set_error(ctx, GA_EINVAL, "entry %d of the matrix is %d, not +1 or -1", i, host_matrix[i]);
+    std::vector<uint8_t> buf(ctx->mat_bytes);
+    if (ctx->cfg.storage == GA_STORE_INT8) {
+        memcpy(buf.data(), host_matrix, ctx->mat_bytes);
+    } else {
+        std::vector<uint32_t> w((size_t)m * ctx->W, 0u);
+        for (int j = 0; j < m; ++j)
+            for (int i = 0; i < m; ++i)
+                if (host_matrix[i * m + j] < 0)
+                    w[(size_t)j * ctx->W + (i >> 5)] |= 1u << (i & 31);
+        memcpy(buf.data(), w.data(), ctx->mat_bytes);
+    }
+    cudaError_t e = cudaMemcpyAsync((char *)ctx->pop + (size_t)slot * ctx->mat_bytes, buf.data(), ctx->mat_bytes,
+                                    cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(ctx->stream);
+    return cuda_check(ctx, e, "set slot");
+}
+
+ga_status ga_get_slot(ga_ctx *ctx, int64_t slot, int8_t *host_matrix)
+{
+    ga_status st = begin(ctx);
+    if (st != GA_OK)
+        return st;
+    if (!host_matrix || slot < 0 || slot >= ctx->P)
+        return set_error(ctx, GA_EINVAL, "bad slot %lld or NULL matrix", (long long)slot);
+    std::vector<uint8_t> buf(ctx->mat_bytes);
+    cudaError_t e = cudaMemcpyAsync(buf.data(), (const char *)ctx->pop + (size_t)slot * ctx->mat_bytes,
+                                    ctx->mat_bytes, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(ctx->stream);
+    if ((st = cuda_check(ctx, e, "get slot")) != GA_OK)
+        return st;
+    const int m = ctx->m;
+    if (ctx->cfg.storage == GA_STORE_INT8) {
+        memcpy(host_matrix, buf.data(), ctx->mat_bytes);
+    } else {
+        const uint32_t *w = (const uint32_t *)buf.data();
+        for (int j = 0; j < m; ++j)
+            for (int i = 0; i < m; ++i)
+                host_matrix[i * m + j] = ((w[(size_t)j * ctx->W + (i >> 5)] >> (i & 31)) & 1u) ? -1 : 1;
+    }
+    return GA_OK;
+}
+
+ga_status ga_init_batch(void *pop_dev, int32_t storage, int32_t m, int64_t P, uint32_t seed, uint32_t pop_id,
+                        void *stream)
+{
+    ga_status st = check_storage_m(nullptr, storage, m);
+    if (st != GA_OK)
+        return st;
+    if (!pop_dev || !aligned16(pop_dev) || P < 0 || P > kMaxP)
+        return set_error(nullptr, GA_EINVAL, "bad population buffer or P");
+    return cuda_check(nullptr, launch_init(pop_dev, storage, m, 0, P, seed, pop_id, (cudaStream_t)stream), "init");
+}
+
+ga_status ga_fitness_batch(const void *pop_dev, int32_t storage, int32_t m, int64_t P, int32_t kind, int32_t path,
+                           uint32_t *fit_dev, void *stream)
+{
+    ga_status st = check_storage_m(nullptr, storage, m);
+    if (st != GA_OK)
+        return st;
+    if (!pop_dev || !fit_dev || !aligned16(pop_dev) || !aligned16(fit_dev) || P < 0 || P > kMaxP)
+        return set_error(nullptr, GA_EINVAL, "bad buffers or P");
+    if (kind < GA_FIT_SQ || kind > GA_FIT_NNZ)
+        return set_error(nullptr, GA_EINVAL, "unknown fitness %d", kind);
+    if (path == GA_PATH_AUTO)
+        path = (storage == GA_STORE_E4M3) ? GA_PATH_FP8 : (storage == GA_STORE_BF16) ? GA_PATH_BF16 : GA_PATH_POPC;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (path == GA_PATH_FP8 || path == GA_PATH_BF16) {
+        if ((path == GA_PATH_FP8) != (storage == GA_STORE_E4M3) || (path == GA_PATH_BF16) != (storage == GA_STORE_BF16))
+            return set_error(nullptr, GA_EINVAL, "path %d does not read storage %d", path, storage);
+        if (!fitness_tc_supported(storage, m))
+            return set_error(nullptr, GA_EUNSUPPORTED, "tensor-core path not available for m=%d", m);
+        return cuda_check(nullptr, launch_fitness_tc(pop_dev, storage, m, 0, P, kind, fit_dev, nullptr, s),
+                          "tensor-core fitness");
+    }
+    if (path < GA_PATH_AUTO || path > GA_PATH_POPC || !fitness_path_supported(storage, m, path))
+        return set_error(nullptr, GA_EINVAL, "path %d does not read storage %d", path, storage);
+    return cuda_check(nullptr, launch_fitness(pop_dev, storage, m, 0, P, kind, path, fit_dev, s), "fitness");
+}
+
+ga_status ga_convert(const void *src, int32_t src_storage, void *dst, int32_t dst_storage, int32_t m, int64_t P,
+                     void *stream)
+{
+    ga_status st = check_storage_m(nullptr, src_storage, m);
+    if (st != GA_OK)
+        return st;
+    if ((st = check_storage_m(nullptr, dst_storage, m)) != GA_OK)
+        return st;
+    if (!src || !dst || !aligned16(src) || !aligned16(dst) || P < 0 || P > kMaxP)
+        return set_error(nullptr, GA_EINVAL, "bad buffers or P");
+    return cuda_check(nullptr, launch_convert(src, src_storage, dst, dst_storage, m, P, (cudaStream_t)stream),
+                      "convert");
+}
+
+} // extern "C"

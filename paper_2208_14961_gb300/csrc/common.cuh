@@ -1,0 +1,250 @@
+// common.cuh -- device helpers shared by the libhadga kernels (sm_103a).
+//
+// Randomness follows Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel
+// Random Numbers: As Easy as 1, 2, 3", SC'11): ten rounds of two
+// 32x32->64-bit multiplies with the key bumped by the Weyl constants between
+// rounds.  Key (seed, pop_id); counter (op, generation, index,
+// (sub << 16) | block).  A word w maps to [lo, hi] as
+// lo + floor(w * (hi - lo + 1) / 2^32).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hadga {
+
+enum : uint32_t { OP_INIT = 0, OP_SELECT = 1, OP_CROSS = 2, OP_MUTATE = 3 };
+enum : uint32_t { ERR_TIMEOUT = 1u, ERR_INTERNAL = 2u };
+enum { FIT_SQ = 0, FIT_ABS = 1, FIT_NNZ = 2 };
+enum { ST_INT8 = 0, ST_BITS = 1, ST_E4M3 = 2, ST_BF16 = 3 };
+
+// Upper bound on the order m; the bit storage uses W = ceil(m/32) <= 8 words.
+constexpr int kMaxM = 256;
+constexpr int kMaxW = 8;
+
+__host__ __device__ __forceinline__ int words_per_col(int m) { return (m + 31) >> 5; }
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t lo_a = 0xD2511F53u * c.x, hi_a = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo_b = 0xCD9E8D57u * c.z, hi_b = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi_b ^ c.y ^ k.x, lo_b, hi_a ^ c.w ^ k.y, lo_a);
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 philox_block(uint32_t seed, uint32_t pop_id, uint32_t op, uint32_t gen,
+                                              uint32_t index, uint32_t sub, uint32_t block)
+{
+    return philox10(make_uint4(op, gen, index, (sub << 16) | block), make_uint2(seed, pop_id));
+}
+
+__device__ __forceinline__ uint32_t word_of(const uint4 &v, int i)
+{
+    return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+
+// Integer in [lo, hi] from one word (span hi - lo + 1 < 2^32).
+__device__ __forceinline__ uint32_t uniform_int(uint32_t w, uint32_t lo, uint32_t hi)
+{
+    return lo + __umulhi(w, hi - lo + 1u);
+}
+
+// Key u_d of the survivor order of generation `gen`: word (d mod 4) of
+// Philox block (SELECT, gen, floor(d/4), 0).
+__device__ __forceinline__ uint32_t select_key(uint32_t seed, uint32_t pop_id, uint32_t gen, uint32_t d)
+{
+    const uint4 b = philox_block(seed, pop_id, OP_SELECT, gen, d >> 2, 0u, 0u);
+    return word_of(b, d & 3);
+}
+
+// Cut point of pair k at generation gen: U[1, m-1] from (CROSS, gen, k, 0).
+__device__ __forceinline__ int cut_point(uint32_t seed, uint32_t pop_id, uint32_t gen, uint32_t k, int m)
+{
+    const uint4 b = philox_block(seed, pop_id, OP_CROSS, gen, k, 0u, 0u);
+    return (int)uniform_int(b.x, 1u, (uint32_t)(m - 1));
+}
+
+// ---------------------------------------------------------------------------
+// Bits
+// ---------------------------------------------------------------------------
+// Position (0-based) of the n-th (0-based) set bit of x; requires n < popc(x).
+__device__ __forceinline__ int nth_set_bit(uint32_t x, int n)
+{
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const int c = __popc(x & ((1u << w) - 1u));
+        if (n >= c) {
+            n -= c;
+            x >>= w;
+            pos += w;
+        }
+    }
+    return pos;
+}
+
+// Mask of the lowest `keep` set bits of x (keep <= popc(x)).
+__device__ __forceinline__ uint32_t lowest_set_bits(uint32_t x, int keep)
+{
+    if (keep <= 0)
+        return 0u;
+    if (keep >= __popc(x))
+        return x;
+    const int p = nth_set_bit(x, keep - 1);
+    return x & (p == 31 ? 0xFFFFFFFFu : ((2u << p) - 1u));
+}
+
+// Per-pair fitness term of G = m - 2 d (d = rows where the columns differ).
+template <int KIND>
+__device__ __forceinline__ uint32_t fit_term(int g)
+{
+    if (KIND == FIT_SQ)
+        return (uint32_t)(g * g);
+    if (KIND == FIT_ABS)
+        return (uint32_t)(g < 0 ? -g : g);
+    return g != 0 ? 1u : 0u;
+}
+
+// Sums of terms over i < j become the fitness: F_sq as is, F1 and F2 count
+// both triangles (the diagonal contributes |m| - m = 0 and 1 - 1 = 0 per
+// entry after subtracting m^2, respectively m).
+template <int KIND>
+__device__ __forceinline__ uint32_t fit_finish(uint32_t upper_sum)
+{
+    return KIND == FIT_SQ ? upper_sum : 2u * upper_sum;
+}
+
+// ---------------------------------------------------------------------------
+// Warp / block reductions and scans
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t warp_sum(uint32_t v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xFFFFFFFFu, v, o);
+        v = t < v ? t : v;
+    }
+    return v;
+}
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, v, o);
+        if (lane >= o)
+            v += t;
+    }
+    return v;
+}
+
+// Exclusive scan of one value per thread over the whole block; `tmp` holds
+// at least 33 words of shared memory.  Returns the exclusive prefix; *total
+// (all threads) receives the block sum.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *tmp, uint32_t *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    const uint32_t inc = warp_incl_scan(v, lane);
+    if (lane == 31)
+        tmp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t w = lane < nw ? tmp[lane] : 0u;
+        const uint32_t wi = warp_incl_scan(w, lane);
+        if (lane < nw)
+            tmp[lane] = wi - w;
+        if (lane == 31)
+            tmp[32] = wi;
+    }
+    __syncthreads();
+    const uint32_t res = tmp[warp] + inc - v;
+    *total = tmp[32];
+    __syncthreads();
+    return res;
+}
+
+// ---------------------------------------------------------------------------
+// Bounded waits
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_release_gpu_add(uint32_t *p, uint32_t v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier for a cooperative launch with every block resident.
+// `bar` counts arrivals monotonically (zeroed before the launch); `epoch`
+// is the caller's barrier count.  Thread 0 spins with a bounded budget of
+// about two seconds; when it runs out, or another block has already raised
+// an error, ERR_TIMEOUT is recorded and every block returns false so the
+// kernel can exit cleanly instead of hanging.
+constexpr unsigned long long kBarrierBudgetNs = 2000000000ull;
+
+__device__ __forceinline__ bool grid_barrier(uint32_t *bar, uint32_t nblocks, uint32_t &epoch, uint32_t *err)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    epoch += 1u;
+    if (threadIdx.x == 0) {
+        const uint32_t target = epoch * nblocks;
+        __threadfence();
+        red_release_gpu_add(bar, 1u);
+        int ok = 1;
+        const unsigned long long t0 = global_ns();
+        uint32_t spins = 0;
+        for (;;) {
+            const uint32_t v = ld_acquire_gpu(bar);
+            if ((int32_t)(v - target) >= 0)
+                break;
+            if ((++spins & 63u) == 0u) {
+                if (*(volatile uint32_t *)err != 0u) {
+                    ok = 0;
+                    break;
+                }
+                if (global_ns() - t0 > kBarrierBudgetNs) {
+                    atomicOr(err, ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+            __nanosleep(32);
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+} // namespace hadga

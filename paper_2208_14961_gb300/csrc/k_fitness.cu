@@ -1,0 +1,368 @@
+// k_fitness.cu -- a2, batched column Gram G = Q^T Q and the fitness reduced
+// from its off-diagonal entries (Sec. 3.2, Eq. (3)-(5); Sec. 4.2, Eq. (8)-(9)).
+//
+// All paths are exact integer computations:
+//  * POPC  -- bit storage: G_ij = m - 2 popc(b_i ^ b_j), where b_j holds the
+//             -1 rows of column j.  m <= 32: one thread per matrix with the
+//             columns in registers; larger m: one warp per matrix, columns
+//             staged in shared memory, lane a owning columns a, a + 32, ...
+//  * POPC on int8 storage -- one warp per matrix; the sign bits of 32 rows
+//             become one column word per __ballot_sync, then as above.
+//  * INT32 -- int8 storage, CUDA-core 4-way byte dot products (__dp4a) on a
+//             transposed copy in shared memory.
+//  * IMMA  -- int8 storage, warp-level mma.sync m16n8k32 s8 x s8 -> s32 on
+//             the same transposed copy (both Gram operands read Q^T with the
+//             row index contiguous).
+// The pairs i < j of a warp's matrix are enumerated without a table: lane
+// a pairs column a with (a + s) mod m for s = 1 .. m/2, the s = m/2 pair only
+// when a < m/2, which visits each unordered pair exactly once.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace hadga {
+
+// ---------------------------------------------------------------------------
+// POPC, bit storage, m <= 32: one thread per matrix
+// ---------------------------------------------------------------------------
+template <int M, int KIND>
+__global__ void __launch_bounds__(128) k_fit_bits_thread(const uint32_t *__restrict__ pop, int64_t first,
+                                                         int64_t count, uint32_t *__restrict__ fit)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count)
+        return;
+    const int64_t q = first + t;
+    const uint4 *src = reinterpret_cast<const uint4 *>(pop + (size_t)q * M);
+    uint32_t c[M];
+#pragma unroll
+    for (int v = 0; v < M / 4; ++v) {
+        const uint4 x = __ldg(src + v);
+        c[4 * v + 0] = x.x;
+        c[4 * v + 1] = x.y;
+        c[4 * v + 2] = x.z;
+        c[4 * v + 3] = x.w;
+    }
+    uint32_t acc = 0;
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+#pragma unroll
+        for (int j = i + 1; j < M; ++j)
+            acc += fit_term<KIND>(M - 2 * __popc(c[i] ^ c[j]));
+    }
+    fit[q] = fit_finish<KIND>(acc);
+}
+
+// ---------------------------------------------------------------------------
+// Warp-level fitness of columns staged in shared memory (W words / column)
+// ---------------------------------------------------------------------------
+template <int W, int KIND>
+__device__ __forceinline__ uint32_t warp_fitness_cols(const uint32_t *cols, int m, int lane)
+{
+    uint32_t acc = 0;
+    const int half = m >> 1;
+    for (int a = lane; a < m; a += 32) {
+        uint32_t ca[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w)
+            ca[w] = cols[a * W + w];
+        const int smax = a < half ? half : half - 1;
+        int b = a;
+        for (int s = 1; s <= smax; ++s) {
+            b = (b + 1 == m) ? 0 : b + 1;
+            int d = 0;
+#pragma unroll
+            for (int w = 0; w < W; ++w)
+                d += __popc(ca[w] ^ cols[b * W + w]);
+            acc += fit_term<KIND>(m - 2 * d);
+        }
+    }
+    return fit_finish<KIND>(warp_sum(acc));
+}
+
+template <int W, int KIND>
+__global__ void __launch_bounds__(256) k_fit_bits_warp(const uint32_t *__restrict__ pop, int m, int64_t first,
+                                                       int64_t count, uint32_t *__restrict__ fit)
+{
+    extern __shared__ uint32_t s_cols[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint32_t *cols = s_cols + (size_t)wib * m * W;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int words = m * W;
+    for (int64_t q = first + gw; q < first + count; q += nw) {
+        const uint32_t *src = pop + (size_t)q * words;
+        for (int e = lane; e < words; e += 32)
+            cols[e] = __ldg(src + e);
+        __syncwarp();
+        const uint32_t f = warp_fitness_cols<W, KIND>(cols, m, lane);
+        if (lane == 0)
+            fit[q] = f;
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// POPC on int8 storage: sign bits -> column words by ballot
+// ---------------------------------------------------------------------------
+// Builds the W-word bit columns of an int8 row-major matrix in `cols`.
+__device__ __forceinline__ void int8_to_cols(const int8_t *Q, int m, int W, uint32_t *cols, int lane)
+{
+    for (int rg = 0; rg < W; ++rg) {
+        const int r = rg * 32 + lane;
+        const uint32_t *row = reinterpret_cast<const uint32_t *>(Q + (size_t)r * m);
+        for (int cw = 0; cw < (m >> 2); ++cw) {
+            const uint32_t x = r < m ? __ldg(row + cw) : 0u;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, (x >> (8 * k + 7)) & 1u);
+                const int j = 4 * cw + k;
+                if (lane == (j & 31))
+                    cols[j * W + rg] = bal;
+            }
+        }
+    }
+}
+
+template <int W, int KIND>
+__global__ void __launch_bounds__(256) k_fit_int8_popc(const int8_t *__restrict__ pop, int m, int64_t first,
+                                                       int64_t count, uint32_t *__restrict__ fit)
+{
+    extern __shared__ uint32_t s_cols[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint32_t *cols = s_cols + (size_t)wib * m * W;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t q = first + gw; q < first + count; q += nw) {
+        int8_to_cols(pop + (size_t)q * m * m, m, W, cols, lane);
+        __syncwarp();
+        const uint32_t f = warp_fitness_cols<W, KIND>(cols, m, lane);
+        if (lane == 0)
+            fit[q] = f;
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Transposed int8 copy in shared memory: T[j][r] = Q[r][j], row stride
+// `ts` bytes (kpad + 16, kpad = m rounded up to 32; padding is zero).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void int8_transpose_to_smem(const int8_t *Q, int m, int mpad, int kpad, int ts,
+                                                       int8_t *T, int lane)
+{
+    // zero the whole tile (padding rows / columns must contribute nothing)
+    uint32_t *T32 = reinterpret_cast<uint32_t *>(T);
+    for (int e = lane; e < (mpad * ts) >> 2; e += 32)
+        T32[e] = 0u;
+    __syncwarp();
+    const int words = (m * m) >> 2;
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(Q);
+    for (int e = lane; e < words; e += 32) {
+        const uint32_t x = __ldg(src + e);
+        const int r = (4 * e) / m, j0 = (4 * e) % m;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            T[(j0 + k) * ts + r] = (int8_t)(x >> (8 * k));
+    }
+    (void)kpad;
+    __syncwarp();
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(128) k_fit_int8_dp4a(const int8_t *__restrict__ pop, int m, int64_t first,
+                                                       int64_t count, uint32_t *__restrict__ fit)
+{
+    extern __shared__ __align__(16) int8_t s_t[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int kpad = (m + 31) & ~31, mpad = (m + 15) & ~15, ts = kpad + 16;
+    int8_t *T = s_t + (size_t)wib * mpad * ts;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int half = m >> 1, kw = m >> 2;
+    for (int64_t q = first + gw; q < first + count; q += nw) {
+        int8_transpose_to_smem(pop + (size_t)q * m * m, m, mpad, kpad, ts, T, lane);
+        uint32_t acc = 0;
+        for (int a = lane; a < m; a += 32) {
+            const int *ra = reinterpret_cast<const int *>(T + a * ts);
+            const int smax = a < half ? half : half - 1;
+            int b = a;
+            for (int s = 1; s <= smax; ++s) {
+                b = (b + 1 == m) ? 0 : b + 1;
+                const int *rb = reinterpret_cast<const int *>(T + b * ts);
+                int g = 0;
+                for (int k = 0; k < kw; ++k)
+                    g = __dp4a(ra[k], rb[k], g);
+                acc += fit_term<KIND>(g);
+            }
+        }
+        const uint32_t f = fit_finish<KIND>(warp_sum(acc));
+        if (lane == 0)
+            fit[q] = f;
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// IMMA: mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32
+// A (16x32, row) = rows i0.. of T, B (32x8, col) = rows j0.. of T: both read
+// 4 consecutive k bytes of one T row per register.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mma_s8_16832(int (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
+{
+    asm volatile("mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 "
+                 "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                 : "+r"(d[0]), "+r"(d[1]), "+r"(d[2]), "+r"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(128) k_fit_int8_imma(const int8_t *__restrict__ pop, int m, int64_t first,
+                                                       int64_t count, uint32_t *__restrict__ fit)
+{
+    extern __shared__ __align__(16) int8_t s_t[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int kpad = (m + 31) & ~31, mpad = (m + 15) & ~15, ts = kpad + 16;
+    int8_t *T = s_t + (size_t)wib * mpad * ts;
+    const int grp = lane >> 2, tig = lane & 3;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t q = first + gw; q < first + count; q += nw) {
+        int8_transpose_to_smem(pop + (size_t)q * m * m, m, mpad, kpad, ts, T, lane);
+        uint32_t acc = 0;
+        for (int i0 = 0; i0 < mpad; i0 += 16) {
+            // only column tiles that reach above the diagonal of this row tile
+            for (int j0 = i0 & ~7; j0 < mpad; j0 += 8) {
+                int d[4] = {0, 0, 0, 0};
+                for (int k0 = 0; k0 < kpad; k0 += 32) {
+                    uint32_t a[4], b[2];
+                    const int8_t *ta = T + (i0 + grp) * ts + k0 + tig * 4;
+                    a[0] = *reinterpret_cast<const uint32_t *>(ta);
+                    a[1] = *reinterpret_cast<const uint32_t *>(ta + 8 * ts);
+                    a[2] = *reinterpret_cast<const uint32_t *>(ta + 16);
+                    a[3] = *reinterpret_cast<const uint32_t *>(ta + 8 * ts + 16);
+                    const int8_t *tb = T + (j0 + grp) * ts + k0 + tig * 4;
+                    b[0] = *reinterpret_cast<const uint32_t *>(tb);
+                    b[1] = *reinterpret_cast<const uint32_t *>(tb + 16);
+                    mma_s8_16832(d, a, b);
+                }
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int i = i0 + grp + ((e >> 1) << 3);
+                    const int j = j0 + tig * 2 + (e & 1);
+                    if (i < j && j < m)
+                        acc += fit_term<KIND>(d[e]);
+                }
+            }
+        }
+        const uint32_t f = fit_finish<KIND>(warp_sum(acc));
+        if (lane == 0)
+            fit[q] = f;
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Dispatch
+// ---------------------------------------------------------------------------
+bool fitness_path_supported(int storage, int m, int path)
+{
+    if (path == 5)
+        return storage == ST_BITS || storage == ST_INT8;
+    if (path == 1 || path == 2)
+        return storage == ST_INT8;
+    return false;
+}
+
+static int grid_for_warps(int64_t count, int warps_per_block)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = (count + warps_per_block - 1) / warps_per_block;
+    const int64_t cap = (int64_t)(sms > 0 ? sms : 148) * 64;
+    return (int)(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+template <int KIND>
+static cudaError_t fitness_kind(const void *pop, int storage, int m, int64_t first, int64_t count, int path,
+                                uint32_t *fit, cudaStream_t s)
+{
+    const int W = words_per_col(m);
+    if (path == 5 && storage == ST_BITS && m <= 32) {
+        const int bs = 128;
+        const unsigned grid = (unsigned)((count + bs - 1) / bs);
+        const uint32_t *p = (const uint32_t *)pop;
+        switch (m) {
+#define HADGA_FT(M)                                                                                         \
+    case M:                                                                                                 \
+        k_fit_bits_thread<M, KIND><<<grid, bs, 0, s>>>(p, first, count, fit);                               \
+        break;
+            HADGA_FT(4) HADGA_FT(8) HADGA_FT(12) HADGA_FT(16) HADGA_FT(20) HADGA_FT(24) HADGA_FT(28) HADGA_FT(32)
+#undef HADGA_FT
+        default:
+            return cudaErrorInvalidValue;
+        }
+        note_launches(1);
+        return cudaGetLastError();
+    }
+    if (path == 5) {
+        const int wpb = 8;
+        const size_t smem = (size_t)wpb * m * W * 4;  // at most 64 KiB (m = 256)
+        const int grid = grid_for_warps(count, wpb);
+        switch (W) {
+#define HADGA_FW(WW)                                                                                        \
+    case WW:                                                                                                \
+        if (storage == ST_BITS) {                                                                           \
+            cudaFuncSetAttribute(k_fit_bits_warp<WW, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                                 (int)smem);                                                                \
+            k_fit_bits_warp<WW, KIND><<<grid, wpb * 32, smem, s>>>((const uint32_t *)pop, m, first, count,  \
+                                                                  fit);                                     \
+        } else {                                                                                            \
+            cudaFuncSetAttribute(k_fit_int8_popc<WW, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                                 (int)smem);                                                                \
+            k_fit_int8_popc<WW, KIND><<<grid, wpb * 32, smem, s>>>((const int8_t *)pop, m, first, count,    \
+                                                                  fit);                                     \
+        }                                                                                                   \
+        break;
+            HADGA_FW(1) HADGA_FW(2) HADGA_FW(3) HADGA_FW(4) HADGA_FW(5) HADGA_FW(6) HADGA_FW(7) HADGA_FW(8)
+#undef HADGA_FW
+        default:
+            return cudaErrorInvalidValue;
+        }
+        note_launches(1);
+        return cudaGetLastError();
+    }
+    // INT32 / IMMA on int8
+    const int kpad = (m + 31) & ~31, mpad = (m + 15) & ~15, ts = kpad + 16;
+    const size_t per_warp = (size_t)mpad * ts;
+    int wpb = 4;
+    while (wpb > 1 && per_warp * wpb > 96 * 1024)
+        wpb >>= 1;
+    const size_t smem = per_warp * wpb;
+    const int grid = grid_for_warps(count, wpb);
+    if (path == 1) {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(k_fit_int8_dp4a<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_fit_int8_dp4a<KIND><<<grid, wpb * 32, smem, s>>>((const int8_t *)pop, m, first, count, fit);
+    } else {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(k_fit_int8_imma<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_fit_int8_imma<KIND><<<grid, wpb * 32, smem, s>>>((const int8_t *)pop, m, first, count, fit);
+    }
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fitness(const void *pop, int storage, int m, int64_t first, int64_t count, int kind, int path,
+                           uint32_t *fit, cudaStream_t s)
+{
+    if (count <= 0)
+        return cudaSuccess;
+    switch (kind) {
+    case FIT_SQ: return fitness_kind<FIT_SQ>(pop, storage, m, first, count, path, fit, s);
+    case FIT_ABS: return fitness_kind<FIT_ABS>(pop, storage, m, first, count, path, fit, s);
+    case FIT_NNZ: return fitness_kind<FIT_NNZ>(pop, storage, m, first, count, path, fit, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+} // namespace hadga

@@ -1,0 +1,307 @@
+"""Thin ctypes binding of libhadga (include/hadga.h).
+
+Argument marshalling only: every step of the genetic algorithm runs in the
+CUDA kernels of ``libhadga.so``.  Device buffers are torch tensors (device
+memory and streams are the only things torch provides here).  There is no
+CPU fallback: importing this module without a built library, or calling it
+without a CUDA device, raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhadga.so")
+
+GA_OK, GA_EINVAL, GA_ENOMEM, GA_ECUDA, GA_ETIMEOUT, GA_EUNSUPPORTED = range(6)
+FIT_SQ, FIT_ABS, FIT_NNZ = 0, 1, 2
+STORE_INT8, STORE_BITS, STORE_E4M3, STORE_BF16 = 0, 1, 2, 3
+PATH_AUTO, PATH_INT32, PATH_IMMA, PATH_FP8, PATH_BF16, PATH_POPC = range(6)
+
+_STATUS_NAMES = {0: "GA_OK", 1: "GA_EINVAL", 2: "GA_ENOMEM", 3: "GA_ECUDA", 4: "GA_ETIMEOUT",
+                 5: "GA_EUNSUPPORTED"}
+
+
+class GAError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class ga_config(ctypes.Structure):
+    _fields_ = [
+        ("m", ctypes.c_int32),
+        ("NC", ctypes.c_int32),
+        ("N", ctypes.c_int64),
+        ("seed", ctypes.c_uint32),
+        ("pop_id", ctypes.c_uint32),
+        ("NR", ctypes.c_int32),
+        ("fitness", ctypes.c_int32),
+        ("storage", ctypes.c_int32),
+        ("path", ctypes.c_int32),
+        ("traj_cap", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
+# name -> (restype, argtypes); the full set of symbols include/hadga.h declares
+_vp, _i32, _i64, _u32, _sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_size_t
+SIGNATURES = {
+    "ga_version": (_i32, []),
+    "ga_storage_bytes": (_sz, [_i32, _i32]),
+    "ga_create": (_i32, [ctypes.POINTER(ga_config), _vp, _vp, _vp, ctypes.POINTER(_vp)]),
+    "ga_destroy": (_i32, [_vp]),
+    "ga_init_population": (_i32, [_vp]),
+    "ga_fitness": (_i32, [_vp, _i64, _i64]),
+    "ga_select": (_i32, [_vp]),
+    "ga_crossover": (_i32, [_vp]),
+    "ga_mutate": (_i32, [_vp]),
+    "ga_record_best": (_i32, [_vp]),
+    "ga_step_plain": (_i32, [_vp, _i32]),
+    "ga_step": (_i32, [_vp, _i32, _i32, ctypes.POINTER(_i32)]),
+    "ga_step_multi": (_i32, [ctypes.POINTER(_vp), _i32, _i32]),
+    "ga_step_is_fused": (_i32, [_vp]),
+    "ga_best": (_i32, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_u32)]),
+    "ga_trajectory": (_i32, [_vp, _vp, _vp, _i32, ctypes.POINTER(_i32)]),
+    "ga_generation": (_i32, [_vp, ctypes.POINTER(_u32)]),
+    "ga_set_generation": (_i32, [_vp, _u32]),
+    "ga_sync": (_i32, [_vp]),
+    "ga_set_slot": (_i32, [_vp, _i64, _vp]),
+    "ga_get_slot": (_i32, [_vp, _i64, _vp]),
+    "ga_last_error": (ctypes.c_char_p, [_vp]),
+    "ga_kernel_launches": (ctypes.c_uint64, []),
+    "ga_profile": (_i32, [_vp, _i32]),
+    "ga_profile_read": (_i32, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                                ctypes.POINTER(_i32)]),
+    "ga_init_batch": (_i32, [_vp, _i32, _i32, _i64, _u32, _u32, _vp]),
+    "ga_fitness_batch": (_i32, [_vp, _i32, _i32, _i64, _i32, _i32, _vp, _vp]),
+    "ga_convert": (_i32, [_vp, _i32, _vp, _i32, _i32, _i64, _vp]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads libhadga.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libhadga.so not built at {path}; run paper_2208_14961_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def last_error(ctx=None) -> str:
+    msg = load().ga_last_error(ctx)
+    return msg.decode() if msg else ""
+
+
+def check(status: int, ctx=None) -> None:
+    if status != GA_OK:
+        raise GAError(status, last_error(ctx))
+
+
+def _ptr(t: torch.Tensor):
+    if not t.is_cuda:
+        raise ValueError("libhadga works on CUDA tensors only")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def kernel_launches() -> int:
+    return int(load().ga_kernel_launches())
+
+
+def storage_bytes(storage: int, m: int) -> int:
+    return int(load().ga_storage_bytes(storage, m))
+
+
+def storage_shape(storage: int, m: int, P: int):
+    """(shape, dtype) of a torch tensor holding P matrices in `storage`."""
+    if storage == STORE_INT8:
+        return (P, m, m), torch.int8
+    if storage == STORE_BITS:
+        return (P, m, (m + 31) // 32), torch.int32
+    if storage == STORE_E4M3:
+        return (P, m, m), torch.uint8
+    if storage == STORE_BF16:
+        return (P, m, m), torch.int16
+    raise ValueError(storage)
+
+
+def empty_population(storage: int, m: int, P: int, device="cuda") -> torch.Tensor:
+    shape, dt = storage_shape(storage, m, P)
+    return torch.empty(shape, dtype=dt, device=device)
+
+
+# ---------------------------------------------------------------------------
+# Stateless batch calls
+# ---------------------------------------------------------------------------
+def ga_init_batch(pop: torch.Tensor, storage: int, m: int, P: int, seed: int, pop_id: int = 0, stream=None):
+    check(load().ga_init_batch(_ptr(pop), storage, m, P, seed, pop_id, _stream(stream)))
+
+
+def ga_fitness_batch(pop: torch.Tensor, storage: int, m: int, P: int, kind: int, path: int,
+                     fit: torch.Tensor, stream=None):
+    check(load().ga_fitness_batch(_ptr(pop), storage, m, P, kind, path, _ptr(fit), _stream(stream)))
+
+
+def ga_convert(src: torch.Tensor, src_storage: int, dst: torch.Tensor, dst_storage: int, m: int, P: int,
+               stream=None):
+    check(load().ga_convert(_ptr(src), src_storage, _ptr(dst), dst_storage, m, P, _stream(stream)))
+
+
+# ---------------------------------------------------------------------------
+# Context
+# ---------------------------------------------------------------------------
+class Population:
+    """A GA context over torch-owned device buffers (population + fitness)."""
+
+    def __init__(self, m: int, N: int, seed: int = 0, pop_id: int = 0, NC: int = 1, NR: int = 1,
+                 fitness: int = FIT_SQ, storage: int = STORE_BITS, path: int = PATH_AUTO,
+                 traj_cap: int = 1024, device="cuda", stream=None):
+        lib = load()
+        self.m, self.N, self.P = m, N, 4 * N
+        self.storage = storage
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        self.pop = empty_population(storage, m, self.P, device)
+        self.fit = torch.zeros(self.P, dtype=torch.int32, device=device)
+        self.cfg = ga_config(m=m, NC=NC, N=N, seed=seed, pop_id=pop_id, NR=NR, fitness=fitness,
+                             storage=storage, path=path, traj_cap=traj_cap, reserved=0)
+        ctx = ctypes.c_void_p()
+        check(lib.ga_create(ctypes.byref(self.cfg), _ptr(self.pop), _ptr(self.fit),
+                            ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(ctx)))
+        self.ctx = ctx
+        self.traj_cap = traj_cap
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            load().ga_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, status):
+        check(status, self.ctx)
+
+    def init_population(self):
+        self._chk(load().ga_init_population(self.ctx))
+
+    def fitness(self, first: int = 0, count: int | None = None):
+        self._chk(load().ga_fitness(self.ctx, first, self.P - first if count is None else count))
+
+    def select(self):
+        self._chk(load().ga_select(self.ctx))
+
+    def crossover(self):
+        self._chk(load().ga_crossover(self.ctx))
+
+    def mutate(self):
+        self._chk(load().ga_mutate(self.ctx))
+
+    def record_best(self):
+        self._chk(load().ga_record_best(self.ctx))
+
+    def step_plain(self, generations: int):
+        self._chk(load().ga_step_plain(self.ctx, generations))
+
+    def step(self, generations: int, stop_at_zero: bool = False, want_done: bool = False):
+        done = ctypes.c_int32(0)
+        self._chk(load().ga_step(self.ctx, generations, int(stop_at_zero),
+                                 ctypes.byref(done) if (want_done or stop_at_zero) else None))
+        return int(done.value)
+
+    def is_fused(self) -> bool:
+        return bool(load().ga_step_is_fused(self.ctx))
+
+    def profile(self, enable: bool):
+        self._chk(load().ga_profile(self.ctx, int(enable)))
+
+    def profile_read(self):
+        a, b, n = ctypes.c_float(), ctypes.c_float(), ctypes.c_int32()
+        self._chk(load().ga_profile_read(self.ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)))
+        return float(a.value), float(b.value), int(n.value)
+
+    def best(self):
+        s, f = ctypes.c_int64(), ctypes.c_uint32()
+        self._chk(load().ga_best(self.ctx, ctypes.byref(s), ctypes.byref(f)))
+        return int(s.value), int(f.value)
+
+    def trajectory(self):
+        import numpy as np
+        fit = np.zeros(self.traj_cap, dtype=np.uint32)
+        slot = np.zeros(self.traj_cap, dtype=np.int64)
+        n = ctypes.c_int32()
+        self._chk(load().ga_trajectory(self.ctx, fit.ctypes.data_as(ctypes.c_void_p),
+                                       slot.ctypes.data_as(ctypes.c_void_p), self.traj_cap, ctypes.byref(n)))
+        return fit[:n.value], slot[:n.value]
+
+    def generation(self) -> int:
+        g = ctypes.c_uint32()
+        self._chk(load().ga_generation(self.ctx, ctypes.byref(g)))
+        return int(g.value)
+
+    def set_generation(self, g: int):
+        self._chk(load().ga_set_generation(self.ctx, g))
+
+    def sync(self):
+        self._chk(load().ga_sync(self.ctx))
+
+    def set_slot(self, slot: int, matrix):
+        import numpy as np
+        a = np.ascontiguousarray(matrix, dtype=np.int8)
+        assert a.shape == (self.m, self.m)
+        self._chk(load().ga_set_slot(self.ctx, slot, a.ctypes.data_as(ctypes.c_void_p)))
+
+    def get_slot(self, slot: int):
+        import numpy as np
+        a = np.zeros((self.m, self.m), dtype=np.int8)
+        self._chk(load().ga_get_slot(self.ctx, slot, a.ctypes.data_as(ctypes.c_void_p)))
+        return a
+
+    def as_int8(self):
+        """The whole population as a host int8 array [P, m, m] (via the GPU)."""
+        if self.storage == STORE_INT8:
+            return self.pop.cpu().numpy()
+        out = empty_population(STORE_INT8, self.m, self.P, self.pop.device)
+        ga_convert(self.pop, self.storage, out, STORE_INT8, self.m, self.P, self.stream)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+
+    def load_int8(self, host_pop):
+        """Replaces the population by a host int8 array [P, m, m]."""
+        t = torch.as_tensor(host_pop, dtype=torch.int8).to(self.pop.device).contiguous()
+        if self.storage == STORE_INT8:
+            self.pop.copy_(t)
+        else:
+            ga_convert(t, STORE_INT8, self.pop, self.storage, self.m, self.P, self.stream)
+        torch.cuda.synchronize()
+
+    def fitness_host(self):
+        import numpy as np
+        torch.cuda.synchronize()
+        return self.fit.cpu().numpy().view(np.uint32).astype(np.uint64)
+
+
+def step_multi(pops, generations: int):
+    arr = (ctypes.c_void_p * len(pops))(*[p.ctx for p in pops])
+    check(load().ga_step_multi(arr, len(pops), generations))
