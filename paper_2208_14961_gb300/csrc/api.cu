@@ -92,6 +92,13 @@ ga_status cuda_check(ga_ctx *c, cudaError_t e, const char *what)
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
+void drop_events(std::vector<cudaEvent_t> &v)
+{
+    for (cudaEvent_t e : v)
+        cudaEventDestroy(e);
+    v.clear();
+}
+
 ga_status check_storage_m(ga_ctx *c, int32_t storage, int32_t m)
 {
     if (m < 4 || m > kMaxM || (m & 3))
@@ -399,13 +406,6 @@ ga_status ga_step_multi(ga_ctx *const *ctxs, int32_t n, int32_t generations)
             return set_error(nullptr, st, "population %d: %s", i, ga_last_error(ctxs[i]));
     }
     return GA_OK;
-}
-
-static void drop_events(std::vector<cudaEvent_t> &v)
-{
-    for (cudaEvent_t e : v)
-        cudaEventDestroy(e);
-    v.clear();
 }
 
 ga_status ga_profile(ga_ctx *ctx, int32_t enable)
