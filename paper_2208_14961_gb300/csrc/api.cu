@@ -1,5 +1,6 @@
 // api.cu -- the extern "C" entry points of libhadga (declared, with the
 // passages of the paper they implement, in include/hadga.h).
+#include <algorithm>
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
@@ -47,11 +48,11 @@ struct ga_ctx {
     uint32_t *err = nullptr;
     // fused path
     uint32_t *bits[2] = {nullptr, nullptr};  // bit-storage ping-pong (int8 contexts)
-    uint32_t *ffit[2] = {nullptr, nullptr};
-    uint32_t *fhist[3] = {nullptr, nullptr, nullptr};
-    uint32_t *fmisc = nullptr;                // orv[2], cap[2], bar, done
+    uint32_t *ffit = nullptr;                 // second fitness buffer
+    uint32_t *fstate = nullptr;               // kFusedStateWords selection state
+    uint32_t *fmisc = nullptr;                // [0] grid-barrier counter, [1] generations done
     unsigned long long *ftmask = nullptr;
-    uint32_t *fperm = nullptr;                // [chunk][2N]
+    uint32_t *fperm = nullptr;                // [chunk][2N] survivor orders
     int fused_ok = 0;
 
     // opt-in event profile of ga_step's kernels
@@ -204,10 +205,8 @@ ga_status ga_create(const ga_config *cfg, void *pop_dev, uint32_t *fit_dev, void
             parts.push_back({(void **)&c->bits[0], bits_bytes});
             parts.push_back({(void **)&c->bits[1], bits_bytes});
         }
-        parts.push_back({(void **)&c->ffit[0], (size_t)P * 4u});
-        parts.push_back({(void **)&c->ffit[1], (size_t)P * 4u});
-        for (int i = 0; i < 3; ++i)
-            parts.push_back({(void **)&c->fhist[i], 4096u * 4u});
+        parts.push_back({(void **)&c->ffit, (size_t)P * 4u});
+        parts.push_back({(void **)&c->fstate, kFusedStateWords * 4u});
         parts.push_back({(void **)&c->fmisc, 64u * 4u});
         parts.push_back({(void **)&c->ftmask, (size_t)tiles * 8u});
         parts.push_back({(void **)&c->fperm, (size_t)kChunk * n_keep * 4u});
@@ -241,7 +240,7 @@ ga_status ga_create(const ga_config *cfg, void *pop_dev, uint32_t *fit_dev, void
         delete c;
         return set_error(nullptr, GA_ECUDA, "workspace initialisation failed: %s", cudaGetErrorString(e));
     }
-    c->fused_ok = fused_fit ? 1 : 0;
+    c->fused_ok = (fused_fit && c->m <= kFusedMaxM && (uint64_t)tiles <= kFusedMaxTiles) ? 1 : 0;
     *out = c;
     return GA_OK;
 }
@@ -370,6 +369,153 @@ ga_status ga_step_plain(ga_ctx *ctx, int32_t generations)
 
 int32_t ga_step_is_fused(const ga_ctx *ctx) { return ctx ? ctx->fused_ok : 0; }
 
+// Runs `generations` generations of ctxs[0..n) with the persistent kernel,
+// in chunks of kChunk generations (survivor orders of a chunk first).
+static ga_status fused_run(ga_ctx *const *ctxs, int n, int32_t generations, int stop_at_zero, int32_t *done_out)
+{
+    ga_ctx *c0 = ctxs[0];
+    FusedParams prm;
+    memset(&prm, 0, sizeof(prm));
+    prm.npop = n;
+    uint32_t tiles = 0, tslots = 0, wpairs = 0;
+    int max_words = 0;
+    for (int i = 0; i < n; ++i) {
+        ga_ctx *c = ctxs[i];
+        FusedPop &p = prm.p[i];
+        const bool int8 = c->cfg.storage == GA_STORE_INT8;
+        p.pop[0] = int8 ? c->bits[0] : (uint32_t *)c->pop;
+        p.pop[1] = int8 ? c->bits[1] : (uint32_t *)c->scratch_pop;
+        p.fit[0] = c->fit;
+        p.fit[1] = c->ffit;
+        p.state = c->fstate;
+        p.tmask = c->ftmask;
+        p.perm = c->fperm;
+        p.traj = c->traj;
+        p.m = c->m;
+        p.W = c->W;
+        p.NC = c->cfg.NC;
+        p.NR = c->cfg.NR;
+        p.kind = c->cfg.fitness;
+        p.traj_cap = c->cfg.traj_cap;
+        p.N = c->N;
+        p.seed = c->cfg.seed;
+        p.pop_id = c->cfg.pop_id;
+        p.tile_base = tiles;
+        p.ntiles = (uint32_t)((c->P + 31) / 32);
+        tiles += p.ntiles;
+        if (c->m <= 32) {
+            p.work_base = tslots;
+            tslots += (uint32_t)((2 * c->N + 31) / 32 * 32);
+        } else {
+            p.work_base = wpairs;
+            wpairs += (uint32_t)c->N;
+            max_words = std::max(max_words, 3 * c->m * c->W);
+        }
+        if (int8) {
+            cudaError_t e = launch_convert(c->pop, GA_STORE_INT8, c->bits[0], GA_STORE_BITS, c->m, c->P, c0->stream);
+            if (e != cudaSuccess)
+                return cuda_check(c0, e, "convert to bit storage");
+        }
+    }
+    if (tiles > kFusedMaxTiles)
+        return set_error(c0, GA_EUNSUPPORTED, "populations too large for one persistent launch");
+    prm.total_tiles = tiles;
+    prm.thread_slots = tslots;
+    prm.warp_pairs = wpairs;
+    prm.warp_buf_words = max_words;
+    prm.stop_at_zero = stop_at_zero;
+    prm.bar = c0->fmisc;
+    prm.done = (int32_t *)(c0->fmisc + 1);
+    prm.err = c0->err;
+    const size_t smem = fused_smem_bytes(prm);
+    int grid = 0;
+    cudaError_t e = fused_grid(smem, &grid);
+    if (e != cudaSuccess)
+        return cuda_check(c0, e, "fused kernel occupancy");
+
+    int cur = 0;
+    int32_t total_done = 0;
+    for (int32_t left = generations; left > 0;) {
+        const int chunk = left < kChunk ? left : kChunk;
+        for (int i = 0; i < n; ++i) {
+            ga_ctx *c = ctxs[i];
+            cudaEvent_t ev[2] = {nullptr, nullptr};
+            if (c->profiling) {
+                cudaEventCreate(&ev[0]);
+                cudaEventCreate(&ev[1]);
+                cudaEventRecord(ev[0], c0->stream);
+            }
+            e = launch_perm_table((uint32_t)(2 * c->N), c->cfg.seed, c->cfg.pop_id, c->gen + 1u, chunk, c->fperm,
+                                  c0->stream);
+            if (c->profiling) {
+                cudaEventRecord(ev[1], c0->stream);
+                c->prof_perm.push_back(ev[0]);
+                c->prof_perm.push_back(ev[1]);
+            }
+            if (e == cudaSuccess)
+                e = cudaMemsetAsync(c->fstate, 0, kFusedStateWords * 4u, c0->stream);
+            if (e != cudaSuccess)
+                return cuda_check(c0, e, "survivor orders");
+        }
+        e = cudaMemsetAsync(c0->fmisc, 0, 2 * sizeof(uint32_t), c0->stream);
+        if (e != cudaSuccess)
+            return cuda_check(c0, e, "barrier reset");
+        prm.gen0 = c0->gen;
+        prm.ngen = chunk;
+        prm.src = cur;
+        cudaEvent_t ev[2] = {nullptr, nullptr};
+        if (c0->profiling) {
+            cudaEventCreate(&ev[0]);
+            cudaEventCreate(&ev[1]);
+            cudaEventRecord(ev[0], c0->stream);
+        }
+        e = launch_fused(prm, grid, smem, c0->stream);
+        if (c0->profiling) {
+            cudaEventRecord(ev[1], c0->stream);
+            c0->prof_fused.push_back(ev[0]);
+            c0->prof_fused.push_back(ev[1]);
+        }
+        if (e != cudaSuccess)
+            return cuda_check(c0, e, "persistent generation kernel");
+        int32_t ran = chunk;
+        if (stop_at_zero) {
+            e = cudaMemcpyAsync(&ran, c0->fmisc + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, c0->stream);
+            if (e == cudaSuccess)
+                e = cudaStreamSynchronize(c0->stream);
+            if (e != cudaSuccess)
+                return cuda_check(c0, e, "generations done");
+            uint32_t err = 0;
+            cudaMemcpy(&err, c0->err, 4, cudaMemcpyDeviceToHost);
+            if (err)
+                return ga_sync(c0);
+        }
+        for (int i = 0; i < n; ++i)
+            ctxs[i]->gen += (uint32_t)ran;
+        total_done += ran;
+        cur ^= (ran & 1);
+        left -= chunk;
+        if (ran < chunk)
+            break;
+    }
+    for (int i = 0; i < n; ++i) {
+        ga_ctx *c = ctxs[i];
+        const bool int8 = c->cfg.storage == GA_STORE_INT8;
+        if (int8) {
+            e = launch_convert(c->bits[cur], GA_STORE_BITS, c->pop, GA_STORE_INT8, c->m, c->P, c0->stream);
+        } else if (cur == 1) {
+            e = cudaMemcpyAsync(c->pop, c->scratch_pop, (size_t)c->P * c->mat_bytes, cudaMemcpyDeviceToDevice,
+                                c0->stream);
+        }
+        if (e == cudaSuccess && cur == 1)
+            e = cudaMemcpyAsync(c->fit, c->ffit, (size_t)c->P * 4u, cudaMemcpyDeviceToDevice, c0->stream);
+        if (e != cudaSuccess)
+            return cuda_check(c0, e, "copy-back of the final population");
+    }
+    if (done_out)
+        *done_out = total_done;
+    return GA_OK;
+}
+
 ga_status ga_step(ga_ctx *ctx, int32_t generations, int32_t stop_at_zero, int32_t *done)
 {
     ga_status st = begin(ctx);
@@ -377,6 +523,16 @@ ga_status ga_step(ga_ctx *ctx, int32_t generations, int32_t stop_at_zero, int32_
         return st;
     if (generations < 0)
         return set_error(ctx, GA_EINVAL, "generations must be >= 0");
+    if (ctx->fused_ok) {
+        int32_t d = 0;
+        st = fused_run(&ctx, 1, generations, stop_at_zero, &d);
+        if (st == GA_OK && done) {
+            if ((st = ga_sync(ctx)) != GA_OK)
+                return st;
+            *done = d;
+        }
+        return st;
+    }
     int32_t n = 0;
     for (; n < generations;) {
         if ((st = ga_step_plain(ctx, 1)) != GA_OK)
@@ -400,8 +556,27 @@ ga_status ga_step_multi(ga_ctx *const *ctxs, int32_t n, int32_t generations)
 {
     if (!ctxs || n < 1)
         return set_error(nullptr, GA_EINVAL, "ctxs must hold n >= 1 contexts");
+    if (generations < 0)
+        return set_error(nullptr, GA_EINVAL, "generations must be >= 0");
+    bool fused = n <= kMaxPops;
     for (int32_t i = 0; i < n; ++i) {
-        ga_status st = ga_step(ctxs[i], generations, 0, nullptr);
+        if (!ctxs[i])
+            return set_error(nullptr, GA_EINVAL, "context %d is NULL", i);
+        if (ctxs[i]->stream != ctxs[0]->stream || ctxs[i]->device != ctxs[0]->device)
+            return set_error(nullptr, GA_EINVAL, "contexts must share stream and device");
+        fused = fused && ctxs[i]->fused_ok;
+    }
+    ga_status st = begin(ctxs[0]);
+    if (st != GA_OK)
+        return st;
+    if (fused) {
+        st = fused_run(ctxs, n, generations, 0, nullptr);
+        if (st != GA_OK)
+            return set_error(nullptr, st, "%s", ga_last_error(ctxs[0]));
+        return GA_OK;
+    }
+    for (int32_t i = 0; i < n; ++i) {
+        st = ga_step_plain(ctxs[i], generations);
         if (st != GA_OK)
             return set_error(nullptr, st, "population %d: %s", i, ga_last_error(ctxs[i]));
     }

@@ -182,6 +182,35 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *tmp, u
 }
 
 // ---------------------------------------------------------------------------
+// Warp-level fitness of one matrix whose bit columns (W words each) sit in
+// shared memory.  Lane a pairs column a with (a + s) mod m for s = 1..m/2,
+// the s = m/2 pair only when a < m/2, so each unordered pair is visited once.
+// ---------------------------------------------------------------------------
+template <int W, int KIND>
+__device__ __forceinline__ uint32_t warp_fitness_cols(const uint32_t *cols, int m, int lane)
+{
+    uint32_t acc = 0;
+    const int half = m >> 1;
+    for (int a = lane; a < m; a += 32) {
+        uint32_t ca[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w)
+            ca[w] = cols[a * W + w];
+        const int smax = a < half ? half : half - 1;
+        int b = a;
+        for (int s = 1; s <= smax; ++s) {
+            b = (b + 1 == m) ? 0 : b + 1;
+            int d = 0;
+#pragma unroll
+            for (int w = 0; w < W; ++w)
+                d += __popc(ca[w] ^ cols[b * W + w]);
+            acc += fit_term<KIND>(m - 2 * d);
+        }
+    }
+    return fit_finish<KIND>(warp_sum(acc));
+}
+
+// ---------------------------------------------------------------------------
 // Bounded waits
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned long long global_ns()

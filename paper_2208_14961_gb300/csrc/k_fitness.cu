@@ -52,33 +52,6 @@ __global__ void __launch_bounds__(128) k_fit_bits_thread(const uint32_t *__restr
     fit[q] = fit_finish<KIND>(acc);
 }
 
-// ---------------------------------------------------------------------------
-// Warp-level fitness of columns staged in shared memory (W words / column)
-// ---------------------------------------------------------------------------
-template <int W, int KIND>
-__device__ __forceinline__ uint32_t warp_fitness_cols(const uint32_t *cols, int m, int lane)
-{
-    uint32_t acc = 0;
-    const int half = m >> 1;
-    for (int a = lane; a < m; a += 32) {
-        uint32_t ca[W];
-#pragma unroll
-        for (int w = 0; w < W; ++w)
-            ca[w] = cols[a * W + w];
-        const int smax = a < half ? half : half - 1;
-        int b = a;
-        for (int s = 1; s <= smax; ++s) {
-            b = (b + 1 == m) ? 0 : b + 1;
-            int d = 0;
-#pragma unroll
-            for (int w = 0; w < W; ++w)
-                d += __popc(ca[w] ^ cols[b * W + w]);
-            acc += fit_term<KIND>(m - 2 * d);
-        }
-    }
-    return fit_finish<KIND>(warp_sum(acc));
-}
-
 template <int W, int KIND>
 __global__ void __launch_bounds__(256) k_fit_bits_warp(const uint32_t *__restrict__ pop, int m, int64_t first,
                                                        int64_t count, uint32_t *__restrict__ fit)

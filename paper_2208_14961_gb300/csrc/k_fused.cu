@@ -1,0 +1,722 @@
+// k_fused.cu -- the fused persistent generation kernel: every step of the
+// population step (a2-a8; Sec. 3, the enumerated GA loop; Sec. 6, the loop of
+// the listing) for one or more populations, generation after generation, in
+// one cooperative launch.  Results are bit-identical to the one-kernel-per-
+// operator path.
+//
+// Per generation g (all CTAs resident; two grid barriers):
+//  Phase A  select.  The selection histogram of the population entering g
+//           was filled by the previous generation's build phase (buckets
+//           f >> shift for f <= cap, cap = previous threshold, which bounds
+//           every survivor).  Each CTA scans it (one warp per population) to
+//           find the threshold T of the 2N smallest; a bucket is exact when
+//           its width 2^shift does not exceed 2^v, v = trailing zeros of the
+//           OR of all fitness values (all F are multiples of 2^v), otherwise
+//           extra refinement passes narrow it.  Warps then write, per tile of
+//           32 slots, ballot masks of F < T and F == T.
+//  Phase B  build.  Each CTA scans the tile masks into shared memory
+//           (survivors in slot order), then builds pairs: parents k, k+N are
+//           survivors number pi(k), pi(k+N) of the precomputed survivor order
+//           of generation g; crossover, mutation and fitness of both
+//           offspring run in registers (m <= 32: two threads per pair, one
+//           per offspring) or in shared memory (32 < m <= 128: a warp per
+//           pair); the new population goes to the other ping-pong buffer and
+//           the histogram, OR word and best key of generation g + 1 are
+//           accumulated with warp-aggregated atomics.
+// Data written inside the launch is read with ld.global.cg (L2) so no SM
+// can see a stale L1 line across generations.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace hadga {
+
+namespace {
+
+constexpr uint32_t FULL = 0xFFFFFFFFu;
+
+struct PopSel {
+    uint32_t cap, shift;  // histogram of the current generation: f >> shift for f <= cap
+    uint32_t v;           // every current F is a multiple of 2^v
+    uint32_t lo, need;    // candidate bucket [lo, lo + 2^sr) and survivors still to take there
+    uint32_t sr;          // width exponent of the candidate bucket
+    uint32_t exact;
+    uint32_t T, take;     // threshold and number of F == T survivors
+    uint32_t base;        // joint survivor count before the first tile of the population
+    uint32_t capn, shiftn;  // histogram parameters of the next generation
+};
+
+__device__ __forceinline__ uint32_t ldcg32(const uint32_t *p) { return __ldcg(p); }
+__device__ __forceinline__ unsigned long long ldcg64(const unsigned long long *p) { return __ldcg(p); }
+
+// smallest s with (cap >> s) < kHistR
+__device__ __forceinline__ uint32_t shift_for(uint32_t cap)
+{
+    const int bl = 32 - __clz(cap);
+    return bl > 12 ? (uint32_t)(bl - 12) : 0u;
+}
+
+__device__ __forceinline__ uint32_t ctz_or(uint32_t orv) { return orv ? (uint32_t)(__ffs(orv) - 1) : 31u; }
+
+__device__ __forceinline__ uint32_t *hist_of(const FusedPop &p, int parity) { return p.state + parity * kHistR; }
+__device__ __forceinline__ uint32_t *ref_of(const FusedPop &p, int level) { return p.state + (2 + level) * kHistR; }
+__device__ __forceinline__ uint32_t *stat_of(const FusedPop &p) { return p.state + 5 * kHistR; }
+
+// Whole warp: bucket b in [0, nb) of h where the running count first reaches
+// `need` (1 <= need <= total), and the count before it.
+__device__ void warp_find_bucket(const uint32_t *h, uint32_t nb, uint32_t need, uint32_t *err, uint32_t &b_out,
+                                 uint32_t &before_out)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t per = (nb + 31u) >> 5;
+    const uint32_t lo = (uint32_t)lane * per, hi = min(lo + per, nb);
+    uint32_t sum = 0;
+    for (uint32_t b = lo; b < hi; ++b)
+        sum += ldcg32(h + b);
+    const uint32_t incl = warp_incl_scan(sum, lane), excl = incl - sum;
+    const uint32_t bal = __ballot_sync(FULL, excl < need && need <= incl);
+    uint32_t bres = 0, before = 0;
+    if (bal == 0u) {
+        if (lane == 0)
+            atomicOr(err, ERR_INTERNAL);
+        b_out = 0;
+        before_out = 0;
+        return;
+    }
+    const int owner = __ffs(bal) - 1;
+    if (lane == owner) {
+        uint32_t run = excl;
+        bres = hi - 1;
+        for (uint32_t b = lo; b < hi; ++b) {
+            const uint32_t c = ldcg32(h + b);
+            if (run + c >= need) {
+                bres = b;
+                break;
+            }
+            run += c;
+        }
+        before = run;
+    }
+    b_out = __shfl_sync(FULL, bres, owner);
+    before_out = __shfl_sync(FULL, before, owner);
+}
+
+// Warp-aggregated histogram increment (all lanes call; ok selects the lanes
+// that add one to bucket key).
+__device__ __forceinline__ void warp_hist_add(uint32_t *h, bool ok, uint32_t key)
+{
+    const uint32_t k = ok ? key : 0xFFFFFFFFu;
+    const uint32_t peers = __match_any_sync(FULL, k);
+    const int lane = threadIdx.x & 31;
+    if (ok && (__ffs(peers) - 1) == lane)
+        atomicAdd(h + key, (uint32_t)__popc(peers));
+}
+
+__device__ __forceinline__ uint32_t warp_or(uint32_t v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v |= __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+__device__ __forceinline__ uint32_t warp_max(uint32_t v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = max(v, __shfl_xor_sync(FULL, v, o));
+    return v;
+}
+
+// Slot of survivor number d of a population: binary search over the joint
+// survivor prefix (shared memory), then a select-bit inside the tile.
+__device__ __forceinline__ uint32_t survivor_of(uint32_t d, const FusedPop &p, const PopSel &S, const uint32_t *smask,
+                                                const uint32_t *sbefore, uint32_t *err)
+{
+    const uint32_t tb = p.tile_base;
+    uint32_t lo = 0, hi = p.ntiles - 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (sbefore[tb + mid] - S.base <= d)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const uint32_t mask = smask[tb + lo];
+    const uint32_t r = d - (sbefore[tb + lo] - S.base);
+    const uint32_t P = (uint32_t)(4 * p.N);
+    if (r >= (uint32_t)__popc(mask)) {
+        atomicOr(err, ERR_INTERNAL);
+        return P - 1;
+    }
+    const uint32_t slot = lo * 32u + (uint32_t)nth_set_bit(mask, (int)r);
+    return slot < P ? slot : P - 1;
+}
+
+// Mutation draws of offspring o: NC columns, NR first rows, NR second rows.
+struct Draws {
+    uint32_t seed, pop_id, gen, o, block;
+    uint4 cur;
+    int used;
+    __device__ Draws(uint32_t s, uint32_t p, uint32_t g, uint32_t oo)
+        : seed(s), pop_id(p), gen(g), o(oo), block(0), cur(make_uint4(0, 0, 0, 0)), used(4) {}
+    __device__ __forceinline__ uint32_t next()
+    {
+        if (used == 4) {
+            cur = philox_block(seed, pop_id, OP_MUTATE, gen, o, 0u, block++);
+            used = 0;
+        }
+        return word_of(cur, used++);
+    }
+};
+
+template <int M, int KIND>
+__device__ __forceinline__ uint32_t fitness_regs(const uint32_t (&c)[M])
+{
+    uint32_t acc = 0;
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+#pragma unroll
+        for (int j = i + 1; j < M; ++j)
+            acc += fit_term<KIND>(M - 2 * __popc(c[i] ^ c[j]));
+    }
+    return fit_finish<KIND>(acc);
+}
+
+// ---------------------------------------------------------------------------
+// m <= 32: two threads per pair (lane pair 2j, 2j+1), thread `half` builds
+// offspring O_{1 + half}; its parent is P_1 (half 0) or P_2 (half 1).
+// ---------------------------------------------------------------------------
+template <int M>
+__device__ __forceinline__ void pair_thread(const FusedPop &p, const PopSel &S, int src, uint32_t gen, uint32_t tch,
+                                            uint32_t k, int half, bool valid, const uint32_t *smask,
+                                            const uint32_t *sbefore, uint32_t *err, uint32_t &f_par,
+                                            uint32_t &slot_par, uint32_t &f_child, uint32_t &slot_child)
+{
+    const uint32_t N = (uint32_t)p.N;
+    uint32_t s_mine = 0;
+    if (valid) {
+        const uint32_t d = __ldg(p.perm + (size_t)tch * 2u * N + k + (half ? N : 0u));
+        s_mine = survivor_of(d, p, S, smask, sbefore, err);
+    }
+    const uint32_t s_other = __shfl_xor_sync(FULL, s_mine, 1);
+    if (!valid)
+        return;
+    const uint32_t s1 = half ? s_other : s_mine, s2 = half ? s_mine : s_other;
+    const uint32_t *src_pop = p.pop[src];
+    uint32_t *dst_pop = p.pop[src ^ 1];
+    uint32_t p1[M], p2[M];
+    const uint4 *a = reinterpret_cast<const uint4 *>(src_pop + (size_t)s1 * M);
+    const uint4 *b = reinterpret_cast<const uint4 *>(src_pop + (size_t)s2 * M);
+#pragma unroll
+    for (int v = 0; v < M / 4; ++v) {
+        const uint4 x = __ldcg(a + v), y = __ldcg(b + v);
+        p1[4 * v] = x.x, p1[4 * v + 1] = x.y, p1[4 * v + 2] = x.z, p1[4 * v + 3] = x.w;
+        p2[4 * v] = y.x, p2[4 * v + 1] = y.y, p2[4 * v + 2] = y.z, p2[4 * v + 3] = y.w;
+    }
+    f_par = ldcg32(p.fit[src] + s_mine);
+    slot_par = half ? k + N : k;
+    {
+        uint4 *d = reinterpret_cast<uint4 *>(dst_pop + (size_t)slot_par * M);
+#pragma unroll
+        for (int v = 0; v < M / 4; ++v) {
+            const uint32_t *q = half ? p2 : p1;
+            d[v] = make_uint4(q[4 * v], q[4 * v + 1], q[4 * v + 2], q[4 * v + 3]);
+        }
+        p.fit[src ^ 1][slot_par] = f_par;
+    }
+    // crossover (Sec. 3.4): O1 = P1[:, :c] | P2[:, c:], O2 = P2[:, :c] | P1[:, c:]
+    const int c = cut_point(p.seed, p.pop_id, gen, k, M);
+    uint32_t o[M];
+#pragma unroll
+    for (int j = 0; j < M; ++j)
+        o[j] = ((j < c) != (half != 0)) ? p1[j] : p2[j];
+    // mutation (Sec. 3.5): columns in order, pairs in order, flip iff different
+    {
+        Draws dr(p.seed, p.pop_id, gen, k + (half ? N : 0u));
+        const int NC = p.NC, NR = p.NR;
+        if (NC == 1 && NR == 1) {
+            const uint32_t cc = uniform_int(dr.next(), 1u, (uint32_t)(M - 1));
+            const uint32_t ra = uniform_int(dr.next(), 0u, (uint32_t)(M - 1));
+            const uint32_t rb = uniform_int(dr.next(), 0u, (uint32_t)(M - 1));
+#pragma unroll
+            for (int j = 1; j < M; ++j) {
+                if ((uint32_t)j == cc) {
+                    const uint32_t t = ((o[j] >> ra) ^ (o[j] >> rb)) & 1u;
+                    o[j] ^= (t << ra) | (t << rb);
+                }
+            }
+        } else {
+            uint8_t cols[64], r1[64], r2[64];
+            for (int jc = 0; jc < NC; ++jc)
+                cols[jc] = (uint8_t)uniform_int(dr.next(), 1u, (uint32_t)(M - 1));
+            for (int ir = 0; ir < NR; ++ir)
+                r1[ir] = (uint8_t)uniform_int(dr.next(), 0u, (uint32_t)(M - 1));
+            for (int ir = 0; ir < NR; ++ir)
+                r2[ir] = (uint8_t)uniform_int(dr.next(), 0u, (uint32_t)(M - 1));
+            for (int jc = 0; jc < NC; ++jc) {
+                const int cc = cols[jc];
+                uint32_t w = 0;
+#pragma unroll
+                for (int j = 1; j < M; ++j)
+                    w = (j == cc) ? o[j] : w;
+                for (int ir = 0; ir < NR; ++ir) {
+                    const uint32_t ra = r1[ir], rb = r2[ir];
+                    const uint32_t t = ((w >> ra) ^ (w >> rb)) & 1u;
+                    w ^= (t << ra) | (t << rb);
+                }
+#pragma unroll
+                for (int j = 1; j < M; ++j)
+                    o[j] = (j == cc) ? w : o[j];
+            }
+        }
+    }
+    uint32_t f;
+    switch (p.kind) {
+    case FIT_SQ: f = fitness_regs<M, FIT_SQ>(o); break;
+    case FIT_ABS: f = fitness_regs<M, FIT_ABS>(o); break;
+    default: f = fitness_regs<M, FIT_NNZ>(o); break;
+    }
+    slot_child = 2u * N + k + (half ? N : 0u);
+    {
+        uint4 *d = reinterpret_cast<uint4 *>(dst_pop + (size_t)slot_child * M);
+#pragma unroll
+        for (int v = 0; v < M / 4; ++v)
+            d[v] = make_uint4(o[4 * v], o[4 * v + 1], o[4 * v + 2], o[4 * v + 3]);
+        p.fit[src ^ 1][slot_child] = f;
+    }
+    f_child = f;
+}
+
+// ---------------------------------------------------------------------------
+// 32 < m <= 128: a warp per pair, matrices staged in shared memory.
+// ---------------------------------------------------------------------------
+template <int W>
+__device__ void pair_warp(const FusedPop &p, const PopSel &S, int src, uint32_t gen, uint32_t tch, uint32_t k,
+                          const uint32_t *smask, const uint32_t *sbefore, uint32_t *err, uint32_t *buf,
+                          uint32_t *hist_next, uint32_t *orv_next, unsigned long long *best)
+{
+    const int lane = threadIdx.x & 31;
+    const int m = p.m;
+    const uint32_t N = (uint32_t)p.N, words = (uint32_t)(m * W);
+    uint32_t s1 = 0, s2 = 0, F1 = 0, F2 = 0;
+    int c = 1;
+    if (lane == 0) {
+        const uint32_t *row = p.perm + (size_t)tch * 2u * N;
+        s1 = survivor_of(__ldg(row + k), p, S, smask, sbefore, err);
+        s2 = survivor_of(__ldg(row + k + N), p, S, smask, sbefore, err);
+        F1 = ldcg32(p.fit[src] + s1);
+        F2 = ldcg32(p.fit[src] + s2);
+        c = cut_point(p.seed, p.pop_id, gen, k, m);
+    }
+    s1 = __shfl_sync(FULL, s1, 0);
+    s2 = __shfl_sync(FULL, s2, 0);
+    c = __shfl_sync(FULL, c, 0);
+    uint32_t *b1 = buf, *b2 = buf + words, *bo = buf + 2 * words;
+    const uint32_t *sp = p.pop[src];
+    uint32_t *dp = p.pop[src ^ 1];
+    for (uint32_t e = lane; e < words; e += 32) {
+        const uint32_t x = ldcg32(sp + (size_t)s1 * words + e), y = ldcg32(sp + (size_t)s2 * words + e);
+        b1[e] = x;
+        b2[e] = y;
+        dp[(size_t)k * words + e] = x;
+        dp[(size_t)(k + N) * words + e] = y;
+    }
+    if (lane == 0) {
+        p.fit[src ^ 1][k] = F1;
+        p.fit[src ^ 1][k + N] = F2;
+    }
+    uint32_t fc[2] = {0, 0};
+    for (int half = 0; half < 2; ++half) {
+        __syncwarp();
+        for (uint32_t e = lane; e < words; e += 32)
+            bo[e] = (((int)(e / W) < c) != (half != 0)) ? b1[e] : b2[e];
+        __syncwarp();
+        if (lane == 0) {
+            Draws dr(p.seed, p.pop_id, gen, k + (half ? N : 0u));
+            uint8_t cols[64], r1[64], r2[64];
+            for (int jc = 0; jc < p.NC; ++jc)
+                cols[jc] = (uint8_t)uniform_int(dr.next(), 1u, (uint32_t)(m - 1));
+            for (int ir = 0; ir < p.NR; ++ir)
+                r1[ir] = (uint8_t)uniform_int(dr.next(), 0u, (uint32_t)(m - 1));
+            for (int ir = 0; ir < p.NR; ++ir)
+                r2[ir] = (uint8_t)uniform_int(dr.next(), 0u, (uint32_t)(m - 1));
+            for (int jc = 0; jc < p.NC; ++jc) {
+                uint32_t *col = bo + cols[jc] * W;
+                for (int ir = 0; ir < p.NR; ++ir) {
+                    const int ra = r1[ir], rb = r2[ir];
+                    const uint32_t ba = (col[ra >> 5] >> (ra & 31)) & 1u, bb = (col[rb >> 5] >> (rb & 31)) & 1u;
+                    if (ba != bb) {
+                        col[ra >> 5] ^= 1u << (ra & 31);
+                        col[rb >> 5] ^= 1u << (rb & 31);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        uint32_t f;
+        switch (p.kind) {
+        case FIT_SQ: f = warp_fitness_cols<W, FIT_SQ>(bo, m, lane); break;
+        case FIT_ABS: f = warp_fitness_cols<W, FIT_ABS>(bo, m, lane); break;
+        default: f = warp_fitness_cols<W, FIT_NNZ>(bo, m, lane); break;
+        }
+        const uint32_t slot = 2u * N + k + (half ? N : 0u);
+        for (uint32_t e = lane; e < words; e += 32)
+            dp[(size_t)slot * words + e] = bo[e];
+        if (lane == 0)
+            p.fit[src ^ 1][slot] = f;
+        fc[half] = f;
+    }
+    if (lane == 0) {
+        const uint32_t fv[4] = {F1, F2, fc[0], fc[1]};
+        const uint32_t sv[4] = {k, k + N, 2u * N + k, 3u * N + k};
+        unsigned long long bk = ~0ull;
+        uint32_t orr = 0;
+        for (int i = 0; i < 4; ++i) {
+            if (fv[i] <= S.capn)
+                atomicAdd(hist_next + (fv[i] >> S.shiftn), 1u);
+            orr |= fv[i];
+            const unsigned long long key = ((unsigned long long)fv[i] << 32) | sv[i];
+            bk = key < bk ? key : bk;
+        }
+        atomicOr(orv_next, orr);
+        atomicMin(best, bk);
+    }
+    __syncwarp();
+}
+
+} // namespace
+
+__global__ void __launch_bounds__(kFusedThreads) k_fused(const __grid_constant__ FusedParams prm)
+{
+    extern __shared__ __align__(16) uint32_t dyn[];
+    __shared__ PopSel S[kMaxPops];
+    __shared__ uint32_t s_tmp[33];
+    __shared__ int s_flag;
+
+    const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
+    const int npop = prm.npop;
+    const uint32_t nblocks = gridDim.x;
+    const uint32_t gtid = blockIdx.x * blockDim.x + tid, gthreads = nblocks * blockDim.x;
+    const uint32_t gwarp = gtid >> 5, gwarps = gthreads >> 5;
+    uint32_t *smask = dyn;
+    uint32_t *sbefore = dyn + prm.total_tiles;
+    uint32_t *wbuf = dyn + 2 * prm.total_tiles + wib * prm.warp_buf_words;
+    uint32_t *err = prm.err;
+    uint32_t epoch = 0;
+    int src = prm.src;
+    int done = 0;
+
+    // ---- pre-pass: max and OR of the current fitness of every population -----
+    {
+        const int par0 = (int)((prm.gen0 + 1u) & 1u);
+        for (int i = 0; i < npop; ++i) {
+            const FusedPop &p = prm.p[i];
+            const uint32_t P = (uint32_t)(4 * p.N);
+            uint32_t mx = 0, orr = 0;
+            for (uint32_t q = gtid; q < P; q += gthreads) {
+                const uint32_t f = ldcg32(p.fit[src] + q);
+                mx = max(mx, f);
+                orr |= f;
+            }
+            mx = warp_max(mx);
+            orr = warp_or(orr);
+            if (lane == 0) {
+                atomicMax(stat_of(p) + 0, mx);
+                atomicOr(stat_of(p) + 1 + par0, orr);
+            }
+        }
+        if (!grid_barrier(prm.bar, nblocks, epoch, err))
+            return;
+        if (tid < npop) {
+            const FusedPop &p = prm.p[tid];
+            const uint32_t cap = ldcg32(stat_of(p) + 0);
+            const uint32_t v = ctz_or(ldcg32(stat_of(p) + 1 + par0));
+            S[tid].cap = cap;
+            S[tid].shift = max(v, shift_for(cap));
+        }
+        __syncthreads();
+        for (int i = 0; i < npop; ++i) {
+            const FusedPop &p = prm.p[i];
+            const uint32_t P = (uint32_t)(4 * p.N);
+            uint32_t *h = hist_of(p, par0);
+            const uint32_t cap = S[i].cap, sh = S[i].shift;
+            // uniform trip count per warp so the warp-collective add stays converged
+            const uint32_t span = (P + 31u) & ~31u;
+            for (uint32_t q = gtid; q < ((span + gthreads - 1) / gthreads) * gthreads; q += gthreads) {
+                const bool in = q < P;
+                const uint32_t f = in ? ldcg32(p.fit[src] + q) : 0u;
+                warp_hist_add(h, in && f <= cap, f >> sh);
+            }
+        }
+        if (!grid_barrier(prm.bar, nblocks, epoch, err))
+            return;
+    }
+
+    uint32_t ref_level = 0;
+    for (int t = 0; t < prm.ngen; ++t) {
+        const uint32_t gen = prm.gen0 + 1u + (uint32_t)t;
+        const int par = (int)(gen & 1u);
+
+        // ---- phase A: threshold of the 2N smallest ---------------------------------
+        for (int i = 0; i < npop; ++i) {
+            const FusedPop &p = prm.p[i];
+            uint32_t *hn = hist_of(p, par ^ 1);
+            for (uint32_t e = gtid; e < (uint32_t)kHistR; e += gthreads)
+                hn[e] = 0u;
+        }
+        if (blockIdx.x == 0 && tid < npop) {
+            const FusedPop &p = prm.p[tid];
+            stat_of(p)[1 + (par ^ 1)] = 0u;
+            p.traj[(gen - 1u) % (uint32_t)p.traj_cap] = ~0ull;
+        }
+        if (wib < npop) {
+            const FusedPop &p = prm.p[wib];
+            PopSel &s = S[wib];
+            uint32_t b, before;
+            const uint32_t need = (uint32_t)(2 * p.N);
+            warp_find_bucket(hist_of(p, par), (s.cap >> s.shift) + 1u, need, err, b, before);
+            const uint32_t v = ctz_or(ldcg32(stat_of(p) + 1 + par));
+            if (lane == 0) {
+                s.v = v;
+                s.lo = b << s.shift;
+                s.need = need - before;
+                s.sr = s.shift;
+                s.exact = s.shift <= v ? 1u : 0u;
+            }
+        }
+        __syncthreads();
+        for (;;) {
+            if (tid == 0) {
+                int any = 0;
+                for (int i = 0; i < npop; ++i)
+                    any |= S[i].exact ? 0 : 1;
+                s_flag = any;
+            }
+            __syncthreads();
+            if (!s_flag)
+                break;
+            const int rl = (int)(ref_level % 3u), rz = (int)((ref_level + 1u) % 3u);
+            for (int i = 0; i < npop; ++i) {
+                const FusedPop &p = prm.p[i];
+                uint32_t *hz = ref_of(p, rz);
+                for (uint32_t e = gtid; e < (uint32_t)kHistR; e += gthreads)
+                    hz[e] = 0u;
+                if (S[i].exact)
+                    continue;
+                const uint32_t P = (uint32_t)(4 * p.N);
+                const uint32_t lo = S[i].lo, sr = S[i].sr;
+                const uint32_t sn = max(S[i].v, sr > 12u ? sr - 12u : 0u);
+                uint32_t *h = ref_of(p, rl);
+                const uint32_t span = (P + 31u) & ~31u;
+                for (uint32_t q = gtid; q < ((span + gthreads - 1) / gthreads) * gthreads; q += gthreads) {
+                    const bool in = q < P;
+                    const uint32_t f = in ? ldcg32(p.fit[src] + q) : 0u;
+                    const bool hit = in && f >= lo && ((uint64_t)(f - lo) >> sr) == 0u;
+                    warp_hist_add(h, hit, hit ? (f - lo) >> sn : 0u);
+                }
+            }
+            if (!grid_barrier(prm.bar, nblocks, epoch, err))
+                return;
+            if (wib < npop && !S[wib].exact) {
+                const FusedPop &p = prm.p[wib];
+                PopSel &s = S[wib];
+                const uint32_t sn = max(s.v, s.sr > 12u ? s.sr - 12u : 0u);
+                uint32_t b, before;
+                warp_find_bucket(ref_of(p, rl), 1u << (s.sr - sn), s.need, err, b, before);
+                if (lane == 0) {
+                    s.lo += b << sn;
+                    s.need -= before;
+                    s.sr = sn;
+                    s.exact = sn <= s.v ? 1u : 0u;
+                }
+            }
+            ++ref_level;
+            __syncthreads();
+        }
+        if (tid < npop) {
+            PopSel &s = S[tid];
+            s.T = s.lo;
+            s.take = s.need;
+            s.capn = s.T;
+            s.shiftn = max(s.v, shift_for(s.T));
+        }
+        __syncthreads();
+        // tile masks
+        for (int i = 0; i < npop; ++i) {
+            const FusedPop &p = prm.p[i];
+            const uint32_t P = (uint32_t)(4 * p.N), T = S[i].T;
+            for (uint32_t tl = gwarp; tl < p.ntiles; tl += gwarps) {
+                const uint32_t q = tl * 32u + lane;
+                const uint32_t f = q < P ? ldcg32(p.fit[src] + q) : 0u;
+                const uint32_t lt = __ballot_sync(FULL, q < P && f < T);
+                const uint32_t eq = __ballot_sync(FULL, q < P && f == T);
+                if (lane == 0)
+                    p.tmask[tl] = (unsigned long long)lt | ((unsigned long long)eq << 32);
+            }
+        }
+        if (!grid_barrier(prm.bar, nblocks, epoch, err))
+            return;
+
+        // ---- phase B: survivors in slot order, then build ------------------------
+        {
+            const uint32_t TT = prm.total_tiles;
+            uint32_t carry = 0, tot;
+            for (uint32_t b0 = 0; b0 < TT; b0 += blockDim.x) {
+                const uint32_t tt = b0 + tid;
+                uint32_t c = 0;
+                if (tt < TT) {
+                    int i = 0;
+                    while (i + 1 < npop && tt >= prm.p[i + 1].tile_base)
+                        ++i;
+                    c = (uint32_t)__popc((uint32_t)(ldcg64(prm.p[i].tmask + (tt - prm.p[i].tile_base)) >> 32));
+                }
+                const uint32_t ex = block_excl_scan(c, s_tmp, &tot) + carry;
+                carry += tot;
+                if (tt < TT)
+                    sbefore[tt] = ex;
+            }
+            __syncthreads();
+            for (uint32_t tt = tid; tt < TT; tt += blockDim.x) {
+                int i = 0;
+                while (i + 1 < npop && tt >= prm.p[i + 1].tile_base)
+                    ++i;
+                const unsigned long long tm = ldcg64(prm.p[i].tmask + (tt - prm.p[i].tile_base));
+                const uint32_t eqb = sbefore[tt] - sbefore[prm.p[i].tile_base];
+                const uint32_t take = S[i].take;
+                const int keep = take > eqb ? (int)(take - eqb) : 0;
+                smask[tt] = (uint32_t)tm | lowest_set_bits((uint32_t)(tm >> 32), keep);
+            }
+            __syncthreads();
+            carry = 0;
+            for (uint32_t b0 = 0; b0 < TT; b0 += blockDim.x) {
+                const uint32_t tt = b0 + tid;
+                const uint32_t c = tt < TT ? (uint32_t)__popc(smask[tt]) : 0u;
+                const uint32_t ex = block_excl_scan(c, s_tmp, &tot) + carry;
+                carry += tot;
+                if (tt < TT)
+                    sbefore[tt] = ex;
+            }
+            __syncthreads();
+            if (tid < npop) {
+                const FusedPop &p = prm.p[tid];
+                const uint32_t base = sbefore[p.tile_base];
+                const uint32_t last = p.tile_base + p.ntiles - 1u;
+                S[tid].base = base;
+                if (sbefore[last] + (uint32_t)__popc(smask[last]) - base != (uint32_t)(2 * p.N))
+                    atomicOr(err, ERR_INTERNAL);
+            }
+            __syncthreads();
+        }
+        // m <= 32: two threads per pair
+        for (uint32_t u = gtid & ~31u; u < prm.thread_slots; u += gthreads) {
+            // the population whose (32-aligned) thread range holds this warp
+            int i = -1;
+            for (int j = 0; j < npop; ++j)
+                if (prm.p[j].m <= 32 && u >= prm.p[j].work_base)
+                    i = (i < 0 || prm.p[j].work_base >= prm.p[i].work_base) ? j : i;
+            const FusedPop &p = prm.p[i < 0 ? 0 : i];
+            const uint32_t local = u + (uint32_t)lane - p.work_base;
+            const uint32_t k = local >> 1;
+            const int half = (int)(local & 1u);
+            const bool valid = i >= 0 && k < (uint32_t)p.N;
+            uint32_t fpar = 0, spar = 0, fch = 0, sch = 0;
+            switch (p.m) {
+#define HADGA_PT(MM)                                                                                       \
+    case MM:                                                                                               \
+        pair_thread<MM>(p, S[i < 0 ? 0 : i], src, gen, (uint32_t)t, k, half, valid, smask, sbefore, err,  \
+                        fpar, spar, fch, sch);                                                             \
+        break;
+                HADGA_PT(4) HADGA_PT(8) HADGA_PT(12) HADGA_PT(16) HADGA_PT(20) HADGA_PT(24) HADGA_PT(28) HADGA_PT(32)
+#undef HADGA_PT
+            default:
+                break;
+            }
+            const PopSel &s = S[i < 0 ? 0 : i];
+            uint32_t *hn = hist_of(p, par ^ 1);
+            warp_hist_add(hn, valid && fpar <= s.capn, fpar >> s.shiftn);
+            warp_hist_add(hn, valid && fch <= s.capn, fch >> s.shiftn);
+            const uint32_t orr = warp_or(valid ? (fpar | fch) : 0u);
+            unsigned long long key = ~0ull;
+            if (valid) {
+                const unsigned long long k1 = ((unsigned long long)fpar << 32) | spar;
+                const unsigned long long k2 = ((unsigned long long)fch << 32) | sch;
+                key = k1 < k2 ? k1 : k2;
+            }
+            key = warp_min_u64(key);
+            if (lane == 0 && i >= 0) {
+                atomicOr(stat_of(p) + 1 + (par ^ 1), orr);
+                atomicMin(p.traj + (gen - 1u) % (uint32_t)p.traj_cap, key);
+            }
+        }
+        // 32 < m <= 128: a warp per pair
+        for (uint32_t pr = gwarp; pr < prm.warp_pairs; pr += gwarps) {
+            int i = -1;
+            for (int j = 0; j < npop; ++j)
+                if (prm.p[j].m > 32 && pr >= prm.p[j].work_base && pr < prm.p[j].work_base + (uint32_t)prm.p[j].N)
+                    i = j;
+            if (i < 0)
+                continue;
+            const FusedPop &p = prm.p[i];
+            const uint32_t k = pr - p.work_base;
+            uint32_t *hn = hist_of(p, par ^ 1);
+            uint32_t *on = stat_of(p) + 1 + (par ^ 1);
+            unsigned long long *bk = p.traj + (gen - 1u) % (uint32_t)p.traj_cap;
+            switch (p.W) {
+            case 2: pair_warp<2>(p, S[i], src, gen, (uint32_t)t, k, smask, sbefore, err, wbuf, hn, on, bk); break;
+            case 3: pair_warp<3>(p, S[i], src, gen, (uint32_t)t, k, smask, sbefore, err, wbuf, hn, on, bk); break;
+            case 4: pair_warp<4>(p, S[i], src, gen, (uint32_t)t, k, smask, sbefore, err, wbuf, hn, on, bk); break;
+            default: break;
+            }
+        }
+        if (!grid_barrier(prm.bar, nblocks, epoch, err))
+            return;
+        src ^= 1;
+        if (tid < npop) {
+            S[tid].cap = S[tid].capn;
+            S[tid].shift = S[tid].shiftn;
+        }
+        done = t + 1;
+        if (prm.stop_at_zero) {
+            const FusedPop &p = prm.p[0];
+            const unsigned long long key = ldcg64(p.traj + (gen - 1u) % (uint32_t)p.traj_cap);
+            if ((key >> 32) == 0ull)
+                break;
+        }
+        __syncthreads();
+    }
+    if (blockIdx.x == 0 && tid == 0)
+        *prm.done = done;
+}
+
+size_t fused_smem_bytes(const FusedParams &p)
+{
+    return (size_t)2 * p.total_tiles * 4u + (size_t)(kFusedThreads / 32) * p.warp_buf_words * 4u;
+}
+
+cudaError_t fused_grid(size_t smem, int *grid)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused, kFusedThreads, smem);
+    if (e != cudaSuccess)
+        return e;
+    if (per < 1)
+        return cudaErrorCooperativeLaunchTooLarge;
+    *grid = sms * (per < 2 ? per : 2);
+    return cudaSuccess;
+}
+
+cudaError_t launch_fused(const FusedParams &p, int grid, size_t smem, cudaStream_t s)
+{
+    void *args[] = {(void *)&p};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_fused, dim3(grid), dim3(kFusedThreads), args, smem, s);
+    if (e == cudaSuccess)
+        note_launches(1);
+    return e;
+}
+
+} // namespace hadga

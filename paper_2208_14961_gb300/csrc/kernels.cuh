@@ -85,40 +85,49 @@ cudaError_t launch_perm_table(uint32_t n, uint32_t seed, uint32_t pop_id, uint32
 int perm_global_bits(uint32_t n);
 
 // ---- fused persistent generation kernel (k_fused.cu) -------------------------
+constexpr int kMaxPops = 16;       // populations in one persistent launch
+constexpr int kHistR = 4096;       // buckets of a selection histogram
+constexpr int kFusedThreads = 256;
+constexpr int kFusedMaxM = 128;    // orders the fused kernel builds (larger: plain path)
+constexpr uint32_t kFusedMaxTiles = 16384;  // joint tiles of 32 slots (P <= 524288)
+
+// Per-population state words of the fused kernel (device memory):
+// hist[2][kHistR] selection histograms by generation parity, ref[3][kHistR]
+// refinement histograms, stat[4] = {max F, OR of F (parity 0, parity 1), spare}.
+constexpr size_t kFusedStateWords = 5 * kHistR + 4;
+
 struct FusedPop {
     uint32_t *pop[2];          // bit storage, ping-pong
-    uint32_t *fit[2];
-    uint32_t *hist[2];         // level-0 histograms, ping-pong by generation
-    uint32_t *hist_ref;        // refinement histogram
-    unsigned long long *tmask; // [tiles]
-    const uint32_t *perm;      // [chunk][2N]
-    unsigned long long *traj;  // [traj_cap]
-    uint32_t *orv;             // [2] OR of all fitness values, by generation parity
-    uint32_t *cap;             // [2] histogram cap (threshold of the previous generation)
+    uint32_t *fit[2];          // fitness, ping-pong
+    uint32_t *state;           // kFusedStateWords words, zeroed before each launch
+    unsigned long long *tmask; // [ntiles] (F < T) | (F == T) << 32 per tile
+    const uint32_t *perm;      // [ngen][2N] survivor orders of the chunk
+    unsigned long long *traj;  // [traj_cap] best keys (F << 32 | slot)
     int32_t m, W, NC, NR, kind, traj_cap;
     int64_t N;
     uint32_t seed, pop_id;
-    uint32_t tile_base;        // first tile of this population in the joint tile space
-    uint32_t pair_base;        // first pair-chunk slot in the joint pair space (multiple of 32)
+    uint32_t tile_base, ntiles;  // tiles of 32 slots in the joint tile space
+    uint32_t work_base;          // m <= 32: first thread slot; m > 32: first pair
 };
 
-struct FusedArgs {
-    const FusedPop *pops;      // device array
+struct FusedParams {
+    FusedPop p[kMaxPops];
     int32_t npop;
     uint32_t total_tiles;
-    uint32_t total_pair_slots; // joint pair space (each population padded to 32)
-    uint32_t gen0;             // generation before the chunk
-    int32_t ngen;              // generations in this chunk
-    int32_t stop_at_zero;
-    int32_t src;               // which ping-pong buffer holds the current state
-    uint32_t *bar;
-    uint32_t *err;
-    int32_t *done;             // generations completed (device)
+    uint32_t thread_slots;   // joint space of m <= 32 populations, 2 threads per pair, padded to 32
+    uint32_t warp_pairs;     // joint pair space of m > 32 populations
+    uint32_t gen0;           // generation number before the chunk
+    int32_t ngen;            // generations to run
+    int32_t stop_at_zero;    // stop after a generation whose best fitness (population 0) is 0
+    int32_t src;             // ping-pong buffer holding the current population
+    int32_t warp_buf_words;  // shared words per warp for m > 32 populations
+    uint32_t *bar;           // grid-barrier counter (zeroed before the launch)
+    uint32_t *err;           // device error word
+    int32_t *done;           // generations completed
 };
 
-cudaError_t launch_fused_prepare(const FusedArgs &a, int npop_host, const FusedPop *pops_host, cudaStream_t s);
-cudaError_t launch_fused(const FusedArgs &a, int blocks, int threads, size_t smem, cudaStream_t s);
-cudaError_t fused_occupancy(int threads, size_t smem, int *blocks_per_sm);
-size_t fused_smem_bytes(uint32_t total_tiles, int threads);
+size_t fused_smem_bytes(const FusedParams &p);
+cudaError_t fused_grid(size_t smem, int *grid);
+cudaError_t launch_fused(const FusedParams &p, int grid, size_t smem, cudaStream_t s);
 
 } // namespace hadga

@@ -63,3 +63,76 @@ def test_small_configs(mode, m, N, NC, NR, kind):
     h = need_gpu()
     _assert_same(_run_gpu(h, m, N, 7, 30, 1, mode, NC, NR, kind, pop_id=3),
                  _run_oracle(m, N, 7, 30, NC, NR, kind, pop_id=3))
+
+
+def test_fused_kernel_is_used_for_the_paper_scale():
+    h = need_gpu()
+    pop = h.Population(20, 10000, seed=1, storage=1)
+    assert pop.is_fused()
+    pop.close()
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_mixed_plain_and_fused_resume(storage):
+    """Checkpoint/resume: plain generations, then fused ones, then plain,
+    equal one oracle run (the state is population, fitness and g)."""
+    h = need_gpu()
+    m, N, seed = 16, 300, 9
+    pop = h.Population(m, N, seed=seed, NC=2, NR=2, fitness=2, storage=storage, traj_cap=64)
+    pop.init_population()
+    pop.fitness()
+    pop.step_plain(7)
+    pop.step(70)           # crosses a chunk boundary of the persistent kernel
+    pop.step_plain(3)
+    pop.sync()
+    assert pop.generation() == 80
+    ref = oracle.init_population(m, 4 * N, seed)
+    F = oracle.fitness(ref, 2)
+    _, tf, ts = oracle.run(ref, F, N, 2, 2, 2, seed, 0, 0, 80)
+    assert np.array_equal(pop.as_int8(), ref)
+    assert np.array_equal(pop.fitness_host(), F)
+    gtf, gts = pop.trajectory()
+    assert np.array_equal(gtf.astype(np.uint64), tf[-64:]) and np.array_equal(gts, ts[-64:])
+
+
+def test_stop_at_zero_finds_order_12_hadamard():
+    h = need_gpu()
+    m, N, seed, NC, NR = 12, 1000, 3, 2, 2
+    ref = oracle.init_population(m, 4 * N, seed)
+    F = oracle.fitness(ref, 2)
+    n_ref, tf, ts = oracle.run(ref, F, N, NC, NR, 2, seed, 0, 0, 400, stop_at_zero=True)
+    pop = h.Population(m, N, seed=seed, NC=NC, NR=NR, fitness=2, storage=1, traj_cap=512)
+    pop.init_population()
+    pop.fitness()
+    done = pop.step(400, stop_at_zero=True)
+    assert done == n_ref
+    assert np.array_equal(pop.as_int8(), ref)
+    if tf[-1] == 0:
+        H = pop.get_slot(int(ts[-1])).astype(np.int64)
+        assert np.array_equal(H.T @ H, m * np.eye(m, dtype=np.int64))
+
+
+def test_multi_population_mixed_orders_one_launch():
+    """Mixed orders 12..36 in one persistent launch, each population equal
+    to its own oracle run (sizes reduced from the 2,000-20,000 range)."""
+    h = need_gpu()
+    orders = [12, 16, 20, 24, 28, 32, 36]
+    pops, refs = [], []
+    for idx, m in enumerate(orders):
+        N = 40 + 37 * idx
+        p = h.Population(m, N, seed=3, pop_id=idx, fitness=0, storage=1, traj_cap=64)
+        p.init_population()
+        p.fitness()
+        pops.append(p)
+        r = oracle.init_population(m, 4 * N, 3, idx)
+        F = oracle.fitness(r, 0)
+        _, tf, ts = oracle.run(r, F, N, 1, 1, 0, 3, idx, 0, 60)
+        refs.append((r, F, tf, ts))
+    h.step_multi(pops, 60)
+    for p, (r, F, tf, ts) in zip(pops, refs):
+        p.sync()
+        assert p.generation() == 60
+        assert np.array_equal(p.as_int8(), r)
+        assert np.array_equal(p.fitness_host(), F)
+        gtf, gts = p.trajectory()
+        assert np.array_equal(gtf.astype(np.uint64), tf) and np.array_equal(gts, ts)
