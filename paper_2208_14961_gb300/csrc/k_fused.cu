@@ -25,6 +25,8 @@
 //           accumulated with warp-aggregated atomics.
 // Data written inside the launch is read with ld.global.cg (L2) so no SM
 // can see a stale L1 line across generations.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -125,6 +127,27 @@ __device__ __forceinline__ uint32_t warp_max(uint32_t v)
     for (int o = 16; o > 0; o >>= 1)
         v = max(v, __shfl_xor_sync(FULL, v, o));
     return v;
+}
+
+// Exclusive prefix sums over e in [0, n) of cnt(e) into out[e] (shared
+// memory), each thread walking one contiguous chunk: two short sequential
+// passes around a single block-wide scan.  Every thread calls.
+template <class Cnt>
+__device__ __forceinline__ void block_scan_chunks(uint32_t n, Cnt cnt, uint32_t *out, uint32_t *tmp)
+{
+    const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
+    const uint32_t lo = min(n, threadIdx.x * per), hi = min(n, lo + per);
+    uint32_t sum = 0;
+    for (uint32_t e = lo; e < hi; ++e)
+        sum += cnt(e);
+    uint32_t tot;
+    uint32_t ex = block_excl_scan(sum, tmp, &tot);
+    for (uint32_t e = lo; e < hi; ++e) {
+        const uint32_t c = cnt(e);
+        out[e] = ex;
+        ex += c;
+    }
+    __syncthreads();
 }
 
 // Slot of survivor number d of a population: binary search over the joint
@@ -386,11 +409,12 @@ __device__ void pair_warp(const FusedPop &p, const PopSel &S, int src, uint32_t 
 
 } // namespace
 
-__global__ void __launch_bounds__(kFusedThreads) k_fused(const __grid_constant__ FusedParams prm)
+__global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constant__ FusedParams prm)
 {
     extern __shared__ __align__(16) uint32_t dyn[];
     __shared__ PopSel S[kMaxPops];
     __shared__ uint32_t s_tmp[33];
+    __shared__ uint32_t hoff[kMaxPops];
     __shared__ int s_flag;
 
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
@@ -398,9 +422,14 @@ __global__ void __launch_bounds__(kFusedThreads) k_fused(const __grid_constant__
     const uint32_t nblocks = gridDim.x;
     const uint32_t gtid = blockIdx.x * blockDim.x + tid, gthreads = nblocks * blockDim.x;
     const uint32_t gwarp = gtid >> 5, gwarps = gthreads >> 5;
-    uint32_t *smask = dyn;
-    uint32_t *sbefore = dyn + prm.total_tiles;
-    uint32_t *wbuf = dyn + 2 * prm.total_tiles + wib * prm.warp_buf_words;
+    // shared layout: [region shared by the tile masks (phase B) and the staged
+    // histograms (phase A)] [survivor masks] [survivor prefix] [warp buffers]
+    const uint32_t r1 = max(2u * prm.total_tiles, 2u * kHistSmem);
+    unsigned long long *tm = reinterpret_cast<unsigned long long *>(dyn);
+    uint32_t *hcnt = dyn, *hpre = dyn + kHistSmem;
+    uint32_t *smask = dyn + r1;
+    uint32_t *sbefore = smask + prm.total_tiles;
+    uint32_t *wbuf = sbefore + prm.total_tiles + wib * prm.warp_buf_words;
     uint32_t *err = prm.err;
     uint32_t epoch = 0;
     int src = prm.src;
@@ -469,20 +498,52 @@ __global__ void __launch_bounds__(kFusedThreads) k_fused(const __grid_constant__
             stat_of(p)[1 + (par ^ 1)] = 0u;
             p.traj[(gen - 1u) % (uint32_t)p.traj_cap] = ~0ull;
         }
-        if (wib < npop) {
-            const FusedPop &p = prm.p[wib];
-            PopSel &s = S[wib];
-            uint32_t b, before;
-            const uint32_t need = (uint32_t)(2 * p.N);
-            warp_find_bucket(hist_of(p, par), (s.cap >> s.shift) + 1u, need, err, b, before);
-            const uint32_t v = ctz_or(ldcg32(stat_of(p) + 1 + par));
-            if (lane == 0) {
-                s.v = v;
-                s.lo = b << s.shift;
-                s.need = need - before;
-                s.sr = s.shift;
-                s.exact = s.shift <= v ? 1u : 0u;
+        if (tid < npop) {
+            PopSel &s = S[tid];
+            s.v = ctz_or(ldcg32(stat_of(prm.p[tid]) + 1 + par));
+            s.sr = s.shift;
+            s.exact = s.shift <= s.v ? 1u : 0u;
+            s.need = 0xFFFFFFFFu;  // marks "crossing not found"
+        }
+        // histograms staged in shared memory (groups of populations that fit),
+        // scanned in one block-wide pass, crossing of 2N located per population
+        for (int i0 = 0; i0 < npop;) {
+            uint32_t off = 0;
+            int i1 = i0;
+            while (i1 < npop) {
+                const uint32_t nb = (S[i1].cap >> S[i1].shift) + 1u;
+                if (i1 > i0 && off + nb > kHistSmem)
+                    break;
+                hoff[i1] = off;
+                off += nb;
+                ++i1;
             }
+            for (uint32_t e = tid; e < off; e += blockDim.x) {
+                int i = i0;
+                while (i + 1 < i1 && e >= hoff[i + 1])
+                    ++i;
+                hcnt[e] = ldcg32(hist_of(prm.p[i], par) + (e - hoff[i]));
+            }
+            __syncthreads();
+            block_scan_chunks(off, [&](uint32_t e) { return hcnt[e]; }, hpre, s_tmp);
+            for (uint32_t e = tid; e < off; e += blockDim.x) {
+                int i = i0;
+                while (i + 1 < i1 && e >= hoff[i + 1])
+                    ++i;
+                const uint32_t need = (uint32_t)(2 * prm.p[i].N);
+                const uint32_t ex = hpre[e] - hpre[hoff[i]], h = hcnt[e];
+                if (h && ex < need && need <= ex + h) {
+                    S[i].lo = (e - hoff[i]) << S[i].shift;
+                    S[i].need = need - ex;
+                }
+            }
+            __syncthreads();
+            i0 = i1;
+        }
+        if (tid < npop && S[tid].need == 0xFFFFFFFFu) {
+            atomicOr(err, ERR_INTERNAL);
+            S[tid].lo = 0;
+            S[tid].need = 1;
         }
         __syncthreads();
         for (;;) {
@@ -560,43 +621,27 @@ __global__ void __launch_bounds__(kFusedThreads) k_fused(const __grid_constant__
         // ---- phase B: survivors in slot order, then build ------------------------
         {
             const uint32_t TT = prm.total_tiles;
-            uint32_t carry = 0, tot;
-            for (uint32_t b0 = 0; b0 < TT; b0 += blockDim.x) {
-                const uint32_t tt = b0 + tid;
-                uint32_t c = 0;
-                if (tt < TT) {
-                    int i = 0;
-                    while (i + 1 < npop && tt >= prm.p[i + 1].tile_base)
-                        ++i;
-                    c = (uint32_t)__popc((uint32_t)(ldcg64(prm.p[i].tmask + (tt - prm.p[i].tile_base)) >> 32));
-                }
-                const uint32_t ex = block_excl_scan(c, s_tmp, &tot) + carry;
-                carry += tot;
-                if (tt < TT)
-                    sbefore[tt] = ex;
-            }
-            __syncthreads();
             for (uint32_t tt = tid; tt < TT; tt += blockDim.x) {
                 int i = 0;
                 while (i + 1 < npop && tt >= prm.p[i + 1].tile_base)
                     ++i;
-                const unsigned long long tm = ldcg64(prm.p[i].tmask + (tt - prm.p[i].tile_base));
+                tm[tt] = ldcg64(prm.p[i].tmask + (tt - prm.p[i].tile_base));
+            }
+            __syncthreads();
+            block_scan_chunks(TT, [&](uint32_t e) { return (uint32_t)__popc((uint32_t)(tm[e] >> 32)); }, sbefore,
+                              s_tmp);
+            for (uint32_t tt = tid; tt < TT; tt += blockDim.x) {
+                int i = 0;
+                while (i + 1 < npop && tt >= prm.p[i + 1].tile_base)
+                    ++i;
+                const unsigned long long v = tm[tt];
                 const uint32_t eqb = sbefore[tt] - sbefore[prm.p[i].tile_base];
                 const uint32_t take = S[i].take;
                 const int keep = take > eqb ? (int)(take - eqb) : 0;
-                smask[tt] = (uint32_t)tm | lowest_set_bits((uint32_t)(tm >> 32), keep);
+                smask[tt] = (uint32_t)v | lowest_set_bits((uint32_t)(v >> 32), keep);
             }
             __syncthreads();
-            carry = 0;
-            for (uint32_t b0 = 0; b0 < TT; b0 += blockDim.x) {
-                const uint32_t tt = b0 + tid;
-                const uint32_t c = tt < TT ? (uint32_t)__popc(smask[tt]) : 0u;
-                const uint32_t ex = block_excl_scan(c, s_tmp, &tot) + carry;
-                carry += tot;
-                if (tt < TT)
-                    sbefore[tt] = ex;
-            }
-            __syncthreads();
+            block_scan_chunks(TT, [&](uint32_t e) { return (uint32_t)__popc(smask[e]); }, sbefore, s_tmp);
             if (tid < npop) {
                 const FusedPop &p = prm.p[tid];
                 const uint32_t base = sbefore[p.tile_base];
@@ -690,7 +735,8 @@ __global__ void __launch_bounds__(kFusedThreads) k_fused(const __grid_constant__
 
 size_t fused_smem_bytes(const FusedParams &p)
 {
-    return (size_t)2 * p.total_tiles * 4u + (size_t)(kFusedThreads / 32) * p.warp_buf_words * 4u;
+    const size_t r1 = std::max((size_t)2 * p.total_tiles, (size_t)2 * kHistSmem);
+    return (r1 + (size_t)2 * p.total_tiles + (size_t)(kFusedThreads / 32) * p.warp_buf_words) * 4u;
 }
 
 cudaError_t fused_grid(size_t smem, int *grid)
@@ -706,7 +752,7 @@ cudaError_t fused_grid(size_t smem, int *grid)
         return e;
     if (per < 1)
         return cudaErrorCooperativeLaunchTooLarge;
-    *grid = sms * (per < 2 ? per : 2);
+    *grid = sms;  // one resident block per SM
     return cudaSuccess;
 }
 

@@ -87,9 +87,10 @@ int perm_global_bits(uint32_t n);
 // ---- fused persistent generation kernel (k_fused.cu) -------------------------
 constexpr int kMaxPops = 16;       // populations in one persistent launch
 constexpr int kHistR = 4096;       // buckets of a selection histogram
-constexpr int kFusedThreads = 256;
+constexpr int kFusedThreads = 512;
+constexpr uint32_t kHistSmem = 8192;  // histogram words staged in shared memory per pass
 constexpr int kFusedMaxM = 128;    // orders the fused kernel builds (larger: plain path)
-constexpr uint32_t kFusedMaxTiles = 16384;  // joint tiles of 32 slots (P <= 524288)
+constexpr uint32_t kFusedMaxTiles = 8192;   // joint tiles of 32 slots (P <= 262144)
 
 // Per-population state words of the fused kernel (device memory):
 // hist[2][kHistR] selection histograms by generation parity, ref[3][kHistR]
