@@ -234,10 +234,12 @@ __device__ __forceinline__ void red_release_gpu_add(uint32_t *p, uint32_t v)
 
 // Grid-wide barrier for a cooperative launch with every block resident.
 // `bar` counts arrivals monotonically (zeroed before the launch); `epoch`
-// is the caller's barrier count.  Thread 0 spins with a bounded budget of
-// about two seconds; when it runs out, or another block has already raised
-// an error, ERR_TIMEOUT is recorded and every block returns false so the
-// kernel can exit cleanly instead of hanging.
+// is the caller's barrier count.  Arrival is a release reduction after a
+// gpu-scope fence; thread 0 then polls with acquire loads under a bounded
+// budget of about two seconds; when it runs out, or another block has
+// already raised an error, ERR_TIMEOUT is recorded and every block returns
+// false so the kernel can exit cleanly instead of hanging.  Callers read
+// data written by other blocks through L2 (ld.global.cg or atomics).
 constexpr unsigned long long kBarrierBudgetNs = 2000000000ull;
 
 __device__ __forceinline__ bool grid_barrier(uint32_t *bar, uint32_t nblocks, uint32_t &epoch, uint32_t *err)
@@ -257,7 +259,7 @@ __device__ __forceinline__ bool grid_barrier(uint32_t *bar, uint32_t nblocks, ui
             if ((int32_t)(v - target) >= 0)
                 break;
             if ((++spins & 63u) == 0u) {
-                if (*(volatile uint32_t *)err != 0u) {
+                if (ld_acquire_gpu(err) != 0u) {
                     ok = 0;
                     break;
                 }
@@ -267,9 +269,7 @@ __device__ __forceinline__ bool grid_barrier(uint32_t *bar, uint32_t nblocks, ui
                     break;
                 }
             }
-            __nanosleep(32);
         }
-        __threadfence();
         s_ok = ok;
     }
     __syncthreads();

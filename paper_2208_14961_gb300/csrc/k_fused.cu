@@ -43,7 +43,7 @@ struct PopSel {
     uint32_t sr;          // width exponent of the candidate bucket
     uint32_t exact;
     uint32_t T, take;     // threshold and number of F == T survivors
-    uint32_t base;        // joint survivor count before the first tile of the population
+    uint32_t lb, eb;      // joint (F < T, F == T) counts before the first tile of the population
     uint32_t capn, shiftn;  // histogram parameters of the next generation
 };
 
@@ -150,22 +150,41 @@ __device__ __forceinline__ void block_scan_chunks(uint32_t n, Cnt cnt, uint32_t 
     __syncthreads();
 }
 
-// Slot of survivor number d of a population: binary search over the joint
-// survivor prefix (shared memory), then a select-bit inside the tile.
-__device__ __forceinline__ uint32_t survivor_of(uint32_t d, const FusedPop &p, const PopSel &S, const uint32_t *smask,
-                                                const uint32_t *sbefore, uint32_t *err)
+// Survivor bookkeeping of phase B, per tile t of the joint tile space:
+//   tm[t] = (F < T mask) | (F == T mask) << 32
+//   ex[t] = exclusive prefix over tiles of (popc(lt) << 32 | popc(eq))
+// Within population i (bases lb, eb at its first tile) the survivors before
+// tile t number (lt_before) + min(eq_before, take), and the tile's survivor
+// mask is lt | the lowest (take - eq_before) bits of eq.
+struct Surv {
+    const unsigned long long *tm, *ex;
+};
+
+__device__ __forceinline__ uint32_t surv_before(const Surv &sv, uint32_t tt, const PopSel &S)
+{
+    const unsigned long long e = sv.ex[tt];
+    const uint32_t ltb = (uint32_t)(e >> 32) - S.lb, eqb = (uint32_t)e - S.eb;
+    return ltb + min(eqb, S.take);
+}
+
+// Slot of survivor number d of a population: binary search over the tile
+// prefix, then a select-bit inside the tile.
+__device__ __forceinline__ uint32_t survivor_of(uint32_t d, const FusedPop &p, const PopSel &S, const Surv &sv,
+                                                uint32_t *err)
 {
     const uint32_t tb = p.tile_base;
     uint32_t lo = 0, hi = p.ntiles - 1;
     while (lo < hi) {
         const uint32_t mid = (lo + hi + 1) >> 1;
-        if (sbefore[tb + mid] - S.base <= d)
+        if (surv_before(sv, tb + mid, S) <= d)
             lo = mid;
         else
             hi = mid - 1;
     }
-    const uint32_t mask = smask[tb + lo];
-    const uint32_t r = d - (sbefore[tb + lo] - S.base);
+    const unsigned long long m64 = sv.tm[tb + lo];
+    const uint32_t eqb = min((uint32_t)sv.ex[tb + lo] - S.eb, S.take);
+    const uint32_t mask = (uint32_t)m64 | lowest_set_bits((uint32_t)(m64 >> 32), (int)(S.take - eqb));
+    const uint32_t r = d - surv_before(sv, tb + lo, S);
     const uint32_t P = (uint32_t)(4 * p.N);
     if (r >= (uint32_t)__popc(mask)) {
         atomicOr(err, ERR_INTERNAL);
@@ -210,17 +229,15 @@ __device__ __forceinline__ uint32_t fitness_regs(const uint32_t (&c)[M])
 // offspring O_{1 + half}; its parent is P_1 (half 0) or P_2 (half 1).
 // ---------------------------------------------------------------------------
 template <int M>
-__device__ __forceinline__ void pair_thread(const FusedPop &p, const PopSel &S, int src, uint32_t gen, uint32_t tch,
-                                            uint32_t k, int half, bool valid, const uint32_t *smask,
-                                            const uint32_t *sbefore, uint32_t *err, uint32_t &f_par,
-                                            uint32_t &slot_par, uint32_t &f_child, uint32_t &slot_child)
+__device__ __forceinline__ void pair_thread(const FusedPop &p, const PopSel &S, int src, uint32_t gen, uint32_t d,
+                                            uint32_t k, int half, bool valid, const Surv &sv, uint32_t *err,
+                                            uint32_t &f_par, uint32_t &slot_par, uint32_t &f_child,
+                                            uint32_t &slot_child)
 {
     const uint32_t N = (uint32_t)p.N;
     uint32_t s_mine = 0;
-    if (valid) {
-        const uint32_t d = __ldg(p.perm + (size_t)tch * 2u * N + k + (half ? N : 0u));
-        s_mine = survivor_of(d, p, S, smask, sbefore, err);
-    }
+    if (valid)
+        s_mine = survivor_of(d, p, S, sv, err);
     const uint32_t s_other = __shfl_xor_sync(FULL, s_mine, 1);
     if (!valid)
         return;
@@ -315,8 +332,8 @@ __device__ __forceinline__ void pair_thread(const FusedPop &p, const PopSel &S, 
 // ---------------------------------------------------------------------------
 template <int W>
 __device__ void pair_warp(const FusedPop &p, const PopSel &S, int src, uint32_t gen, uint32_t tch, uint32_t k,
-                          const uint32_t *smask, const uint32_t *sbefore, uint32_t *err, uint32_t *buf,
-                          uint32_t *hist_next, uint32_t *orv_next, unsigned long long *best)
+                          const Surv &sv, uint32_t *err, uint32_t *buf, uint32_t *hist_next, uint32_t *orv_next,
+                          unsigned long long *best)
 {
     const int lane = threadIdx.x & 31;
     const int m = p.m;
@@ -325,8 +342,8 @@ __device__ void pair_warp(const FusedPop &p, const PopSel &S, int src, uint32_t 
     int c = 1;
     if (lane == 0) {
         const uint32_t *row = p.perm + (size_t)tch * 2u * N;
-        s1 = survivor_of(__ldg(row + k), p, S, smask, sbefore, err);
-        s2 = survivor_of(__ldg(row + k + N), p, S, smask, sbefore, err);
+        s1 = survivor_of(__ldg(row + k), p, S, sv, err);
+        s2 = survivor_of(__ldg(row + k + N), p, S, sv, err);
         F1 = ldcg32(p.fit[src] + s1);
         F2 = ldcg32(p.fit[src] + s2);
         c = cut_point(p.seed, p.pop_id, gen, k, m);
@@ -407,6 +424,59 @@ __device__ void pair_warp(const FusedPop &p, const PopSel &S, int src, uint32_t 
     __syncwarp();
 }
 
+__device__ __forceinline__ unsigned long long warp_incl_scan_u64(unsigned long long v, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(FULL, v, o);
+        if (lane >= o)
+            v += t;
+    }
+    return v;
+}
+
+// Exclusive prefix of cnt(e) over e in [0, n) into out[e] (shared memory),
+// 64-bit, one contiguous chunk per thread, one block-wide scan.
+template <class Cnt>
+__device__ __forceinline__ void block_scan_chunks_u64(uint32_t n, Cnt cnt, unsigned long long *out,
+                                                      unsigned long long *tmp)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
+    const uint32_t lo = min(n, threadIdx.x * per), hi = min(n, lo + per);
+    unsigned long long sum = 0;
+    for (uint32_t e = lo; e < hi; ++e)
+        sum += cnt(e);
+    const unsigned long long inc = warp_incl_scan_u64(sum, lane);
+    if (lane == 31)
+        tmp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned long long w = lane < nw ? tmp[lane] : 0ull;
+        const unsigned long long wi = warp_incl_scan_u64(w, lane);
+        if (lane < nw)
+            tmp[lane] = wi - w;
+    }
+    __syncthreads();
+    unsigned long long ex = tmp[warp] + inc - sum;
+    for (uint32_t e = lo; e < hi; ++e) {
+        const unsigned long long c = cnt(e);
+        out[e] = ex;
+        ex += c;
+    }
+    __syncthreads();
+}
+
+// Population owning joint index x given increasing bases (linear: npop <= 16).
+template <class Base>
+__device__ __forceinline__ int owner_of(uint32_t x, int npop, Base base)
+{
+    int i = 0;
+    while (i + 1 < npop && x >= base(i + 1))
+        ++i;
+    return i;
+}
+
 } // namespace
 
 __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constant__ FusedParams prm)
@@ -414,6 +484,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
     extern __shared__ __align__(16) uint32_t dyn[];
     __shared__ PopSel S[kMaxPops];
     __shared__ uint32_t s_tmp[33];
+    __shared__ unsigned long long s_tmp64[32];
     __shared__ uint32_t hoff[kMaxPops];
     __shared__ int s_flag;
 
@@ -421,19 +492,23 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
     const int npop = prm.npop;
     const uint32_t nblocks = gridDim.x;
     const uint32_t gtid = blockIdx.x * blockDim.x + tid, gthreads = nblocks * blockDim.x;
-    const uint32_t gwarp = gtid >> 5, gwarps = gthreads >> 5;
-    // shared layout: [region shared by the tile masks (phase B) and the staged
-    // histograms (phase A)] [survivor masks] [survivor prefix] [warp buffers]
-    const uint32_t r1 = max(2u * prm.total_tiles, 2u * kHistSmem);
+    // warps enumerated across blocks first, so consecutive work items land on
+    // different SMs
+    const uint32_t gwarp = (uint32_t)wib * nblocks + blockIdx.x, gwarps = gthreads >> 5;
+    const uint32_t TT = prm.total_tiles;
+    // shared layout: [tile masks and their prefix (phase B) | staged
+    // histograms (phase A)] [warp buffers]
+    const uint32_t r1 = max(4u * TT, 2u * kHistSmem);
     unsigned long long *tm = reinterpret_cast<unsigned long long *>(dyn);
+    unsigned long long *ex = tm + TT;
     uint32_t *hcnt = dyn, *hpre = dyn + kHistSmem;
-    uint32_t *smask = dyn + r1;
-    uint32_t *sbefore = smask + prm.total_tiles;
-    uint32_t *wbuf = sbefore + prm.total_tiles + wib * prm.warp_buf_words;
+    uint32_t *wbuf = dyn + r1 + wib * prm.warp_buf_words;
+    const Surv sv{tm, ex};
     uint32_t *err = prm.err;
     uint32_t epoch = 0;
     int src = prm.src;
     int done = 0;
+    auto tile_base = [&](int i) { return prm.p[i].tile_base; };
 
     // ---- pre-pass: max and OR of the current fitness of every population -----
     {
@@ -469,7 +544,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             const uint32_t P = (uint32_t)(4 * p.N);
             uint32_t *h = hist_of(p, par0);
             const uint32_t cap = S[i].cap, sh = S[i].shift;
-            // uniform trip count per warp so the warp-collective add stays converged
+            // uniform trip count so the warp-collective add stays converged
             const uint32_t span = (P + 31u) & ~31u;
             for (uint32_t q = gtid; q < ((span + gthreads - 1) / gthreads) * gthreads; q += gthreads) {
                 const bool in = q < P;
@@ -487,9 +562,22 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
         const int par = (int)(gen & 1u);
 
         // ---- phase A: threshold of the 2N smallest ---------------------------------
+        // first tile of this warp: its fitness is loaded now, with the histograms
+        uint32_t f_pre = 0;
+        int i_pre = 0;
+        if (gwarp < TT) {
+            i_pre = owner_of(gwarp, npop, tile_base);
+            const FusedPop &p = prm.p[i_pre];
+            const uint32_t q = (gwarp - p.tile_base) * 32u + lane;
+            f_pre = q < (uint32_t)(4 * p.N) ? ldcg32(p.fit[src] + q) : 0u;
+        }
+        if (tid < npop) {
+            PopSel &s = S[tid];
+            s.v = ctz_or(ldcg32(stat_of(prm.p[tid]) + 1 + par));
+            s.need = 0xFFFFFFFFu;  // marks "crossing not found"
+        }
         for (int i = 0; i < npop; ++i) {
-            const FusedPop &p = prm.p[i];
-            uint32_t *hn = hist_of(p, par ^ 1);
+            uint32_t *hn = hist_of(prm.p[i], par ^ 1);
             for (uint32_t e = gtid; e < (uint32_t)kHistR; e += gthreads)
                 hn[e] = 0u;
         }
@@ -497,13 +585,6 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             const FusedPop &p = prm.p[tid];
             stat_of(p)[1 + (par ^ 1)] = 0u;
             p.traj[(gen - 1u) % (uint32_t)p.traj_cap] = ~0ull;
-        }
-        if (tid < npop) {
-            PopSel &s = S[tid];
-            s.v = ctz_or(ldcg32(stat_of(prm.p[tid]) + 1 + par));
-            s.sr = s.shift;
-            s.exact = s.shift <= s.v ? 1u : 0u;
-            s.need = 0xFFFFFFFFu;  // marks "crossing not found"
         }
         // histograms staged in shared memory (groups of populations that fit),
         // scanned in one block-wide pass, crossing of 2N located per population
@@ -514,10 +595,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                 const uint32_t nb = (S[i1].cap >> S[i1].shift) + 1u;
                 if (i1 > i0 && off + nb > kHistSmem)
                     break;
-                hoff[i1] = off;
+                if (tid == 0)
+                    hoff[i1] = off;
                 off += nb;
                 ++i1;
             }
+            __syncthreads();
             for (uint32_t e = tid; e < off; e += blockDim.x) {
                 int i = i0;
                 while (i + 1 < i1 && e >= hoff[i + 1])
@@ -531,21 +614,27 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                 while (i + 1 < i1 && e >= hoff[i + 1])
                     ++i;
                 const uint32_t need = (uint32_t)(2 * prm.p[i].N);
-                const uint32_t ex = hpre[e] - hpre[hoff[i]], h = hcnt[e];
-                if (h && ex < need && need <= ex + h) {
+                const uint32_t x = hpre[e] - hpre[hoff[i]], h = hcnt[e];
+                if (h && x < need && need <= x + h) {
                     S[i].lo = (e - hoff[i]) << S[i].shift;
-                    S[i].need = need - ex;
+                    S[i].need = need - x;
                 }
             }
             __syncthreads();
             i0 = i1;
         }
-        if (tid < npop && S[tid].need == 0xFFFFFFFFu) {
-            atomicOr(err, ERR_INTERNAL);
-            S[tid].lo = 0;
-            S[tid].need = 1;
+        if (tid < npop) {
+            PopSel &s = S[tid];
+            if (s.need == 0xFFFFFFFFu) {
+                atomicOr(err, ERR_INTERNAL);
+                s.lo = 0;
+                s.need = 1;
+            }
+            s.sr = s.shift;
+            s.exact = s.shift <= s.v ? 1u : 0u;
         }
         __syncthreads();
+        // refinement passes while a candidate bucket may hold several values
         for (;;) {
             if (tid == 0) {
                 int any = 0;
@@ -602,58 +691,67 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             s.shiftn = max(s.v, shift_for(s.T));
         }
         __syncthreads();
-        // tile masks
-        for (int i = 0; i < npop; ++i) {
+        // tile masks: F < T and F == T per 32 slots
+        for (uint32_t tl = gwarp; tl < TT; tl += gwarps) {
+            const int i = tl == gwarp ? i_pre : owner_of(tl, npop, tile_base);
             const FusedPop &p = prm.p[i];
             const uint32_t P = (uint32_t)(4 * p.N), T = S[i].T;
-            for (uint32_t tl = gwarp; tl < p.ntiles; tl += gwarps) {
-                const uint32_t q = tl * 32u + lane;
-                const uint32_t f = q < P ? ldcg32(p.fit[src] + q) : 0u;
-                const uint32_t lt = __ballot_sync(FULL, q < P && f < T);
-                const uint32_t eq = __ballot_sync(FULL, q < P && f == T);
-                if (lane == 0)
-                    p.tmask[tl] = (unsigned long long)lt | ((unsigned long long)eq << 32);
-            }
+            const uint32_t q = (tl - p.tile_base) * 32u + lane;
+            const uint32_t f = tl == gwarp ? f_pre : (q < P ? ldcg32(p.fit[src] + q) : 0u);
+            const uint32_t lt = __ballot_sync(FULL, q < P && f < T);
+            const uint32_t eq = __ballot_sync(FULL, q < P && f == T);
+            if (lane == 0)
+                p.tmask[tl - p.tile_base] = (unsigned long long)lt | ((unsigned long long)eq << 32);
         }
         if (!grid_barrier(prm.bar, nblocks, epoch, err))
             return;
 
         // ---- phase B: survivors in slot order, then build ------------------------
-        {
-            const uint32_t TT = prm.total_tiles;
-            for (uint32_t tt = tid; tt < TT; tt += blockDim.x) {
-                int i = 0;
-                while (i + 1 < npop && tt >= prm.p[i + 1].tile_base)
-                    ++i;
-                tm[tt] = ldcg64(prm.p[i].tmask + (tt - prm.p[i].tile_base));
+        // the survivor orders of this warp's first work item are fetched first
+        uint32_t d_pre = 0;
+        const uint32_t nwork_t = prm.thread_slots >> 5;
+        if (gwarp < nwork_t) {
+            const uint32_t u = gwarp * 32u + (uint32_t)lane;
+            int i = -1;
+            for (int j = 0; j < npop; ++j)
+                if (prm.p[j].m <= 32 && u >= prm.p[j].work_base)
+                    i = (i < 0 || prm.p[j].work_base >= prm.p[i].work_base) ? j : i;
+            if (i >= 0) {
+                const FusedPop &p = prm.p[i];
+                const uint32_t local = u - p.work_base, k = local >> 1;
+                if (k < (uint32_t)p.N)
+                    d_pre = __ldg(p.perm + (size_t)t * 2u * (uint32_t)p.N + k + ((local & 1u) ? (uint32_t)p.N : 0u));
             }
-            __syncthreads();
-            block_scan_chunks(TT, [&](uint32_t e) { return (uint32_t)__popc((uint32_t)(tm[e] >> 32)); }, sbefore,
-                              s_tmp);
-            for (uint32_t tt = tid; tt < TT; tt += blockDim.x) {
-                int i = 0;
-                while (i + 1 < npop && tt >= prm.p[i + 1].tile_base)
-                    ++i;
-                const unsigned long long v = tm[tt];
-                const uint32_t eqb = sbefore[tt] - sbefore[prm.p[i].tile_base];
-                const uint32_t take = S[i].take;
-                const int keep = take > eqb ? (int)(take - eqb) : 0;
-                smask[tt] = (uint32_t)v | lowest_set_bits((uint32_t)(v >> 32), keep);
-            }
-            __syncthreads();
-            block_scan_chunks(TT, [&](uint32_t e) { return (uint32_t)__popc(smask[e]); }, sbefore, s_tmp);
-            if (tid < npop) {
-                const FusedPop &p = prm.p[tid];
-                const uint32_t base = sbefore[p.tile_base];
-                const uint32_t last = p.tile_base + p.ntiles - 1u;
-                S[tid].base = base;
-                if (sbefore[last] + (uint32_t)__popc(smask[last]) - base != (uint32_t)(2 * p.N))
-                    atomicOr(err, ERR_INTERNAL);
-            }
-            __syncthreads();
         }
+        for (uint32_t tt = tid; tt < TT; tt += blockDim.x) {
+            const int i = owner_of(tt, npop, tile_base);
+            tm[tt] = ldcg64(prm.p[i].tmask + (tt - prm.p[i].tile_base));
+        }
+        __syncthreads();
+        block_scan_chunks_u64(
+            TT,
+            [&](uint32_t e) {
+                const unsigned long long v = tm[e];
+                return ((unsigned long long)__popc((uint32_t)v) << 32) | (unsigned long long)__popc((uint32_t)(v >> 32));
+            },
+            ex, s_tmp64);
+        if (tid < npop) {
+            const FusedPop &p = prm.p[tid];
+            PopSel &s = S[tid];
+            const unsigned long long e0 = ex[p.tile_base];
+            s.lb = (uint32_t)(e0 >> 32);
+            s.eb = (uint32_t)e0;
+            const uint32_t last = p.tile_base + p.ntiles - 1u;
+            const unsigned long long el = ex[last], vl = tm[last];
+            const uint32_t lt_all = (uint32_t)(el >> 32) - s.lb + (uint32_t)__popc((uint32_t)vl);
+            const uint32_t eq_all = (uint32_t)el - s.eb + (uint32_t)__popc((uint32_t)(vl >> 32));
+            if (lt_all + min(eq_all, s.take) != (uint32_t)(2 * p.N) || s.take > eq_all)
+                atomicOr(err, ERR_INTERNAL);
+        }
+        __syncthreads();
         // m <= 32: two threads per pair
-        for (uint32_t u = gtid & ~31u; u < prm.thread_slots; u += gthreads) {
+        for (uint32_t w = gwarp; w < nwork_t; w += gwarps) {
+            const uint32_t u = w * 32u;
             // the population whose (32-aligned) thread range holds this warp
             int i = -1;
             for (int j = 0; j < npop; ++j)
@@ -664,19 +762,21 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             const uint32_t k = local >> 1;
             const int half = (int)(local & 1u);
             const bool valid = i >= 0 && k < (uint32_t)p.N;
+            uint32_t d = d_pre;
+            if (w != gwarp && valid)
+                d = __ldg(p.perm + (size_t)t * 2u * (uint32_t)p.N + k + (half ? (uint32_t)p.N : 0u));
             uint32_t fpar = 0, spar = 0, fch = 0, sch = 0;
+            const PopSel &s = S[i < 0 ? 0 : i];
             switch (p.m) {
-#define HADGA_PT(MM)                                                                                       \
-    case MM:                                                                                               \
-        pair_thread<MM>(p, S[i < 0 ? 0 : i], src, gen, (uint32_t)t, k, half, valid, smask, sbefore, err,  \
-                        fpar, spar, fch, sch);                                                             \
+#define HADGA_PT(MM)                                                                                        \
+    case MM:                                                                                                \
+        pair_thread<MM>(p, s, src, gen, d, k, half, valid, sv, err, fpar, spar, fch, sch);                  \
         break;
                 HADGA_PT(4) HADGA_PT(8) HADGA_PT(12) HADGA_PT(16) HADGA_PT(20) HADGA_PT(24) HADGA_PT(28) HADGA_PT(32)
 #undef HADGA_PT
             default:
                 break;
             }
-            const PopSel &s = S[i < 0 ? 0 : i];
             uint32_t *hn = hist_of(p, par ^ 1);
             warp_hist_add(hn, valid && fpar <= s.capn, fpar >> s.shiftn);
             warp_hist_add(hn, valid && fch <= s.capn, fch >> s.shiftn);
@@ -707,9 +807,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             uint32_t *on = stat_of(p) + 1 + (par ^ 1);
             unsigned long long *bk = p.traj + (gen - 1u) % (uint32_t)p.traj_cap;
             switch (p.W) {
-            case 2: pair_warp<2>(p, S[i], src, gen, (uint32_t)t, k, smask, sbefore, err, wbuf, hn, on, bk); break;
-            case 3: pair_warp<3>(p, S[i], src, gen, (uint32_t)t, k, smask, sbefore, err, wbuf, hn, on, bk); break;
-            case 4: pair_warp<4>(p, S[i], src, gen, (uint32_t)t, k, smask, sbefore, err, wbuf, hn, on, bk); break;
+            case 2: pair_warp<2>(p, S[i], src, gen, (uint32_t)t, k, sv, err, wbuf, hn, on, bk); break;
+            case 3: pair_warp<3>(p, S[i], src, gen, (uint32_t)t, k, sv, err, wbuf, hn, on, bk); break;
+            case 4: pair_warp<4>(p, S[i], src, gen, (uint32_t)t, k, sv, err, wbuf, hn, on, bk); break;
             default: break;
             }
         }
@@ -735,8 +835,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
 
 size_t fused_smem_bytes(const FusedParams &p)
 {
-    const size_t r1 = std::max((size_t)2 * p.total_tiles, (size_t)2 * kHistSmem);
-    return (r1 + (size_t)2 * p.total_tiles + (size_t)(kFusedThreads / 32) * p.warp_buf_words) * 4u;
+    const size_t r1 = std::max((size_t)4 * p.total_tiles, (size_t)2 * kHistSmem);
+    return (r1 + (size_t)(kFusedThreads / 32) * p.warp_buf_words) * 4u;
 }
 
 cudaError_t fused_grid(size_t smem, int *grid)
