@@ -45,6 +45,9 @@ struct PopSel {
     uint32_t T, take;     // threshold and number of F == T survivors
     uint32_t lb, eb;      // joint (F < T, F == T) counts before the first tile of the population
     uint32_t capn, shiftn;  // histogram parameters of the next generation
+    uint32_t boff;          // offset of this population's block histogram (~0: none)
+    uint32_t bor;           // block OR of the new fitness values
+    unsigned long long bbest;  // block minimum of the new best keys
 };
 
 __device__ __forceinline__ uint32_t ldcg32(const uint32_t *p) { return __ldcg(p); }
@@ -331,9 +334,8 @@ __device__ __forceinline__ void pair_thread(const FusedPop &p, const PopSel &S, 
 // 32 < m <= 128: a warp per pair, matrices staged in shared memory.
 // ---------------------------------------------------------------------------
 template <int W>
-__device__ void pair_warp(const FusedPop &p, const PopSel &S, int src, uint32_t gen, uint32_t tch, uint32_t k,
-                          const Surv &sv, uint32_t *err, uint32_t *buf, uint32_t *hist_next, uint32_t *orv_next,
-                          unsigned long long *best)
+__device__ void pair_warp(const FusedPop &p, PopSel &S, int src, uint32_t gen, uint32_t tch, uint32_t k,
+                          const Surv &sv, uint32_t *err, uint32_t *buf, uint32_t *hist_next, uint32_t *bhist)
 {
     const int lane = threadIdx.x & 31;
     const int m = p.m;
@@ -408,18 +410,18 @@ __device__ void pair_warp(const FusedPop &p, const PopSel &S, int src, uint32_t 
     }
     if (lane == 0) {
         const uint32_t fv[4] = {F1, F2, fc[0], fc[1]};
-        const uint32_t sv[4] = {k, k + N, 2u * N + k, 3u * N + k};
+        const uint32_t slots[4] = {k, k + N, 2u * N + k, 3u * N + k};
         unsigned long long bk = ~0ull;
         uint32_t orr = 0;
         for (int i = 0; i < 4; ++i) {
             if (fv[i] <= S.capn)
-                atomicAdd(hist_next + (fv[i] >> S.shiftn), 1u);
+                atomicAdd((S.boff != 0xFFFFFFFFu ? bhist + S.boff : hist_next) + (fv[i] >> S.shiftn), 1u);
             orr |= fv[i];
-            const unsigned long long key = ((unsigned long long)fv[i] << 32) | sv[i];
+            const unsigned long long key = ((unsigned long long)fv[i] << 32) | slots[i];
             bk = key < bk ? key : bk;
         }
-        atomicOr(orv_next, orr);
-        atomicMin(best, bk);
+        atomicOr(&S.bor, orr);
+        atomicMin(&S.bbest, bk);
     }
     __syncwarp();
 }
@@ -502,7 +504,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
     unsigned long long *tm = reinterpret_cast<unsigned long long *>(dyn);
     unsigned long long *ex = tm + TT;
     uint32_t *hcnt = dyn, *hpre = dyn + kHistSmem;
-    uint32_t *wbuf = dyn + r1 + wib * prm.warp_buf_words;
+    uint32_t *bhist = dyn + r1;  // block-local histograms of the next generation
+    uint32_t *wbuf = bhist + kHistSmem + wib * prm.warp_buf_words;
     const Surv sv{tm, ex};
     uint32_t *err = prm.err;
     uint32_t epoch = 0;
@@ -689,8 +692,19 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             s.take = s.need;
             s.capn = s.T;
             s.shiftn = max(s.v, shift_for(s.T));
+            s.bor = 0u;
+            s.bbest = ~0ull;
         }
         __syncthreads();
+        if (tid == 0) {
+            uint32_t off = 0;
+            for (int i = 0; i < npop; ++i) {
+                const uint32_t nb = (S[i].capn >> S[i].shiftn) + 1u;
+                S[i].boff = off + nb <= kHistSmem ? off : 0xFFFFFFFFu;
+                if (off + nb <= kHistSmem)
+                    off += nb;
+            }
+        }
         // tile masks: F < T and F == T per 32 slots
         for (uint32_t tl = gwarp; tl < TT; tl += gwarps) {
             const int i = tl == gwarp ? i_pre : owner_of(tl, npop, tile_base);
@@ -723,10 +737,25 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                     d_pre = __ldg(p.perm + (size_t)t * 2u * (uint32_t)p.N + k + ((local & 1u) ? (uint32_t)p.N : 0u));
             }
         }
-        for (uint32_t tt = tid; tt < TT; tt += blockDim.x) {
-            const int i = owner_of(tt, npop, tile_base);
-            tm[tt] = ldcg64(prm.p[i].tmask + (tt - prm.p[i].tile_base));
+        for (uint32_t t0 = tid; t0 < TT; t0 += 4u * blockDim.x) {
+            unsigned long long v[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const uint32_t tt = t0 + (uint32_t)r * blockDim.x;
+                if (tt < TT) {
+                    const int i = owner_of(tt, npop, tile_base);
+                    v[r] = ldcg64(prm.p[i].tmask + (tt - prm.p[i].tile_base));
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const uint32_t tt = t0 + (uint32_t)r * blockDim.x;
+                if (tt < TT)
+                    tm[tt] = v[r];
+            }
         }
+        for (uint32_t e = tid; e < kHistSmem; e += blockDim.x)
+            bhist[e] = 0u;
         __syncthreads();
         block_scan_chunks_u64(
             TT,
@@ -777,9 +806,17 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             default:
                 break;
             }
-            uint32_t *hn = hist_of(p, par ^ 1);
-            warp_hist_add(hn, valid && fpar <= s.capn, fpar >> s.shiftn);
-            warp_hist_add(hn, valid && fch <= s.capn, fch >> s.shiftn);
+            if (s.boff != 0xFFFFFFFFu) {
+                uint32_t *bh = bhist + s.boff;
+                if (valid && fpar <= s.capn)
+                    atomicAdd(bh + (fpar >> s.shiftn), 1u);
+                if (valid && fch <= s.capn)
+                    atomicAdd(bh + (fch >> s.shiftn), 1u);
+            } else {
+                uint32_t *hn = hist_of(p, par ^ 1);
+                warp_hist_add(hn, valid && fpar <= s.capn, fpar >> s.shiftn);
+                warp_hist_add(hn, valid && fch <= s.capn, fch >> s.shiftn);
+            }
             const uint32_t orr = warp_or(valid ? (fpar | fch) : 0u);
             unsigned long long key = ~0ull;
             if (valid) {
@@ -789,8 +826,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             }
             key = warp_min_u64(key);
             if (lane == 0 && i >= 0) {
-                atomicOr(stat_of(p) + 1 + (par ^ 1), orr);
-                atomicMin(p.traj + (gen - 1u) % (uint32_t)p.traj_cap, key);
+                atomicOr(&S[i].bor, orr);
+                atomicMin(&S[i].bbest, key);
             }
         }
         // 32 < m <= 128: a warp per pair
@@ -804,14 +841,33 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             const FusedPop &p = prm.p[i];
             const uint32_t k = pr - p.work_base;
             uint32_t *hn = hist_of(p, par ^ 1);
-            uint32_t *on = stat_of(p) + 1 + (par ^ 1);
-            unsigned long long *bk = p.traj + (gen - 1u) % (uint32_t)p.traj_cap;
             switch (p.W) {
-            case 2: pair_warp<2>(p, S[i], src, gen, (uint32_t)t, k, sv, err, wbuf, hn, on, bk); break;
-            case 3: pair_warp<3>(p, S[i], src, gen, (uint32_t)t, k, sv, err, wbuf, hn, on, bk); break;
-            case 4: pair_warp<4>(p, S[i], src, gen, (uint32_t)t, k, sv, err, wbuf, hn, on, bk); break;
+            case 2: pair_warp<2>(p, S[i], src, gen, (uint32_t)t, k, sv, err, wbuf, hn, bhist); break;
+            case 3: pair_warp<3>(p, S[i], src, gen, (uint32_t)t, k, sv, err, wbuf, hn, bhist); break;
+            case 4: pair_warp<4>(p, S[i], src, gen, (uint32_t)t, k, sv, err, wbuf, hn, bhist); break;
             default: break;
             }
+        }
+        // one flush per block of its histogram counts, OR word and best key
+        __syncthreads();
+        for (int i = 0; i < npop; ++i) {
+            const uint32_t bo = S[i].boff;
+            if (bo == 0xFFFFFFFFu)
+                continue;
+            const uint32_t nb = (S[i].capn >> S[i].shiftn) + 1u;
+            uint32_t *hn = hist_of(prm.p[i], par ^ 1);
+            for (uint32_t e = tid; e < nb; e += blockDim.x) {
+                const uint32_t c = bhist[bo + e];
+                if (c)
+                    atomicAdd(hn + e, c);
+            }
+        }
+        if (tid < npop) {
+            const FusedPop &p = prm.p[tid];
+            if (S[tid].bor)
+                atomicOr(stat_of(p) + 1 + (par ^ 1), S[tid].bor);
+            if (S[tid].bbest != ~0ull)
+                atomicMin(p.traj + (gen - 1u) % (uint32_t)p.traj_cap, S[tid].bbest);
         }
         if (!grid_barrier(prm.bar, nblocks, epoch, err))
             return;
@@ -836,7 +892,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
 size_t fused_smem_bytes(const FusedParams &p)
 {
     const size_t r1 = std::max((size_t)4 * p.total_tiles, (size_t)2 * kHistSmem);
-    return (r1 + (size_t)(kFusedThreads / 32) * p.warp_buf_words) * 4u;
+    return (r1 + kHistSmem + (size_t)(kFusedThreads / 32) * p.warp_buf_words) * 4u;
 }
 
 cudaError_t fused_grid(size_t smem, int *grid)
