@@ -186,6 +186,31 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *tmp, u
 // shared memory.  Lane a pairs column a with (a + s) mod m for s = 1..m/2,
 // the s = m/2 pair only when a < m/2, so each unordered pair is visited once.
 // ---------------------------------------------------------------------------
+// One column of W words from shared memory with the widest aligned vector
+// loads (consecutive lanes reading consecutive columns stay bank-conflict
+// free; `col` is 4W-byte aligned when W is even).
+template <int W>
+__device__ __forceinline__ void load_col(const uint32_t *col, uint32_t (&c)[W])
+{
+    if (W % 4 == 0) {
+#pragma unroll
+        for (int v = 0; v < W / 4; ++v) {
+            const uint4 x = reinterpret_cast<const uint4 *>(col)[v];
+            c[4 * v] = x.x, c[4 * v + 1] = x.y, c[4 * v + 2] = x.z, c[4 * v + 3] = x.w;
+        }
+    } else if (W % 2 == 0) {
+#pragma unroll
+        for (int v = 0; v < W / 2; ++v) {
+            const uint2 x = reinterpret_cast<const uint2 *>(col)[v];
+            c[2 * v] = x.x, c[2 * v + 1] = x.y;
+        }
+    } else {
+#pragma unroll
+        for (int w = 0; w < W; ++w)
+            c[w] = col[w];
+    }
+}
+
 template <int W, int KIND>
 __device__ __forceinline__ uint32_t warp_fitness_cols(const uint32_t *cols, int m, int lane)
 {
@@ -193,17 +218,17 @@ __device__ __forceinline__ uint32_t warp_fitness_cols(const uint32_t *cols, int 
     const int half = m >> 1;
     for (int a = lane; a < m; a += 32) {
         uint32_t ca[W];
-#pragma unroll
-        for (int w = 0; w < W; ++w)
-            ca[w] = cols[a * W + w];
+        load_col<W>(cols + a * W, ca);
         const int smax = a < half ? half : half - 1;
         int b = a;
         for (int s = 1; s <= smax; ++s) {
             b = (b + 1 == m) ? 0 : b + 1;
+            uint32_t cb[W];
+            load_col<W>(cols + b * W, cb);
             int d = 0;
 #pragma unroll
             for (int w = 0; w < W; ++w)
-                d += __popc(ca[w] ^ cols[b * W + w]);
+                d += __popc(ca[w] ^ cb[w]);
             acc += fit_term<KIND>(m - 2 * d);
         }
     }
