@@ -259,8 +259,9 @@ __device__ __forceinline__ void red_release_gpu_add(uint32_t *p, uint32_t v)
 
 // Grid-wide barrier for a cooperative launch with every block resident.
 // `bar` counts arrivals monotonically (zeroed before the launch); `epoch`
-// is the caller's barrier count.  Arrival is a release reduction after a
-// gpu-scope fence; thread 0 then polls with acquire loads under a bounded
+// is the caller's barrier count.  Arrival is a gpu-scope release reduction
+// (cumulative over the block's writes ordered by the preceding bar.sync);
+// thread 0 then polls with acquire loads under a bounded
 // budget of about two seconds; when it runs out, or another block has
 // already raised an error, ERR_TIMEOUT is recorded and every block returns
 // false so the kernel can exit cleanly instead of hanging.  Callers read
@@ -274,7 +275,7 @@ __device__ __forceinline__ bool grid_barrier(uint32_t *bar, uint32_t nblocks, ui
     epoch += 1u;
     if (threadIdx.x == 0) {
         const uint32_t target = epoch * nblocks;
-        __threadfence();
+        // the block's writes precede this release through the bar.sync above
         red_release_gpu_add(bar, 1u);
         int ok = 1;
         const unsigned long long t0 = global_ns();

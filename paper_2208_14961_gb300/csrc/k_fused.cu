@@ -46,6 +46,7 @@ struct PopSel {
     uint32_t lb, eb;      // joint (F < T, F == T) counts before the first tile of the population
     uint32_t capn, shiftn;  // histogram parameters of the next generation
     uint32_t boff;          // offset of this population's block histogram (~0: none)
+    uint32_t toff;          // offset of this population's survivor table
     uint32_t bor;           // block OR of the new fitness values
     unsigned long long bbest;  // block minimum of the new best keys
 };
@@ -161,6 +162,7 @@ __device__ __forceinline__ void block_scan_chunks(uint32_t n, Cnt cnt, uint32_t 
 // mask is lt | the lowest (take - eq_before) bits of eq.
 struct Surv {
     const unsigned long long *tm, *ex;
+    const uint32_t *tab;  // survivor number -> slot, per population at S.toff (or null)
 };
 
 __device__ __forceinline__ uint32_t surv_before(const Surv &sv, uint32_t tt, const PopSel &S)
@@ -175,6 +177,8 @@ __device__ __forceinline__ uint32_t surv_before(const Surv &sv, uint32_t tt, con
 __device__ __forceinline__ uint32_t survivor_of(uint32_t d, const FusedPop &p, const PopSel &S, const Surv &sv,
                                                 uint32_t *err)
 {
+    if (sv.tab)
+        return sv.tab[S.toff + d];
     const uint32_t tb = p.tile_base;
     uint32_t lo = 0, hi = p.ntiles - 1;
     while (lo < hi) {
@@ -217,14 +221,18 @@ struct Draws {
 template <int M, int KIND>
 __device__ __forceinline__ uint32_t fitness_regs(const uint32_t (&c)[M])
 {
-    uint32_t acc = 0;
+    // four independent partial sums keep the popcount pipe busy
+    uint32_t acc[4] = {0u, 0u, 0u, 0u};
+    int n = 0;
 #pragma unroll
     for (int i = 0; i < M; ++i) {
 #pragma unroll
-        for (int j = i + 1; j < M; ++j)
-            acc += fit_term<KIND>(M - 2 * __popc(c[i] ^ c[j]));
+        for (int j = i + 1; j < M; ++j) {
+            acc[n & 3] += fit_term<KIND>(M - 2 * __popc(c[i] ^ c[j]));
+            ++n;
+        }
     }
-    return fit_finish<KIND>(acc);
+    return fit_finish<KIND>((acc[0] + acc[1]) + (acc[2] + acc[3]));
 }
 
 // ---------------------------------------------------------------------------
@@ -505,8 +513,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
     unsigned long long *ex = tm + TT;
     uint32_t *hcnt = dyn, *hpre = dyn + kHistSmem;
     uint32_t *bhist = dyn + r1;  // block-local histograms of the next generation
-    uint32_t *wbuf = bhist + kHistSmem + wib * prm.warp_buf_words;
-    const Surv sv{tm, ex};
+    uint32_t *tab = bhist + kHistSmem;  // survivor tables (prm.tab_words words, 0: binary search)
+    uint32_t *wbuf = tab + prm.tab_words + wib * prm.warp_buf_words;
+    const Surv sv{tm, ex, prm.tab_words ? tab : nullptr};
     uint32_t *err = prm.err;
     uint32_t epoch = 0;
     int src = prm.src;
@@ -626,6 +635,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             __syncthreads();
             i0 = i1;
         }
+        if (tid == 0)
+            s_flag = 0;
         if (tid < npop) {
             PopSel &s = S[tid];
             if (s.need == 0xFFFFFFFFu) {
@@ -637,17 +648,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             s.exact = s.shift <= s.v ? 1u : 0u;
         }
         __syncthreads();
+        if (tid < npop && !S[tid].exact)
+            atomicOr(&s_flag, 1);
+        __syncthreads();
         // refinement passes while a candidate bucket may hold several values
-        for (;;) {
-            if (tid == 0) {
-                int any = 0;
-                for (int i = 0; i < npop; ++i)
-                    any |= S[i].exact ? 0 : 1;
-                s_flag = any;
-            }
-            __syncthreads();
-            if (!s_flag)
-                break;
+        while (s_flag) {
             const int rl = (int)(ref_level % 3u), rz = (int)((ref_level + 1u) % 3u);
             for (int i = 0; i < npop; ++i) {
                 const FusedPop &p = prm.p[i];
@@ -685,6 +690,13 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             }
             ++ref_level;
             __syncthreads();
+            if (tid == 0) {
+                int any = 0;
+                for (int i = 0; i < npop; ++i)
+                    any |= S[i].exact ? 0 : 1;
+                s_flag = any;
+            }
+            __syncthreads();
         }
         if (tid < npop) {
             PopSel &s = S[tid];
@@ -697,12 +709,14 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
         }
         __syncthreads();
         if (tid == 0) {
-            uint32_t off = 0;
+            uint32_t off = 0, toff = 0;
             for (int i = 0; i < npop; ++i) {
                 const uint32_t nb = (S[i].capn >> S[i].shiftn) + 1u;
                 S[i].boff = off + nb <= kHistSmem ? off : 0xFFFFFFFFu;
                 if (off + nb <= kHistSmem)
                     off += nb;
+                S[i].toff = toff;
+                toff += (uint32_t)(2 * prm.p[i].N);
             }
         }
         // tile masks: F < T and F == T per 32 slots
@@ -778,6 +792,25 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                 atomicOr(err, ERR_INTERNAL);
         }
         __syncthreads();
+        if (prm.tab_words) {
+            // survivor tables: survivor number -> slot, in slot order
+            for (uint32_t tt = tid; tt < TT; tt += blockDim.x) {
+                const int i = owner_of(tt, npop, tile_base);
+                const PopSel &s = S[i];
+                const unsigned long long v = tm[tt], e = ex[tt];
+                const uint32_t eqb = min((uint32_t)e - s.eb, s.take);
+                uint32_t mask = (uint32_t)v | lowest_set_bits((uint32_t)(v >> 32), (int)(s.take - eqb));
+                uint32_t d = (uint32_t)(e >> 32) - s.lb + eqb;
+                const uint32_t base = (tt - prm.p[i].tile_base) * 32u;
+                uint32_t *tb = tab + s.toff;
+                while (mask) {
+                    const int b = __ffs(mask) - 1;
+                    mask &= mask - 1u;
+                    tb[d++] = base + (uint32_t)b;
+                }
+            }
+            __syncthreads();
+        }
         // m <= 32: two threads per pair
         for (uint32_t w = gwarp; w < nwork_t; w += gwarps) {
             const uint32_t u = w * 32u;
@@ -892,7 +925,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
 size_t fused_smem_bytes(const FusedParams &p)
 {
     const size_t r1 = std::max((size_t)4 * p.total_tiles, (size_t)2 * kHistSmem);
-    return (r1 + kHistSmem + (size_t)(kFusedThreads / 32) * p.warp_buf_words) * 4u;
+    return (r1 + kHistSmem + p.tab_words + (size_t)(kFusedThreads / 32) * p.warp_buf_words) * 4u;
 }
 
 cudaError_t fused_grid(size_t smem, int *grid)
