@@ -423,15 +423,6 @@ static ga_status fused_run(ga_ctx *const *ctxs, int n, int32_t generations, int 
     prm.thread_slots = tslots;
     prm.warp_pairs = wpairs;
     prm.warp_buf_words = max_words;
-    prm.tab_words = 0;
-    {
-        uint32_t tw = 0;
-        for (int i = 0; i < n; ++i)
-            tw += (uint32_t)(2 * ctxs[i]->N);
-        prm.tab_words = tw;
-        if (fused_smem_bytes(prm) > kFusedSmemBudget)
-            prm.tab_words = 0;  // survivor lookups by binary search instead
-    }
     prm.stop_at_zero = stop_at_zero;
     prm.bar = c0->fmisc;
     prm.done = (int32_t *)(c0->fmisc + 1);

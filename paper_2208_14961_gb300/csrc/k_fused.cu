@@ -46,7 +46,6 @@ struct PopSel {
     uint32_t lb, eb;      // joint (F < T, F == T) counts before the first tile of the population
     uint32_t capn, shiftn;  // histogram parameters of the next generation
     uint32_t boff;          // offset of this population's block histogram (~0: none)
-    uint32_t toff;          // offset of this population's survivor table
     uint32_t bor;           // block OR of the new fitness values
     unsigned long long bbest;  // block minimum of the new best keys
 };
@@ -162,7 +161,6 @@ __device__ __forceinline__ void block_scan_chunks(uint32_t n, Cnt cnt, uint32_t 
 // mask is lt | the lowest (take - eq_before) bits of eq.
 struct Surv {
     const unsigned long long *tm, *ex;
-    const uint32_t *tab;  // survivor number -> slot, per population at S.toff (or null)
 };
 
 __device__ __forceinline__ uint32_t surv_before(const Surv &sv, uint32_t tt, const PopSel &S)
@@ -177,8 +175,6 @@ __device__ __forceinline__ uint32_t surv_before(const Surv &sv, uint32_t tt, con
 __device__ __forceinline__ uint32_t survivor_of(uint32_t d, const FusedPop &p, const PopSel &S, const Surv &sv,
                                                 uint32_t *err)
 {
-    if (sv.tab)
-        return sv.tab[S.toff + d];
     const uint32_t tb = p.tile_base;
     uint32_t lo = 0, hi = p.ntiles - 1;
     while (lo < hi) {
@@ -201,6 +197,28 @@ __device__ __forceinline__ uint32_t survivor_of(uint32_t d, const FusedPop &p, c
     return slot < P ? slot : P - 1;
 }
 
+// Draws of one build item that do not depend on the selection: survivor
+// number d, cut point c and (for NC = NR = 1) the mutated column and rows.
+struct Pre {
+    uint32_t d, c, cc, ra, rb;
+};
+
+__device__ __forceinline__ Pre make_pre(const FusedPop &p, uint32_t gen, uint32_t tch, uint32_t k, int half)
+{
+    const uint32_t N = (uint32_t)p.N;
+    Pre r;
+    r.d = __ldg(p.perm + (size_t)tch * 2u * N + k + (half ? N : 0u));
+    r.c = (uint32_t)cut_point(p.seed, p.pop_id, gen, k, p.m);
+    r.cc = r.ra = r.rb = 0u;
+    if (p.NC == 1 && p.NR == 1) {
+        const uint4 w = philox_block(p.seed, p.pop_id, OP_MUTATE, gen, k + (half ? N : 0u), 0u, 0u);
+        r.cc = uniform_int(w.x, 1u, (uint32_t)(p.m - 1));
+        r.ra = uniform_int(w.y, 0u, (uint32_t)(p.m - 1));
+        r.rb = uniform_int(w.z, 0u, (uint32_t)(p.m - 1));
+    }
+    return r;
+}
+
 // Mutation draws of offspring o: NC columns, NR first rows, NR second rows.
 struct Draws {
     uint32_t seed, pop_id, gen, o, block;
@@ -221,18 +239,14 @@ struct Draws {
 template <int M, int KIND>
 __device__ __forceinline__ uint32_t fitness_regs(const uint32_t (&c)[M])
 {
-    // four independent partial sums keep the popcount pipe busy
-    uint32_t acc[4] = {0u, 0u, 0u, 0u};
-    int n = 0;
+    uint32_t acc = 0;
 #pragma unroll
     for (int i = 0; i < M; ++i) {
 #pragma unroll
-        for (int j = i + 1; j < M; ++j) {
-            acc[n & 3] += fit_term<KIND>(M - 2 * __popc(c[i] ^ c[j]));
-            ++n;
-        }
+        for (int j = i + 1; j < M; ++j)
+            acc += fit_term<KIND>(M - 2 * __popc(c[i] ^ c[j]));
     }
-    return fit_finish<KIND>((acc[0] + acc[1]) + (acc[2] + acc[3]));
+    return fit_finish<KIND>(acc);
 }
 
 // ---------------------------------------------------------------------------
@@ -240,7 +254,7 @@ __device__ __forceinline__ uint32_t fitness_regs(const uint32_t (&c)[M])
 // offspring O_{1 + half}; its parent is P_1 (half 0) or P_2 (half 1).
 // ---------------------------------------------------------------------------
 template <int M>
-__device__ __forceinline__ void pair_thread(const FusedPop &p, const PopSel &S, int src, uint32_t gen, uint32_t d,
+__device__ __forceinline__ void pair_thread(const FusedPop &p, const PopSel &S, int src, uint32_t gen, const Pre &pre,
                                             uint32_t k, int half, bool valid, const Surv &sv, uint32_t *err,
                                             uint32_t &f_par, uint32_t &slot_par, uint32_t &f_child,
                                             uint32_t &slot_child)
@@ -248,7 +262,7 @@ __device__ __forceinline__ void pair_thread(const FusedPop &p, const PopSel &S, 
     const uint32_t N = (uint32_t)p.N;
     uint32_t s_mine = 0;
     if (valid)
-        s_mine = survivor_of(d, p, S, sv, err);
+        s_mine = survivor_of(pre.d, p, S, sv, err);
     const uint32_t s_other = __shfl_xor_sync(FULL, s_mine, 1);
     if (!valid)
         return;
@@ -276,7 +290,7 @@ __device__ __forceinline__ void pair_thread(const FusedPop &p, const PopSel &S, 
         p.fit[src ^ 1][slot_par] = f_par;
     }
     // crossover (Sec. 3.4): O1 = P1[:, :c] | P2[:, c:], O2 = P2[:, :c] | P1[:, c:]
-    const int c = cut_point(p.seed, p.pop_id, gen, k, M);
+    const int c = (int)pre.c;
     uint32_t o[M];
 #pragma unroll
     for (int j = 0; j < M; ++j)
@@ -286,9 +300,7 @@ __device__ __forceinline__ void pair_thread(const FusedPop &p, const PopSel &S, 
         Draws dr(p.seed, p.pop_id, gen, k + (half ? N : 0u));
         const int NC = p.NC, NR = p.NR;
         if (NC == 1 && NR == 1) {
-            const uint32_t cc = uniform_int(dr.next(), 1u, (uint32_t)(M - 1));
-            const uint32_t ra = uniform_int(dr.next(), 0u, (uint32_t)(M - 1));
-            const uint32_t rb = uniform_int(dr.next(), 0u, (uint32_t)(M - 1));
+            const uint32_t cc = pre.cc, ra = pre.ra, rb = pre.rb;
 #pragma unroll
             for (int j = 1; j < M; ++j) {
                 if ((uint32_t)j == cc) {
@@ -513,9 +525,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
     unsigned long long *ex = tm + TT;
     uint32_t *hcnt = dyn, *hpre = dyn + kHistSmem;
     uint32_t *bhist = dyn + r1;  // block-local histograms of the next generation
-    uint32_t *tab = bhist + kHistSmem;  // survivor tables (prm.tab_words words, 0: binary search)
-    uint32_t *wbuf = tab + prm.tab_words + wib * prm.warp_buf_words;
-    const Surv sv{tm, ex, prm.tab_words ? tab : nullptr};
+    uint32_t *wbuf = bhist + kHistSmem + wib * prm.warp_buf_words;
+    const Surv sv{tm, ex};
     uint32_t *err = prm.err;
     uint32_t epoch = 0;
     int src = prm.src;
@@ -709,14 +720,29 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
         }
         __syncthreads();
         if (tid == 0) {
-            uint32_t off = 0, toff = 0;
+            uint32_t off = 0;
             for (int i = 0; i < npop; ++i) {
                 const uint32_t nb = (S[i].capn >> S[i].shiftn) + 1u;
                 S[i].boff = off + nb <= kHistSmem ? off : 0xFFFFFFFFu;
                 if (off + nb <= kHistSmem)
                     off += nb;
-                S[i].toff = toff;
-                toff += (uint32_t)(2 * prm.p[i].N);
+            }
+        }
+        // selection-independent draws of this warp's first build item, computed
+        // while the other blocks catch up
+        Pre pre0{0u, 1u, 1u, 0u, 0u};
+        const uint32_t nwork_t = prm.thread_slots >> 5;
+        if (gwarp < nwork_t) {
+            const uint32_t u = gwarp * 32u + (uint32_t)lane;
+            int i = -1;
+            for (int j = 0; j < npop; ++j)
+                if (prm.p[j].m <= 32 && u >= prm.p[j].work_base)
+                    i = (i < 0 || prm.p[j].work_base >= prm.p[i].work_base) ? j : i;
+            if (i >= 0) {
+                const FusedPop &p = prm.p[i];
+                const uint32_t local = u - p.work_base, k = local >> 1;
+                if (k < (uint32_t)p.N)
+                    pre0 = make_pre(p, gen, (uint32_t)t, k, (int)(local & 1u));
             }
         }
         // tile masks: F < T and F == T per 32 slots
@@ -735,22 +761,6 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             return;
 
         // ---- phase B: survivors in slot order, then build ------------------------
-        // the survivor orders of this warp's first work item are fetched first
-        uint32_t d_pre = 0;
-        const uint32_t nwork_t = prm.thread_slots >> 5;
-        if (gwarp < nwork_t) {
-            const uint32_t u = gwarp * 32u + (uint32_t)lane;
-            int i = -1;
-            for (int j = 0; j < npop; ++j)
-                if (prm.p[j].m <= 32 && u >= prm.p[j].work_base)
-                    i = (i < 0 || prm.p[j].work_base >= prm.p[i].work_base) ? j : i;
-            if (i >= 0) {
-                const FusedPop &p = prm.p[i];
-                const uint32_t local = u - p.work_base, k = local >> 1;
-                if (k < (uint32_t)p.N)
-                    d_pre = __ldg(p.perm + (size_t)t * 2u * (uint32_t)p.N + k + ((local & 1u) ? (uint32_t)p.N : 0u));
-            }
-        }
         for (uint32_t t0 = tid; t0 < TT; t0 += 4u * blockDim.x) {
             unsigned long long v[4];
 #pragma unroll
@@ -792,25 +802,6 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                 atomicOr(err, ERR_INTERNAL);
         }
         __syncthreads();
-        if (prm.tab_words) {
-            // survivor tables: survivor number -> slot, in slot order
-            for (uint32_t tt = tid; tt < TT; tt += blockDim.x) {
-                const int i = owner_of(tt, npop, tile_base);
-                const PopSel &s = S[i];
-                const unsigned long long v = tm[tt], e = ex[tt];
-                const uint32_t eqb = min((uint32_t)e - s.eb, s.take);
-                uint32_t mask = (uint32_t)v | lowest_set_bits((uint32_t)(v >> 32), (int)(s.take - eqb));
-                uint32_t d = (uint32_t)(e >> 32) - s.lb + eqb;
-                const uint32_t base = (tt - prm.p[i].tile_base) * 32u;
-                uint32_t *tb = tab + s.toff;
-                while (mask) {
-                    const int b = __ffs(mask) - 1;
-                    mask &= mask - 1u;
-                    tb[d++] = base + (uint32_t)b;
-                }
-            }
-            __syncthreads();
-        }
         // m <= 32: two threads per pair
         for (uint32_t w = gwarp; w < nwork_t; w += gwarps) {
             const uint32_t u = w * 32u;
@@ -824,15 +815,15 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             const uint32_t k = local >> 1;
             const int half = (int)(local & 1u);
             const bool valid = i >= 0 && k < (uint32_t)p.N;
-            uint32_t d = d_pre;
+            Pre pre = pre0;
             if (w != gwarp && valid)
-                d = __ldg(p.perm + (size_t)t * 2u * (uint32_t)p.N + k + (half ? (uint32_t)p.N : 0u));
+                pre = make_pre(p, gen, (uint32_t)t, k, half);
             uint32_t fpar = 0, spar = 0, fch = 0, sch = 0;
             const PopSel &s = S[i < 0 ? 0 : i];
             switch (p.m) {
 #define HADGA_PT(MM)                                                                                        \
     case MM:                                                                                                \
-        pair_thread<MM>(p, s, src, gen, d, k, half, valid, sv, err, fpar, spar, fch, sch);                  \
+        pair_thread<MM>(p, s, src, gen, pre, k, half, valid, sv, err, fpar, spar, fch, sch);                \
         break;
                 HADGA_PT(4) HADGA_PT(8) HADGA_PT(12) HADGA_PT(16) HADGA_PT(20) HADGA_PT(24) HADGA_PT(28) HADGA_PT(32)
 #undef HADGA_PT
@@ -925,7 +916,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
 size_t fused_smem_bytes(const FusedParams &p)
 {
     const size_t r1 = std::max((size_t)4 * p.total_tiles, (size_t)2 * kHistSmem);
-    return (r1 + kHistSmem + p.tab_words + (size_t)(kFusedThreads / 32) * p.warp_buf_words) * 4u;
+    return (r1 + kHistSmem + (size_t)(kFusedThreads / 32) * p.warp_buf_words) * 4u;
 }
 
 cudaError_t fused_grid(size_t smem, int *grid)

@@ -91,7 +91,6 @@ constexpr int kFusedThreads = 512;
 constexpr uint32_t kHistSmem = 8192;  // histogram words staged in shared memory per pass
 constexpr int kFusedMaxM = 128;    // orders the fused kernel builds (larger: plain path)
 constexpr uint32_t kFusedMaxTiles = 8192;   // joint tiles of 32 slots (P <= 262144)
-constexpr uint32_t kFusedSmemBudget = 220 * 1024;  // dynamic shared memory the fused kernel may use
 
 // Per-population state words of the fused kernel (device memory):
 // hist[2][kHistR] selection histograms by generation parity, ref[3][kHistR]
@@ -123,7 +122,6 @@ struct FusedParams {
     int32_t stop_at_zero;    // stop after a generation whose best fitness (population 0) is 0
     int32_t src;             // ping-pong buffer holding the current population
     int32_t warp_buf_words;  // shared words per warp for m > 32 populations
-    uint32_t tab_words;      // shared words of the survivor tables (sum of 2N), 0 when they do not fit
     uint32_t *bar;           // grid-barrier counter (zeroed before the launch)
     uint32_t *err;           // device error word
     int32_t *done;           // generations completed
