@@ -229,6 +229,30 @@ ga_status ga_init_batch(void *pop_dev, int32_t storage, int32_t m, int64_t P, ui
 ga_status ga_fitness_batch(const void *pop_dev, int32_t storage, int32_t m, int64_t P, int32_t kind,
                            int32_t path, uint32_t *fit_dev, void *stream);
 
+/* Allocation-free selection, for callers that cannot call cudaMalloc while
+ * this step runs (a framework hook that forbids device allocation, a fixed
+ * workspace, a path where an allocation would synchronise the device).
+ * The paper has no counterpart: this is the a3 + a4 step of ga_select
+ * (generation `gen`, same survivors, same order) with its scratch in one
+ * fixed device array of the library (88.5 KiB, held by every GPU that
+ * loads the library until the process exits) instead of a context.
+ *   pop_in, fit_in   : the population (4N matrices in `storage`, INT8 or
+ *                      BITS) and its fitness, read only.
+ *   parents_out,     : the 2N parents in placement order (2N matrices and
+ *   parent_fit_out     2N fitness words); must not overlap pop_in.
+ * N is limited to 1..8192 (P <= 32768); larger N is rejected with
+ * GA_EINVAL.  No cudaMalloc, cudaFree or allocating routine is called.  The
+ * first call on a device looks up the array's device address (with that
+ * device current) and should therefore come before any stream capture.
+ * Every call shares the one array and leaves its contents behind (the parts
+ * that must start at zero are cleared by each call), so calls that overlap
+ * on the GPU -- on different streams, or from different threads -- race.
+ * Stream-ordered; argument errors are reported through ga_last_error(NULL);
+ * device-side consistency checks are not reported. */
+ga_status ga_select_static(const void *pop_in, const uint32_t *fit_in, void *parents_out, uint32_t *parent_fit_out,
+                           int32_t storage, int32_t m, int64_t N, uint32_t seed, uint32_t pop_id, uint32_t gen,
+                           void *stream);
+
 /* Converts P matrices between storage formats (any pair). */
 ga_status ga_convert(const void *src, int32_t src_storage, void *dst, int32_t dst_storage, int32_t m,
                      int64_t P, void *stream);

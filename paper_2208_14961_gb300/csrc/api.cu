@@ -64,6 +64,7 @@ struct ga_ctx {
 
 namespace hadga {
 void note_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+void set_thread_error(const char *msg) { g_thread_error = msg; }
 } // namespace hadga
 
 namespace {

@@ -1,0 +1,117 @@
+// k_static.cu -- ga_select_static: the selection step (truncation selection
+// and random placement of the survivors) without any device allocation.
+//
+// Some callers cannot call cudaMalloc while they run this step: code that
+// executes inside a framework's execution hook where device memory must not
+// be allocated (plugin enqueue functions with a fixed workspace, pooled
+// allocators that forbid out-of-pool allocations), or code on a hot path
+// where an allocation would implicitly synchronise the device.  For them the
+// scratch of the selection lives in one file-scope device array of fixed
+// size, reserved when the library is loaded and held by every GPU that loads
+// it until the process exits.
+#include <mutex>
+
+#include "common.cuh"
+#include "hadga.h"
+#include "kernels.cuh"
+
+namespace hadga {
+namespace {
+
+// Largest N the allocation-free selection accepts (P = 4N <= 32768).
+constexpr int64_t kStaticMaxN = 8192;
+// Scratch layout (bytes): histogram 2048 words, selection state, per tile
+// (P/32 tiles) an 8-byte mask pair and two 4-byte words, the survivor order
+// (2N words), and the device error word.
+constexpr size_t kStaticHistBytes = 2048 * 4;
+constexpr size_t kStaticStateBytes = 256;
+constexpr size_t kStaticTiles = (size_t)(4 * kStaticMaxN) / 32;
+constexpr size_t kStaticScratchBytes =
+    kStaticHistBytes + kStaticStateBytes + kStaticTiles * (8 + 4 + 4) + (size_t)(2 * kStaticMaxN) * 4 + 256;
+
+static __device__ __align__(256) unsigned char g_select_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mutex;
+void *g_scratch_addr[kMaxDevices] = {};
+
+ga_status fail(ga_status st, const char *msg)
+{
+    set_thread_error(msg);  // reported by ga_last_error(NULL)
+    return st;
+}
+
+} // namespace
+} // namespace hadga
+
+using namespace hadga;
+
+extern "C" ga_status ga_select_static(const void *pop_in, const uint32_t *fit_in, void *parents_out,
+                                      uint32_t *parent_fit_out, int32_t storage, int32_t m, int64_t N, uint32_t seed,
+                                      uint32_t pop_id, uint32_t gen, void *stream)
+{
+    if (!pop_in || !fit_in || !parents_out || !parent_fit_out)
+        return fail(GA_EINVAL, "ga_select_static: NULL buffer");
+    if (m < 4 || m > kMaxM || (m & 3) || (storage != ST_INT8 && storage != ST_BITS))
+        return fail(GA_EINVAL, "ga_select_static: m must be a multiple of 4 in [4, 256], storage INT8 or BITS");
+    if (N < 1 || N > kStaticMaxN)
+        return fail(GA_EINVAL, "ga_select_static: N must lie in [1, 8192] (P <= 32768): the fixed scratch array "
+                               "holds no more");
+    if ((((uintptr_t)pop_in) | ((uintptr_t)fit_in) | ((uintptr_t)parents_out) | ((uintptr_t)parent_fit_out)) & 15u)
+        return fail(GA_EINVAL, "ga_select_static: buffers must be 16-byte aligned");
+    const size_t mat = matrix_bytes(storage, m);
+    const uintptr_t in0 = (uintptr_t)pop_in, in1 = in0 + (size_t)(4 * N) * mat;
+    const uintptr_t o0 = (uintptr_t)parents_out, o1 = o0 + (size_t)(2 * N) * mat;
+    if (o0 < in1 && in0 < o1)
+        return fail(GA_EINVAL, "ga_select_static: parents_out must not overlap pop_in");
+
+    // set-up, once per device, with that device current: the device address
+    // of the scratch array (its host-side name is only a stand-in)
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return fail(GA_ECUDA, "ga_select_static: no usable current device");
+    unsigned char *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_mutex);
+        if (!g_scratch_addr[dev]) {
+            void *ptr = nullptr;
+            e = cudaGetSymbolAddress(&ptr, g_select_scratch);
+            if (e != cudaSuccess || !ptr)
+                return fail(GA_ECUDA, "ga_select_static: cudaGetSymbolAddress of the scratch array failed");
+            g_scratch_addr[dev] = ptr;
+        }
+        base = (unsigned char *)g_scratch_addr[dev];
+    }
+
+    const int64_t tiles = (4 * N + 31) / 32;
+    SelWork w{};
+    size_t off = 0;
+    w.hist = (uint32_t *)(base + off);
+    off += kStaticHistBytes;
+    w.state = (SelState *)(base + off);
+    off += kStaticStateBytes;
+    w.tmask = (unsigned long long *)(base + off);
+    off += (size_t)tiles * 8;
+    w.survmask = (uint32_t *)(base + off);
+    off += (size_t)tiles * 4;
+    w.survbefore = (uint32_t *)(base + off);
+    off += (size_t)tiles * 4;
+    w.perm = (uint32_t *)(base + off);
+    off += (size_t)(2 * N) * 4;
+    off = (off + 255) & ~(size_t)255;
+    w.err = (uint32_t *)(base + off);
+    w.perm_keys = nullptr;  // 2N <= 16384 always takes the shared-memory sort
+    w.perm_cnt = nullptr;
+
+    cudaStream_t s = (cudaStream_t)stream;
+    // the array keeps the previous call's contents: clear what must start at 0
+    e = cudaMemsetAsync(w.hist, 0, kStaticHistBytes + kStaticStateBytes, s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(w.err, 0, 4, s);
+    if (e == cudaSuccess)
+        e = launch_select(pop_in, fit_in, N, mat, seed, pop_id, gen, w, parents_out, parent_fit_out, s);
+    if (e != cudaSuccess)
+        return fail(GA_ECUDA, cudaGetErrorString(e));
+    return GA_OK;
+}

@@ -35,6 +35,8 @@ constexpr int kPermSmemBits = 11;
 
 // Adds n to the process-wide count of launched kernels (ga_kernel_launches).
 void note_launches(int n);
+// Sets the calling thread's message returned by ga_last_error(NULL).
+void set_thread_error(const char *msg);
 
 // ---- init (k_init.cu) -----------------------------------------------------
 cudaError_t launch_init(void *pop, int storage, int m, int64_t first, int64_t count, uint32_t seed, uint32_t pop_id,

@@ -79,6 +79,7 @@ SIGNATURES = {
     "ga_init_batch": (_i32, [_vp, _i32, _i32, _i64, _u32, _u32, _vp]),
     "ga_fitness_batch": (_i32, [_vp, _i32, _i32, _i64, _i32, _i32, _vp, _vp]),
     "ga_convert": (_i32, [_vp, _i32, _vp, _i32, _i32, _i64, _vp]),
+    "ga_select_static": (_i32, [_vp, _vp, _vp, _vp, _i32, _i32, _i64, _u32, _u32, _u32, _vp]),
 }
 
 _lib = None
@@ -164,6 +165,15 @@ def ga_fitness_batch(pop: torch.Tensor, storage: int, m: int, P: int, kind: int,
 def ga_convert(src: torch.Tensor, src_storage: int, dst: torch.Tensor, dst_storage: int, m: int, P: int,
                stream=None):
     check(load().ga_convert(_ptr(src), src_storage, _ptr(dst), dst_storage, m, P, _stream(stream)))
+
+
+def ga_select_static(pop_in: torch.Tensor, fit_in: torch.Tensor, parents_out: torch.Tensor,
+                     parent_fit_out: torch.Tensor, storage: int, m: int, N: int, seed: int, pop_id: int, gen: int,
+                     stream=None):
+    """Selection of generation `gen` into caller buffers, with no device
+    allocation (the scratch is a fixed array inside the library)."""
+    check(load().ga_select_static(_ptr(pop_in), _ptr(fit_in), _ptr(parents_out), _ptr(parent_fit_out), storage, m,
+                                  N, seed, pop_id, gen, _stream(stream)))
 
 
 # ---------------------------------------------------------------------------

@@ -1,0 +1,51 @@
+"""ga_select_static: the selection step for callers that cannot allocate
+device memory while it runs (its scratch is a fixed array inside the
+library).  Checked against the context-based ga_select, bit for bit, on two
+calls in a row.  Named to be collected last."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("storage,m,N", [(1, 20, 2500), (0, 12, 8192)])
+def test_select_static_matches_ga_select(storage, m, N):
+    h = need_gpu()
+    seed, pop_id = 5, 1
+    ref = h.Population(m, N, seed=seed, pop_id=pop_id, storage=storage)
+    ref.init_population()
+    ref.fitness()
+    torch.cuda.synchronize()
+    pop_in = ref.pop.clone()
+    fit_in = ref.fit.clone()
+    shape, dt = h.storage_shape(storage, m, 2 * N)
+    for call in range(2):       # two calls in a row on the shared array
+        gen = call + 1
+        parents = torch.empty(shape, dtype=dt, device="cuda")
+        pfit = torch.empty(2 * N, dtype=torch.int32, device="cuda")
+        h.ga_select_static(pop_in, fit_in, parents, pfit, storage, m, N, seed, pop_id, gen,
+                           stream=torch.cuda.current_stream())
+        ref.select()            # the existing entry point, generation `gen`
+        torch.cuda.synchronize()
+        assert ref.generation() == gen
+        assert torch.equal(parents, ref.pop[:2 * N])
+        assert torch.equal(pfit, ref.fit[:2 * N])
+        # next call: the population after this selection
+        pop_in = ref.pop.clone()
+        fit_in = ref.fit.clone()
+    ref.close()
+
+
+def test_select_static_rejects_too_large_population():
+    h = need_gpu()
+    N = 8193
+    pop = torch.empty((4 * N, 4, 1), dtype=torch.int32, device="cuda")
+    fit = torch.zeros(4 * N, dtype=torch.int32, device="cuda")
+    out = torch.empty((2 * N, 4, 1), dtype=torch.int32, device="cuda")
+    of = torch.empty(2 * N, dtype=torch.int32, device="cuda")
+    with pytest.raises(h.GAError) as ei:
+        h.ga_select_static(pop, fit, out, of, 1, 4, N, 0, 0, 1)
+    assert ei.value.status == h.GA_EINVAL and "8192" in str(ei.value)
