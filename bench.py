@@ -164,6 +164,94 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+GRAM_PATHS = [  # name, storage, path
+    ("int32", 0, 1), ("imma", 0, 2), ("popc_int8", 0, 5), ("popc_bits", 1, 5), ("fp8", 2, 3), ("bf16", 3, 4),
+]
+
+
+def gram_sweep(args):
+    """Precision sweep of the batched Gram + F_sq alone: balanced +-1
+    populations of `--gram-gb` GiB of int8 (seed 2) at each order, every
+    path on its own storage format; one JSON line per (m, path) with the
+    time per pass, matrices/s, achieved GB/s of its storage, the bound
+    roof and an exactness check of 256 sampled slots against the oracle."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2208_14961_gb300.build import build
+    build()
+    from paper_2208_14961_gb300 import hadga as h
+    from paper_2208_14961_gb300 import peaks
+
+    hbm, hbm_kind = _peaks()
+    rates = {k: peaks.rate(k) for k in ("popc_chain", "dp4a", "imma_s8")}
+    print(json.dumps({"peaks": {"hbm_gbs": hbm, "hbm_source": hbm_kind, "popc_per_s": rates["popc_chain"],
+                                "dp4a_per_s": rates["dp4a"], "imma_s8_mac_per_s": rates["imma_s8"]}}), flush=True)
+    rng = np.random.default_rng(7)
+    for m in [int(x) for x in args.gram_ms.split(",")]:
+        P = int(args.gram_gb * (1 << 30)) // (m * m)
+        D = m * (m - 1) // 2
+        W = (m + 31) // 32
+        for name, storage, path in GRAM_PATHS:
+            if args.gram_paths and name not in args.gram_paths.split(","):
+                continue
+            try:
+                pop = h.empty_population(storage, m, P)
+            except RuntimeError as e:
+                print(json.dumps({"m": m, "path": name, "skipped": f"allocation: {e}"[:200]}), flush=True)
+                continue
+            fit = torch.zeros(P, dtype=torch.int32, device="cuda")
+            h.ga_init_batch(pop, storage, m, P, 2)
+            try:
+                h.ga_fitness_batch(pop, storage, m, P, h.FIT_SQ, path, fit)
+            except h.GAError as e:
+                print(json.dumps({"m": m, "path": name, "skipped": str(e)[:200]}), flush=True)
+                del pop, fit
+                torch.cuda.empty_cache()
+                continue
+            torch.cuda.synchronize()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            reps = 5
+            ev[0].record()
+            for _ in range(reps):
+                h.ga_fitness_batch(pop, storage, m, P, h.FIT_SQ, path, fit)
+            ev[1].record()
+            ev[1].synchronize()
+            sec = ev[0].elapsed_time(ev[1]) / 1e3 / reps
+            # exactness on sampled slots
+            idx = torch.as_tensor(np.sort(rng.choice(P, size=min(256, P), replace=False)), device="cuda")
+            sub = pop.index_select(0, idx).contiguous()
+            sub8 = h.empty_population(0, m, len(idx))
+            h.ga_convert(sub, storage, sub8, 0, m, len(idx))
+            torch.cuda.synchronize()
+            ref = oracle.fitness(sub8.cpu().numpy(), oracle.FIT_SQ)
+            got = fit.index_select(0, idx).cpu().numpy().view(np.uint32).astype(np.uint64)
+            exact = bool(np.array_equal(ref, got))
+            nbytes = P * h.storage_bytes(storage, m)
+            t_mem = nbytes / (hbm * 1e9)
+            if name == "popc_bits" or name == "popc_int8":
+                ops, peak, unit = P * D * W, rates["popc_chain"], "popc"
+            elif name == "int32":
+                ops, peak, unit = P * D * (m // 4), rates["dp4a"], "dp4a"
+            elif name == "imma" and m % 32 == 0:
+                mt, ct, ks = m // 16, m // 8, m // 32
+                tiles = sum(ct - 2 * ri for ri in range(mt))
+                ops, peak, unit = P * tiles * ks * 4096, rates["imma_s8"], "s8 MAC"
+            else:
+                ops, peak, unit = None, None, None
+            t_cmp = ops / peak if ops else 0.0
+            bound = "hbm" if t_mem >= t_cmp else "alu" if name != "imma" else "tensor"
+            roof_t = max(t_mem, t_cmp)
+            line = {"m": m, "path": name, "P": P, "storage_gib": nbytes / (1 << 30), "ms": sec * 1e3,
+                    "matrices_per_s": P / sec, "achieved_gbs": nbytes / sec / 1e9, "bound": bound,
+                    "roof_ms": roof_t * 1e3, "frac": roof_t / sec, "hbm_frac": t_mem / sec,
+                    "compute_unit": unit, "compute_frac": (t_cmp / sec) if ops else None, "exact_256": exact}
+            print(json.dumps(line), flush=True)
+            del pop, fit, sub, sub8
+            torch.cuda.empty_cache()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -172,7 +260,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=4)
+    ap.add_argument("--gram-sweep", action="store_true", help="precision sweep of the Gram + fitness paths")
+    ap.add_argument("--gram-gb", type=float, default=8.0)
+    ap.add_argument("--gram-ms", default="32,64,128,256")
+    ap.add_argument("--gram-paths", default="")
     args = ap.parse_args()
+    if args.gram_sweep:
+        gram_sweep(args)
+        return
     args.warmup = max(args.warmup, 3)
 
     rank = int(os.environ.get("RANK", "0"))

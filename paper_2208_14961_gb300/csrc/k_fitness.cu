@@ -234,6 +234,171 @@ __global__ void __launch_bounds__(128) k_fit_int8_imma(const int8_t *__restrict_
 }
 
 // ---------------------------------------------------------------------------
+// F_sq through the row Gram.  For any +-1 matrix, the sum over i < j of the
+// squared column inner products equals the sum over r < s of the squared row
+// inner products (both are (||Q^T Q||_F^2 - m^3) / 2, since the diagonals are
+// m and ||Q^T Q||_F = ||Q Q^T||_F).  R = Q Q^T maps onto mma.sync row.col
+// with both operands read straight from the row-major int8 matrix: A holds
+// rows r, B holds rows s, k runs along a row.  The sum over k is the same
+// under any consistent relabelling of k, so every lane reads 8 contiguous
+// bytes of a row per 32-wide k step (k slots 4t..4t+3 <- bytes 8t..8t+3 and
+// k slots 16+4t..19+4t <- bytes 8t+4..8t+7) and a warp's loads are
+// fully coalesced.
+// ---------------------------------------------------------------------------
+
+// m in {32, 64}: one warp per matrix, the whole matrix in registers
+// (lane (g, t) holds rows g + 8q, q < m/8, bytes 8t..8t+7 of every 32-byte
+// k step).
+template <int M>
+__global__ void __launch_bounds__(256) k_fsq_imma_regs(const int8_t *__restrict__ pop, int64_t first, int64_t count,
+                                                      uint32_t *__restrict__ fit)
+{
+    constexpr int RG = M / 8, KS = M / 32, MT = M / 16;
+    const int lane = threadIdx.x & 31, grp = lane >> 2, tig = lane & 3;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    uint2 cur[RG][KS], nxt[RG][KS];
+    auto load = [&](int64_t q, uint2 (&f)[RG][KS]) {
+        const uint8_t *Q = reinterpret_cast<const uint8_t *>(pop) + (size_t)q * M * M;
+#pragma unroll
+        for (int r = 0; r < RG; ++r)
+#pragma unroll
+            for (int ks = 0; ks < KS; ++ks)
+                f[r][ks] = __ldg(reinterpret_cast<const uint2 *>(Q + (size_t)(grp + 8 * r) * M + ks * 32 + tig * 8));
+    };
+    int64_t q = first + gw;
+    if (q < first + count)
+        load(q, cur);
+    for (; q < first + count; q += nw) {
+        const int64_t qn = q + nw;
+        if (qn < first + count)
+            load(qn, nxt);
+        uint32_t acc = 0;
+#pragma unroll
+        for (int ri = 0; ri < MT; ++ri) {
+#pragma unroll
+            for (int cj = 2 * ri; cj < RG; ++cj) {
+                int d[4] = {0, 0, 0, 0};
+#pragma unroll
+                for (int ks = 0; ks < KS; ++ks) {
+                    const uint32_t a[4] = {cur[2 * ri][ks].x, cur[2 * ri + 1][ks].x, cur[2 * ri][ks].y,
+                                           cur[2 * ri + 1][ks].y};
+                    const uint32_t b[2] = {cur[cj][ks].x, cur[cj][ks].y};
+                    mma_s8_16832(d, a, b);
+                }
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int r = 16 * ri + grp + ((e >> 1) << 3);
+                    const int c = 8 * cj + tig * 2 + (e & 1);
+                    acc += c > r ? (uint32_t)(d[e] * d[e]) : 0u;
+                }
+            }
+        }
+        acc = warp_sum(acc);
+        if (lane == 0)
+            fit[q] = acc;
+#pragma unroll
+        for (int r = 0; r < RG; ++r)
+#pragma unroll
+            for (int ks = 0; ks < KS; ++ks)
+                cur[r][ks] = nxt[r][ks];
+    }
+}
+
+// m a multiple of 32 above 64: one block of 4 warps per matrix, the matrix
+// staged in shared memory with rows padded by 32 bytes (a half-warp's 8-byte
+// reads of 4 rows then cover all 32 banks), the upper-triangle 16 x 8 tiles
+// of R dealt round-robin to the warps.
+__global__ void __launch_bounds__(128) k_fsq_imma_smem(const int8_t *__restrict__ pop, int m, int64_t first,
+                                                       int64_t count, uint32_t *__restrict__ fit)
+{
+    extern __shared__ __align__(16) uint8_t s_q[];
+    __shared__ uint32_t s_part[4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, grp = lane >> 2, tig = lane & 3;
+    const int rs = m + 32;  // padded row stride in bytes
+    const int KS = m / 32, MT = m / 16, CT = m / 8;
+    for (int64_t q = first + blockIdx.x; q < first + count; q += gridDim.x) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(pop + (size_t)q * m * m);
+        const int chunks = m * m / 16, per_row = m / 16;
+        for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
+            const int r = c / per_row, w = c % per_row;
+            *reinterpret_cast<uint4 *>(s_q + r * rs + w * 16) = __ldg(src + c);
+        }
+        __syncthreads();
+        uint32_t acc = 0;
+        int tile = 0;
+        for (int ri = 0; ri < MT; ++ri) {
+            for (int cj = 2 * ri; cj < CT; ++cj, ++tile) {
+                if ((tile & 3) != warp)
+                    continue;
+                int d[4] = {0, 0, 0, 0};
+                for (int ks = 0; ks < KS; ++ks) {
+                    const uint2 a0 = *reinterpret_cast<const uint2 *>(s_q + (16 * ri + grp) * rs + ks * 32 + tig * 8);
+                    const uint2 a1 =
+                        *reinterpret_cast<const uint2 *>(s_q + (16 * ri + grp + 8) * rs + ks * 32 + tig * 8);
+                    const uint2 b0 = *reinterpret_cast<const uint2 *>(s_q + (8 * cj + grp) * rs + ks * 32 + tig * 8);
+                    const uint32_t a[4] = {a0.x, a1.x, a0.y, a1.y};
+                    const uint32_t b[2] = {b0.x, b0.y};
+                    mma_s8_16832(d, a, b);
+                }
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int r = 16 * ri + grp + ((e >> 1) << 3);
+                    const int c = 8 * cj + tig * 2 + (e & 1);
+                    acc += c > r ? (uint32_t)(d[e] * d[e]) : 0u;
+                }
+            }
+        }
+        acc = warp_sum(acc);
+        if (lane == 0)
+            s_part[warp] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0)
+            fit[q] = s_part[0] + s_part[1] + s_part[2] + s_part[3];
+    }
+}
+
+// F_sq with CUDA-core 4-way byte dot products on the row Gram: one warp per
+// matrix staged in shared memory; lane r owns rows r, r + 32, ... and pairs
+// each with the rows that follow it (mod m) by the same circular rule as
+// the popcount kernels.
+__global__ void __launch_bounds__(128) k_fsq_dp4a_rows(const int8_t *__restrict__ pop, int m, int64_t first,
+                                                       int64_t count, uint32_t *__restrict__ fit)
+{
+    extern __shared__ __align__(16) uint8_t s_rows[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int rsw = m / 4 + 1;  // padded row stride in words (odd: conflict-free column reads)
+    uint32_t *R = reinterpret_cast<uint32_t *>(s_rows) + (size_t)wib * m * rsw;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int kw = m / 4, half = m >> 1;
+    for (int64_t q = first + gw; q < first + count; q += nw) {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(pop + (size_t)q * m * m);
+        for (int e = lane; e < m * kw; e += 32)
+            R[(e / kw) * rsw + (e % kw)] = __ldg(src + e);
+        __syncwarp();
+        uint32_t acc = 0;
+        for (int a = lane; a < m; a += 32) {
+            const uint32_t *ra = R + a * rsw;
+            const int smax = a < half ? half : half - 1;
+            int b = a;
+            for (int s = 1; s <= smax; ++s) {
+                b = (b + 1 == m) ? 0 : b + 1;
+                const uint32_t *rb = R + b * rsw;
+                int g = 0;
+                for (int k = 0; k < kw; ++k)
+                    g = __dp4a((int)ra[k], (int)rb[k], g);
+                acc += (uint32_t)(g * g);
+            }
+        }
+        acc = warp_sum(acc);
+        if (lane == 0)
+            fit[q] = acc;
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Dispatch
 // ---------------------------------------------------------------------------
 bool fitness_path_supported(int storage, int m, int path)
@@ -304,7 +469,42 @@ static cudaError_t fitness_kind(const void *pop, int storage, int m, int64_t fir
         note_launches(1);
         return cudaGetLastError();
     }
-    // INT32 / IMMA on int8
+    // F_sq on int8: row-Gram kernels (no transpose)
+    if (KIND == FIT_SQ && path == 2 && (m == 32 || m == 64)) {
+        const int grid = grid_for_warps(count, 8);
+        if (m == 32)
+            k_fsq_imma_regs<32><<<grid, 256, 0, s>>>((const int8_t *)pop, first, count, fit);
+        else
+            k_fsq_imma_regs<64><<<grid, 256, 0, s>>>((const int8_t *)pop, first, count, fit);
+        note_launches(1);
+        return cudaGetLastError();
+    }
+    if (KIND == FIT_SQ && path == 2 && m % 32 == 0) {
+        const size_t smem = (size_t)m * (m + 32);
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(k_fsq_imma_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const int64_t want = count < (int64_t)sms * 16 ? count : (int64_t)sms * 16;
+        k_fsq_imma_smem<<<(unsigned)(want > 0 ? want : 1), 128, smem, s>>>((const int8_t *)pop, m, first, count, fit);
+        note_launches(1);
+        return cudaGetLastError();
+    }
+    if (KIND == FIT_SQ && path == 1) {
+        const size_t per_warp = (size_t)m * (m / 4 + 1) * 4;
+        int wpb = 4;
+        while (wpb > 1 && per_warp * wpb > 200 * 1024)
+            --wpb;
+        const size_t smem = (size_t)wpb * per_warp;
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(k_fsq_dp4a_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const int grid = grid_for_warps(count, wpb);
+        k_fsq_dp4a_rows<<<grid, wpb * 32, smem, s>>>((const int8_t *)pop, m, first, count, fit);
+        note_launches(1);
+        return cudaGetLastError();
+    }
+    // INT32 / IMMA on int8, column Gram on a transposed copy
     const int kpad = (m + 31) & ~31, mpad = (m + 15) & ~15, ts = kpad + 16;
     const size_t per_warp = (size_t)mpad * ts;
     int wpb = 4;

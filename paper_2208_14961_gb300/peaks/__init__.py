@@ -1,0 +1,27 @@
+"""Throughput microbenchmarks (popcount, dp4a, int8 mma.sync) used as the
+compute roof of the Gram paths; built into _build/libpeaks.so."""
+import ctypes
+import os
+import subprocess
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = os.path.join(os.path.dirname(_HERE), "_build", "libpeaks.so")
+
+KINDS = {"popc": 0, "popc_chain": 1, "dp4a": 2, "imma_s8": 3}
+
+
+def build():
+    src = os.path.join(_HERE, "peaks.cu")
+    if os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(src):
+        return _LIB
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-Xcompiler", "-fPIC", "-shared",
+                    "-o", _LIB, src], check=True)
+    return _LIB
+
+
+def rate(kind: str, iters: int = 4096) -> float:
+    lib = ctypes.CDLL(build())
+    lib.peak_rate.restype = ctypes.c_double
+    lib.peak_rate.argtypes = [ctypes.c_int, ctypes.c_int]
+    return float(lib.peak_rate(KINDS[kind], iters))
