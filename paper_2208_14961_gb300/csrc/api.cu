@@ -791,6 +791,8 @@ ga_status ga_fitness_batch(const void *pop_dev, int32_t storage, int32_t m, int6
             return set_error(nullptr, GA_EINVAL, "path %d does not read storage %d", path, storage);
         if (!fitness_tc_supported(storage, m))
             return set_error(nullptr, GA_EUNSUPPORTED, "tensor-core path not available for m=%d", m);
+        if (kind != GA_FIT_SQ)
+            return set_error(nullptr, GA_EUNSUPPORTED, "tensor-core paths compute the sum-of-squares fitness only");
         return cuda_check(nullptr, launch_fitness_tc(pop_dev, storage, m, 0, P, kind, fit_dev, nullptr, s),
                           "tensor-core fitness");
     }

@@ -1,23 +1,477 @@
-// k_tc.cu -- tcgen05 (5th-generation tensor core) Gram + fitness paths for
-// FP8 e4m3 and BF16 storage.  Not built yet in this revision: the entry
-// points report "not supported" so callers get GA_EUNSUPPORTED.
+// k_tc.cu -- batched Gram + F_sq on the 5th-generation tensor cores
+// (tcgen05) for populations stored as FP8 e4m3 or BF16 (+-1 exactly
+// representable; FP32 accumulation of at most 256 products of +-1 is exact).
+//
+// F_sq is taken from the row Gram R = Q Q^T (for +-1 matrices the sum of
+// squared off-diagonal entries above the diagonal equals the column Gram's),
+// so both MMA operands are the row-major matrix itself, K-major, as the TMA
+// copy lands it.  A job is a tile of 128 consecutive rows of the population
+// (128/m whole matrices for m <= 128; for m = 256 a job is one matrix, 256
+// rows, two M-tiles of which only the upper-triangle blocks are computed).
+// The K extent of a row is cut into chunks of 128 bytes (or the row, if
+// shorter); each chunk is one pipeline stage, copied by TMA with the matching
+// 32/64/128-byte swizzle.
+//
+// Roles (warp specialised, one block per SM):
+//   warp 0   one thread issues the TMA copies into a ring of stages
+//   warp 1   allocates TMEM; one thread issues tcgen05.mma per stage and
+//            commits to the stage's "empty" barrier and, at the end of a
+//            job, to the accumulator's "full" barrier
+//   warps 2-5  read the accumulators with tcgen05.ld (warp w reads TMEM
+//            lanes 32(w%4)..32(w%4)+31 = tile rows), square and sum the
+//            entries above the diagonal of each matrix, free the
+//            accumulator and write the fitness
+// Every mbarrier wait is bounded (about two seconds); on a timeout the block
+// records ERR_TIMEOUT, drains its outstanding copies with bounded waits,
+// frees its TMEM and returns.
+#include <cuda.h>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
 namespace hadga {
 
+namespace {
+
+constexpr int kTcThreads = 192;  // 6 warps
+constexpr int kStages = 6;
+constexpr uint32_t kStageBytes = 32768;  // a chunk of up to 256 rows x 128 bytes
+constexpr unsigned long long kWaitBudgetNs = 2000000000ull;
+
+// Error word of launches that come without one (the stateless batch call).
+__device__ uint32_t g_tc_err;
+
+struct TcParams {
+    int64_t P;          // matrices
+    int32_t m;          // order (32, 64, 128, 256)
+    int32_t esize;      // bytes per element (1 e4m3, 2 bf16)
+    int32_t kb;         // chunk width in bytes (<= 128)
+    int32_t nchunks;    // chunks per row
+    int32_t rows;       // rows per job (128, or 256 for m = 256)
+    int64_t jobs;
+    uint32_t idesc_n128, idesc_n256;  // instruction descriptors
+    uint32_t layout;    // smem descriptor layout type of the swizzle
+    uint32_t *fit;
+    uint32_t *err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase of `bar` with parity `parity`; false when the
+// budget ran out, or another thread raised an error and the phase is still
+// open (a completed phase always reports true).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t *err)
+{
+    if (mbar_test(bar, parity))
+        return true;
+    const unsigned long long t0 = global_ns();
+    for (uint32_t i = 1;; ++i) {
+        if (mbar_test(bar, parity))
+            return true;
+        if ((i & 255u) == 0u) {
+            if (ld_acquire_gpu(err) != 0u)
+                return mbar_test(bar, parity);
+            if (global_ns() - t0 > kWaitBudgetNs) {
+                atomicOr(err, ERR_TIMEOUT);
+                return mbar_test(bar, parity);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int32_t x, int32_t y, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+                 "[%4];" ::"r"(smem_u32(dst)),
+                 "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major swizzled operand: start
+// address, leading byte offset (unused for swizzled K-major, 1), stride byte
+// offset between groups of 8 rows, descriptor version 1, layout type.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t sbo, uint32_t layout)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1u << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1u << 46;
+    d |= (uint64_t)layout << 61;
+    return d;
+}
+
+template <bool BF16>
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
+{
+    if (BF16)
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+                     "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+    else
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+                     "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// 32 consecutive fp32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                   "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                   "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                   "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Sum of squares of v[c] (as exact integers) over the columns c0 + c with
+// c0 + c > row.
+__device__ __forceinline__ uint32_t sq_above(const uint32_t (&v)[32], int c0, int row)
+{
+    uint32_t acc = 0;
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+        const int g = (int)__uint_as_float(v[c]);
+        acc += (c0 + c > row) ? (uint32_t)(g * g) : 0u;
+    }
+    return acc;
+}
+
+} // namespace
+
+template <bool BF16>
+__global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant__ CUtensorMap map,
+                                                          const __grid_constant__ TcParams prm)
+{
+    extern __shared__ __align__(1024) uint8_t dyn_raw[];
+    // 1024-byte alignment keeps every stage on the swizzle pattern's base
+    uint8_t *stages = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dyn_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], acc_full[2], acc_empty[2], drain;
+    __shared__ uint32_t tmem_base;
+    __shared__ uint32_t part_sum[2][2], part_cnt[2][2];
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m = prm.m, rows = prm.rows, nch = prm.nchunks, kb = prm.kb;
+    const int nacc = (m == 256) ? 1 : 2;
+    const uint32_t tmem_cols = (m == 256) ? 512u : 256u;
+    uint32_t *err = prm.err ? prm.err : &g_tc_err;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 128);
+            part_sum[b][0] = part_sum[b][1] = 0u;
+            part_cnt[b][0] = part_cnt[b][1] = 0u;
+        }
+        mbar_init(&drain, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tbase = tmem_base;
+
+    if (warp == 0) {
+        // ---- TMA producer ----------------------------------------------------
+        if (lane == 0) {
+            const uint32_t box_bytes = 128u * (uint32_t)kb;
+            uint32_t it = 0;
+            int issued = 0;  // stages issued and not yet known consumed (for draining)
+            bool ok = true;
+            for (int64_t j = blockIdx.x; j < prm.jobs && ok; j += gridDim.x) {
+                for (int c = 0; c < nch && ok; ++c, ++it) {
+                    const int s = (int)(it % kStages);
+                    const uint32_t ph = (it / kStages) & 1u;
+                    if (!mbar_wait(&empty[s], ph ^ 1u, err)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&full[s], box_bytes * (uint32_t)(rows / 128));
+                    const int32_t x = c * (kb / prm.esize);
+                    for (int h = 0; h < rows / 128; ++h)
+                        tma_load_2d(stages + (size_t)s * kStageBytes + (size_t)h * 128 * kb, &map, x,
+                                    (int32_t)(j * rows + h * 128), &full[s]);
+                    issued = issued < kStages ? issued + 1 : kStages;
+                }
+            }
+            if (!ok) {
+                // drain: let copies already in flight land before the block exits
+                for (int q = 0; q < issued; ++q) {
+                    const uint32_t itq = it - 1u - (uint32_t)q;
+                    mbar_wait(&full[itq % kStages], (itq / kStages) & 1u, err);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---- MMA issuer ---------------------------------------------------------
+        if (lane == 0) {
+            const uint32_t sbo = 8u * (uint32_t)kb;
+            uint32_t it = 0, jt = 0;
+            bool ok = true;
+            for (int64_t j = blockIdx.x; j < prm.jobs && ok; j += gridDim.x, ++jt) {
+                const int b = (int)(jt % (uint32_t)nacc);
+                const uint32_t bph = (jt / (uint32_t)nacc) & 1u;
+                if (!mbar_wait(&acc_empty[b], bph ^ 1u, err)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t d0 = tbase + (uint32_t)b * 128u;
+                for (int c = 0; c < nch; ++c, ++it) {
+                    const int s = (int)(it % kStages);
+                    if (!mbar_wait(&full[s], (it / kStages) & 1u, err)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t base = smem_u32(stages + (size_t)s * kStageBytes);
+                    for (int ks = 0; ks < kb / 32; ++ks) {
+                        const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
+                        const uint32_t koff = (uint32_t)ks * 32u;
+                        if (m == 256) {
+                            // upper blocks: rows 0..127 x cols 0..255, rows 128..255 x cols 128..255
+                            const uint64_t a0 = smem_desc(base + koff, sbo, prm.layout);
+                            const uint64_t a1 = smem_desc(base + 128u * (uint32_t)kb + koff, sbo, prm.layout);
+                            mma<BF16>(tbase, a0, a0, prm.idesc_n256, acc);
+                            mma<BF16>(tbase + 256u, a1, a1, prm.idesc_n128, acc);
+                        } else {
+                            const uint64_t a = smem_desc(base + koff, sbo, prm.layout);
+                            mma<BF16>(d0, a, a, prm.idesc_n128, acc);
+                        }
+                    }
+                    mma_commit(&empty[s]);  // the stage is free once these MMAs have read it
+                }
+                if (!ok)
+                    break;
+                mma_commit(&acc_full[b]);  // the accumulator is complete
+            }
+            if (!ok) {
+                // make sure no MMA is still writing TMEM before it is freed
+                mma_commit(&drain);
+                mbar_wait(&drain, 0u, err);
+            }
+        }
+    } else {
+        // ---- epilogue: warps 2..5 ----------------------------------------------
+        const int q = warp & 3;               // TMEM sub-partition this warp may read
+        const int t = q * 32 + lane;          // tile row (and TMEM lane)
+        uint32_t jt = 0;
+        for (int64_t j = blockIdx.x; j < prm.jobs; j += gridDim.x, ++jt) {
+            const int b = (int)(jt % (uint32_t)nacc);
+            if (!mbar_wait(&acc_full[b], (jt / (uint32_t)nacc) & 1u, err))
+                break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t lane_addr = tbase + ((uint32_t)(q * 32) << 16);
+            uint32_t acc = 0;
+            uint32_t v[32];
+            if (m == 256) {
+                // row t: columns t+1..255 of the first block; row 128+t: columns of the second
+                for (int c0 = 0; c0 < 256; c0 += 32) {
+                    tmem_ld32(lane_addr + (uint32_t)c0, v);
+                    acc += sq_above(v, c0, t);
+                }
+                for (int c0 = 0; c0 < 128; c0 += 32) {
+                    tmem_ld32(lane_addr + 256u + (uint32_t)c0, v);
+                    acc += sq_above(v, c0, t);
+                }
+            } else {
+                // row t belongs to matrix t / m of the tile; its block is columns [g*m, g*m + m)
+                const int g = t / m, r = t - g * m;
+                const uint32_t acc_col = (uint32_t)b * 128u;
+                for (int c0 = 0; c0 < m; c0 += 32) {
+                    tmem_ld32(lane_addr + acc_col + (uint32_t)(g * m + c0), v);
+                    acc += sq_above(v, c0, r);
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            acc = warp_sum(acc);
+            if (m <= 32) {
+                // one warp per matrix
+                const int64_t mat = (j * rows + (int64_t)q * 32) / m;
+                if (lane == 0 && mat < prm.P)
+                    prm.fit[mat] = acc;
+            } else if (lane == 0) {
+                // m = 64: warps 2g, 2g+1 hold matrix g of the tile; m >= 128: all four
+                const int g = (m == 64) ? (q >> 1) : 0;
+                const uint32_t need = (m == 64) ? 2u : 4u;
+                const int sl = (int)(jt & 1u);
+                atomicAdd(&part_sum[sl][g], acc);
+                __threadfence_block();
+                if (atomicAdd(&part_cnt[sl][g], 1u) + 1u == need) {
+                    const uint32_t total = atomicExch(&part_sum[sl][g], 0u);
+                    part_cnt[sl][g] = 0u;
+                    const int64_t mat = (j * rows) / m + g;
+                    if (mat < prm.P)
+                        prm.fit[mat] = total;
+                }
+            }
+            __syncwarp();
+            // the accumulator is released only after this job's partial sums are
+            // combined, so a later job cannot reuse the same combining slot early
+            mbar_arrive(&acc_empty[b]);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(tmem_cols)
+                     : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+uint32_t idesc(bool bf16, int n)
+{
+    uint32_t d = 0;
+    d |= 1u << 4;                          // accumulator F32
+    if (bf16)
+        d |= (1u << 7) | (1u << 10);       // A, B BF16 (kind::f16); E4M3 is 0 (kind::f8f6f4)
+    d |= (uint32_t)(n >> 3) << 17;         // N / 8
+    d |= (uint32_t)(128 >> 4) << 24;       // M / 16
+    return d;                              // both operands K-major, dense, no negation
+}
+
+} // namespace
+
 bool fitness_tc_supported(int storage, int m)
 {
-    (void)storage;
-    (void)m;
-    return false;
+    return (storage == ST_E4M3 || storage == ST_BF16) && (m == 32 || m == 64 || m == 128 || m == 256) &&
+           encode_fn() != nullptr;
 }
 
 cudaError_t launch_fitness_tc(const void *pop, int storage, int m, int64_t first, int64_t count, int kind,
                               uint32_t *fit, uint32_t *err, cudaStream_t s)
 {
-    (void)pop; (void)storage; (void)m; (void)first; (void)count; (void)kind; (void)fit; (void)err; (void)s;
-    return cudaErrorNotSupported;
+    if (kind != FIT_SQ || !fitness_tc_supported(storage, m))
+        return cudaErrorNotSupported;
+    if (count <= 0)
+        return cudaSuccess;
+    const bool bf16 = storage == ST_BF16;
+    const int esize = bf16 ? 2 : 1;
+    const int row_bytes = m * esize;
+    TcParams prm{};
+    prm.P = count;
+    prm.m = m;
+    prm.esize = esize;
+    prm.kb = row_bytes < 128 ? row_bytes : 128;
+    prm.nchunks = row_bytes / prm.kb;
+    prm.rows = m == 256 ? 256 : 128;
+    const int64_t total_rows = count * m;
+    prm.jobs = (total_rows + prm.rows - 1) / prm.rows;
+    prm.idesc_n128 = idesc(bf16, 128);
+    prm.idesc_n256 = idesc(bf16, 256);
+    prm.layout = prm.kb == 128 ? 2u : prm.kb == 64 ? 4u : 6u;  // 128B, 64B, 32B swizzle
+    prm.fit = fit + first;
+    prm.err = err;
+
+    CUtensorMap map;
+    const cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)total_rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)row_bytes};
+    const cuuint32_t box[2] = {(cuuint32_t)(prm.kb / esize), 128u};
+    const cuuint32_t estr[2] = {1u, 1u};
+    const CUtensorMapSwizzle sw = prm.kb == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                  : prm.kb == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                                 : CU_TENSOR_MAP_SWIZZLE_32B;
+    const uint8_t *base = (const uint8_t *)pop + (size_t)first * m * row_bytes;
+    CUresult r = encode_fn()(&map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+                             (void *)base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    if (!err) {
+        // the launch's error word starts at zero
+        void *addr = nullptr;
+        cudaError_t e0 = cudaGetSymbolAddress(&addr, g_tc_err);
+        if (e0 == cudaSuccess)
+            e0 = cudaMemsetAsync(addr, 0, sizeof(uint32_t), s);
+        if (e0 != cudaSuccess)
+            return e0;
+    }
+    const size_t smem = (size_t)kStages * kStageBytes + 1024;
+    auto kern = bf16 ? k_fsq_tc<true> : k_fsq_tc<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t grid = prm.jobs < sms ? prm.jobs : sms;
+    kern<<<(unsigned)grid, kTcThreads, smem, s>>>(map, prm);
+    note_launches(1);
+    return cudaGetLastError();
 }
 
 } // namespace hadga
