@@ -13,13 +13,16 @@
 // 32/64/128-byte swizzle.
 //
 // Roles (warp specialised, one block per SM):
-//   warp 0   one thread issues the TMA copies into a ring of stages
-//   warp 1   allocates TMEM; one thread issues tcgen05.mma per stage and
-//            commits to the stage's "empty" barrier and, at the end of a
-//            job, to the accumulator's "full" barrier
-//   warps 2-5  read the accumulators with tcgen05.ld (warp w reads TMEM
-//            lanes 32(w%4)..32(w%4)+31 = tile rows), square and sum the
-//            entries above the diagonal of each matrix, free the
+//   warp 0   one thread issues the TMA copies into a ring of stages (up to
+//            32 stages of rows x chunk bytes within 160 KiB)
+//   warp 1   allocates all 512 TMEM columns; one thread issues tcgen05.mma
+//            per stage and commits to the stage's "empty" barrier and, at
+//            the end of a job, to the accumulator's "full" barrier (four
+//            128-column accumulators for m <= 128, one 384-column pair of
+//            blocks for m = 256)
+//   warps 2-9  two epilogue groups of four warps taking alternate jobs: read
+//            the accumulators with tcgen05.ld (warp w reads TMEM lanes
+//            32(w%4)..32(w%4)+31 = tile rows), square and sum, free the
 //            accumulator and write the fitness
 // Every mbarrier wait is bounded (about two seconds); on a timeout the block
 // records ERR_TIMEOUT, drains its outstanding copies with bounded waits,
@@ -33,9 +36,9 @@ namespace hadga {
 
 namespace {
 
-constexpr int kTcThreads = 192;  // 6 warps
-constexpr int kStages = 6;
-constexpr uint32_t kStageBytes = 32768;  // a chunk of up to 256 rows x 128 bytes
+constexpr int kTcThreads = 320;  // 10 warps: producer, MMA, two epilogue groups of four
+constexpr int kMaxStages = 32;
+constexpr uint32_t kRingBytes = 160 * 1024;  // shared memory of the stage ring
 constexpr unsigned long long kWaitBudgetNs = 2000000000ull;
 
 // Error word of launches that come without one (the stateless batch call).
@@ -48,6 +51,7 @@ struct TcParams {
     int32_t kb;         // chunk width in bytes (<= 128)
     int32_t nchunks;    // chunks per row
     int32_t rows;       // rows per job (128, or 256 for m = 256)
+    int32_t nstages;    // stages in the ring (each rows x kb bytes)
     int64_t jobs;
     uint32_t idesc_n128, idesc_n256;  // instruction descriptors
     uint32_t layout;    // smem descriptor layout type of the swizzle
@@ -148,6 +152,23 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar)
                  : "memory");
 }
 
+// 32 consecutive fp32 accumulator columns of this thread's TMEM lane, without
+// waiting (tmem_wait_ld completes every load issued so far).
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t (&v)[32])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                   "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                   "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                   "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                 : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 // 32 consecutive fp32 accumulator columns of this thread's TMEM lane.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
 {
@@ -163,17 +184,25 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Sum of squares of v[c] (as exact integers) over the columns c0 + c with
-// c0 + c > row.
-__device__ __forceinline__ uint32_t sq_above(const uint32_t (&v)[32], int c0, int row)
+// Sum of squares of U x 32 consecutive accumulator columns of this thread's
+// lane (exact: integer values, partial sums <= 2^24), four independent chains.
+template <int U>
+__device__ __forceinline__ float sq_cols(uint32_t taddr)
 {
-    uint32_t acc = 0;
+    uint32_t v[U][32];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) {
-        const int g = (int)__uint_as_float(v[c]);
-        acc += (c0 + c > row) ? (uint32_t)(g * g) : 0u;
-    }
-    return acc;
+    for (int u = 0; u < U; ++u)
+        tmem_ld32_nowait(taddr + (uint32_t)(u * 32), v[u]);
+    tmem_wait_ld();
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+            const float x = __uint_as_float(v[u][c]);
+            s[c & 3] = fmaf(x, x, s[c & 3]);
+        }
+    return (s[0] + s[1]) + (s[2] + s[3]);
 }
 
 } // namespace
@@ -185,25 +214,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
     extern __shared__ __align__(1024) uint8_t dyn_raw[];
     // 1024-byte alignment keeps every stage on the swizzle pattern's base
     uint8_t *stages = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dyn_raw) + 1023) & ~uintptr_t(1023));
-    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], acc_full[2], acc_empty[2], drain;
+    __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages], acc_full[4], acc_empty[4], drain;
     __shared__ uint32_t tmem_base;
-    __shared__ uint32_t part_sum[2][2], part_cnt[2][2];
+    __shared__ unsigned long long part_sum[4][2];
+    __shared__ uint32_t part_cnt[4][2];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m = prm.m, rows = prm.rows, nch = prm.nchunks, kb = prm.kb;
-    const int nacc = (m == 256) ? 1 : 2;
-    const uint32_t tmem_cols = (m == 256) ? 512u : 256u;
+    const int m = prm.m, rows = prm.rows, nch = prm.nchunks, kb = prm.kb, S = prm.nstages;
+    const uint32_t sbytes = (uint32_t)rows * (uint32_t)kb;  // bytes of one stage
+    const int nacc = (m == 256) ? 1 : 4;
+    const int ngroups = (m == 256) ? 1 : 2;
+    const uint32_t tmem_cols = 512u;
     uint32_t *err = prm.err ? prm.err : &g_tc_err;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+        for (int st = 0; st < S; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < 4; ++b) {
             mbar_init(&acc_full[b], 1);
             mbar_init(&acc_empty[b], 128);
-            part_sum[b][0] = part_sum[b][1] = 0u;
+            part_sum[b][0] = part_sum[b][1] = 0ull;
             part_cnt[b][0] = part_cnt[b][1] = 0u;
         }
         mbar_init(&drain, 1);
@@ -223,31 +255,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
     if (warp == 0) {
         // ---- TMA producer ----------------------------------------------------
         if (lane == 0) {
-            const uint32_t box_bytes = 128u * (uint32_t)kb;
             uint32_t it = 0;
-            int issued = 0;  // stages issued and not yet known consumed (for draining)
+            int issued = 0;
             bool ok = true;
             for (int64_t j = blockIdx.x; j < prm.jobs && ok; j += gridDim.x) {
-                for (int c = 0; c < nch && ok; ++c, ++it) {
-                    const int s = (int)(it % kStages);
-                    const uint32_t ph = (it / kStages) & 1u;
-                    if (!mbar_wait(&empty[s], ph ^ 1u, err)) {
+                for (int c = 0; c < nch; ++c, ++it) {
+                    const int st = (int)(it % (uint32_t)S);
+                    if (!mbar_wait(&empty[st], ((it / (uint32_t)S) & 1u) ^ 1u, err)) {
                         ok = false;
                         break;
                     }
-                    mbar_expect_tx(&full[s], box_bytes * (uint32_t)(rows / 128));
+                    mbar_expect_tx(&full[st], sbytes);
                     const int32_t x = c * (kb / prm.esize);
                     for (int h = 0; h < rows / 128; ++h)
-                        tma_load_2d(stages + (size_t)s * kStageBytes + (size_t)h * 128 * kb, &map, x,
-                                    (int32_t)(j * rows + h * 128), &full[s]);
-                    issued = issued < kStages ? issued + 1 : kStages;
+                        tma_load_2d(stages + (size_t)st * sbytes + (size_t)h * 128 * kb, &map, x,
+                                    (int32_t)(j * rows + h * 128), &full[st]);
+                    issued = issued < S ? issued + 1 : S;
                 }
             }
             if (!ok) {
                 // drain: let copies already in flight land before the block exits
                 for (int q = 0; q < issued; ++q) {
                     const uint32_t itq = it - 1u - (uint32_t)q;
-                    mbar_wait(&full[itq % kStages], (itq / kStages) & 1u, err);
+                    mbar_wait(&full[itq % (uint32_t)S], (itq / (uint32_t)S) & 1u, err);
                 }
             }
         }
@@ -259,21 +289,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
             bool ok = true;
             for (int64_t j = blockIdx.x; j < prm.jobs && ok; j += gridDim.x, ++jt) {
                 const int b = (int)(jt % (uint32_t)nacc);
-                const uint32_t bph = (jt / (uint32_t)nacc) & 1u;
-                if (!mbar_wait(&acc_empty[b], bph ^ 1u, err)) {
+                if (!mbar_wait(&acc_empty[b], ((jt / (uint32_t)nacc) & 1u) ^ 1u, err)) {
                     ok = false;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t d0 = tbase + (uint32_t)b * 128u;
                 for (int c = 0; c < nch; ++c, ++it) {
-                    const int s = (int)(it % kStages);
-                    if (!mbar_wait(&full[s], (it / kStages) & 1u, err)) {
+                    const int st = (int)(it % (uint32_t)S);
+                    if (!mbar_wait(&full[st], (it / (uint32_t)S) & 1u, err)) {
                         ok = false;
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t base = smem_u32(stages + (size_t)s * kStageBytes);
+                    const uint32_t base = smem_u32(stages + (size_t)st * sbytes);
                     for (int ks = 0; ks < kb / 32; ++ks) {
                         const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
                         const uint32_t koff = (uint32_t)ks * 32u;
@@ -288,7 +317,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
                             mma<BF16>(d0, a, a, prm.idesc_n128, acc);
                         }
                     }
-                    mma_commit(&empty[s]);  // the stage is free once these MMAs have read it
+                    mma_commit(&empty[st]);  // the stage is free once these MMAs have read it
                 }
                 if (!ok)
                     break;
@@ -301,63 +330,66 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
             }
         }
     } else {
-        // ---- epilogue: warps 2..5 ----------------------------------------------
+        // ---- epilogue: warps 2..5 (group 0) and 6..9 (group 1) --------------------
+        // Sum over r < s of R_rs^2 = (sum over all r, s of R_rs^2 - m^3) / 2 (the
+        // diagonal is m): each thread squares and adds every accumulator of its row
+        // block with one FFMA per entry; partial sums stay integers <= 2^24, exact.
+        const int grp = (warp - 2) >> 2;      // epilogue group
         const int q = warp & 3;               // TMEM sub-partition this warp may read
         const int t = q * 32 + lane;          // tile row (and TMEM lane)
-        uint32_t jt = 0;
-        for (int64_t j = blockIdx.x; j < prm.jobs; j += gridDim.x, ++jt) {
-            const int b = (int)(jt % (uint32_t)nacc);
-            if (!mbar_wait(&acc_full[b], (jt / (uint32_t)nacc) & 1u, err))
-                break;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t lane_addr = tbase + ((uint32_t)(q * 32) << 16);
-            uint32_t acc = 0;
-            uint32_t v[32];
-            if (m == 256) {
-                // row t: columns t+1..255 of the first block; row 128+t: columns of the second
-                for (int c0 = 0; c0 < 256; c0 += 32) {
-                    tmem_ld32(lane_addr + (uint32_t)c0, v);
-                    acc += sq_above(v, c0, t);
+        if (grp < ngroups) {
+            uint32_t jt = 0;
+            for (int64_t j = blockIdx.x; j < prm.jobs; j += gridDim.x, ++jt) {
+                if ((int)(jt % (uint32_t)ngroups) != grp)
+                    continue;
+                const int b = (int)(jt % (uint32_t)nacc);
+                if (!mbar_wait(&acc_full[b], (jt / (uint32_t)nacc) & 1u, err))
+                    break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t lane_addr = tbase + ((uint32_t)(q * 32) << 16);
+                float sum_a = 0.f, sum_b = 0.f;
+                if (m == 256) {
+                    // row t of the first block: columns 0..127 count once, 128..255 twice
+                    // (their mirror images below the diagonal are not computed); row
+                    // 128 + t of the second block: its 128 columns once
+                    sum_a = sq_cols<4>(lane_addr);
+                    sum_b = sq_cols<4>(lane_addr + 128u);
+                    sum_a += sq_cols<4>(lane_addr + 256u);
+                } else {
+                    const int g = t / m;
+                    const uint32_t col0 = lane_addr + (uint32_t)b * 128u + (uint32_t)(g * m);
+                    sum_a = m == 32 ? sq_cols<1>(col0) : m == 64 ? sq_cols<2>(col0) : sq_cols<4>(col0);
                 }
-                for (int c0 = 0; c0 < 128; c0 += 32) {
-                    tmem_ld32(lane_addr + 256u + (uint32_t)c0, v);
-                    acc += sq_above(v, c0, t);
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                unsigned long long tot = (unsigned long long)(uint32_t)sum_a + 2ull * (uint32_t)sum_b;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+                    tot += __shfl_xor_sync(0xFFFFFFFFu, tot, o);
+                const unsigned long long m3 = (unsigned long long)m * m * m;
+                if (m <= 32) {
+                    // one warp per matrix
+                    const int64_t mat = (j * rows + (int64_t)q * 32) / m;
+                    if (lane == 0 && mat < prm.P)
+                        prm.fit[mat] = (uint32_t)((tot - m3) >> 1);
+                } else if (lane == 0) {
+                    // m = 64: warps of sub-partitions 2g, 2g+1 hold matrix g; m >= 128: all four
+                    const int g = (m == 64) ? (q >> 1) : 0;
+                    const uint32_t need = (m == 64) ? 2u : 4u;
+                    atomicAdd(&part_sum[b][g], tot);
+                    __threadfence_block();
+                    if (atomicAdd(&part_cnt[b][g], 1u) + 1u == need) {
+                        const unsigned long long all = atomicExch(&part_sum[b][g], 0ull);
+                        part_cnt[b][g] = 0u;
+                        const int64_t mat = (j * rows) / m + g;
+                        if (mat < prm.P)
+                            prm.fit[mat] = (uint32_t)((all - m3) >> 1);
+                    }
                 }
-            } else {
-                // row t belongs to matrix t / m of the tile; its block is columns [g*m, g*m + m)
-                const int g = t / m, r = t - g * m;
-                const uint32_t acc_col = (uint32_t)b * 128u;
-                for (int c0 = 0; c0 < m; c0 += 32) {
-                    tmem_ld32(lane_addr + acc_col + (uint32_t)(g * m + c0), v);
-                    acc += sq_above(v, c0, r);
-                }
+                __syncwarp();
+                // released only after this job's partial sums are combined, so the
+                // next job on this accumulator cannot reuse its combining slot early
+                mbar_arrive(&acc_empty[b]);
             }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            acc = warp_sum(acc);
-            if (m <= 32) {
-                // one warp per matrix
-                const int64_t mat = (j * rows + (int64_t)q * 32) / m;
-                if (lane == 0 && mat < prm.P)
-                    prm.fit[mat] = acc;
-            } else if (lane == 0) {
-                // m = 64: warps 2g, 2g+1 hold matrix g of the tile; m >= 128: all four
-                const int g = (m == 64) ? (q >> 1) : 0;
-                const uint32_t need = (m == 64) ? 2u : 4u;
-                const int sl = (int)(jt & 1u);
-                atomicAdd(&part_sum[sl][g], acc);
-                __threadfence_block();
-                if (atomicAdd(&part_cnt[sl][g], 1u) + 1u == need) {
-                    const uint32_t total = atomicExch(&part_sum[sl][g], 0u);
-                    part_cnt[sl][g] = 0u;
-                    const int64_t mat = (j * rows) / m + g;
-                    if (mat < prm.P)
-                        prm.fit[mat] = total;
-                }
-            }
-            __syncwarp();
-            // the accumulator is released only after this job's partial sums are
-            // combined, so a later job cannot reuse the same combining slot early
-            mbar_arrive(&acc_empty[b]);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -460,7 +492,12 @@ cudaError_t launch_fitness_tc(const void *pop, int storage, int m, int64_t first
         if (e0 != cudaSuccess)
             return e0;
     }
-    const size_t smem = (size_t)kStages * kStageBytes + 1024;
+    {
+        const uint32_t sb = (uint32_t)prm.rows * (uint32_t)prm.kb;
+        uint32_t ns = kRingBytes / sb;
+        prm.nstages = (int32_t)(ns > (uint32_t)kMaxStages ? kMaxStages : ns);
+    }
+    const size_t smem = (size_t)prm.nstages * prm.rows * prm.kb + 1024;
     auto kern = bf16 ? k_fsq_tc<true> : k_fsq_tc<false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
