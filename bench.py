@@ -252,6 +252,68 @@ def gram_sweep(args):
             torch.cuda.empty_cache()
 
 
+MIXED_ORDERS = (12, 16, 20, 24, 28, 32, 36)
+
+
+def mixed_workload(args):
+    """Batched mixed orders in one persistent launch: one population per
+    order m in {12, ..., 36}, P = 4(500 + U[0, 4500]) each (Philox stream
+    CONFIG, seed 3; pop_id = order position), F_sq, NC = NR = 1, 500
+    generations as CUDA-graph replays of 50-generation chunks, block count
+    from the autotuner.  Prints one JSON line."""
+    import torch
+
+    import oracle
+    from paper_2208_14961_gb300.build import build
+    build()
+    from paper_2208_14961_gb300 import autotune
+    from paper_2208_14961_gb300 import hadga as h
+
+    specs = [(m, oracle.mixed_N(3, i)) for i, m in enumerate(MIXED_ORDERS)]
+    stream = torch.cuda.Stream()
+    blocks = autotune.tune_fused_grid(specs, stream=stream)
+
+    def fresh():
+        pops = []
+        for i, (m, N) in enumerate(specs):
+            p = h.Population(m, N, seed=3, pop_id=i, fitness=h.FIT_SQ, storage=h.STORE_BITS, traj_cap=512,
+                             stream=stream)
+            p.init_population()
+            p.fitness()
+            pops.append(p)
+        h.set_fused_grid(pops[0], blocks)
+        return pops
+
+    gens, chunk = args.mixed_gens, 50
+    pops = fresh()
+    h.step_multi_graph(pops, chunk, chunk)  # warm-up (also builds the graph path once)
+    torch.cuda.synchronize()
+    pops = fresh()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    h.step_multi_graph(pops, gens, chunk)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    total_P = sum(4 * N for _, N in specs)
+    exact = None
+    if args.mixed_check:
+        exact = True
+        for i, ((m, N), p) in enumerate(zip(specs, pops)):
+            ref = oracle.init_population(m, 4 * N, 3, i)
+            F = oracle.fitness(ref, oracle.FIT_SQ)
+            oracle.run(ref, F, N, 1, 1, oracle.FIT_SQ, 3, i, 0, gens)
+            exact = exact and bool((p.as_int8() == ref).all()) and bool((p.fitness_host() == F).all())
+    line = {"workload": "mixed orders 12..36 in one persistent launch", "orders": list(MIXED_ORDERS),
+            "P": [4 * N for _, N in specs], "generations": gens, "graph_chunk": chunk, "autotuned_blocks": blocks,
+            "ms": ms, "generations_per_s": gens / (ms / 1e3),
+            "evals_per_s": gens * (total_P // 2) / (ms / 1e3), "exact_vs_oracle": exact}
+    for p in pops:
+        p.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -264,9 +326,15 @@ def main():
     ap.add_argument("--gram-gb", type=float, default=8.0)
     ap.add_argument("--gram-ms", default="32,64,128,256")
     ap.add_argument("--gram-paths", default="")
+    ap.add_argument("--mixed", action="store_true", help="mixed-order multi-population workload")
+    ap.add_argument("--mixed-gens", type=int, default=500)
+    ap.add_argument("--mixed-check", action="store_true")
     args = ap.parse_args()
     if args.gram_sweep:
         gram_sweep(args)
+        return
+    if args.mixed:
+        mixed_workload(args)
         return
     args.warmup = max(args.warmup, 3)
 

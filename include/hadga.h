@@ -72,7 +72,7 @@ typedef enum {
 /* How the Gram contraction of ga_fitness / ga_fitness_batch is computed.
  * Every path is exact; they differ only in speed and accepted storage. */
 typedef enum {
-    GA_PATH_AUTO = 0,   /* fastest exact path for the storage */
+    GA_PATH_AUTO = 0,   /* fastest measured exact path for storage, m and fitness */
     GA_PATH_INT32 = 1,  /* int8 storage, CUDA-core 8-bit dot products */
     GA_PATH_IMMA = 2,   /* int8 storage, warp-level int8 tensor-core MMA */
     GA_PATH_FP8 = 3,    /* e4m3 storage, tcgen05 tensor cores, FP32 accumulate */
@@ -172,6 +172,19 @@ ga_status ga_step(ga_ctx *ctx, int32_t generations, int32_t stop_at_zero, int32_
  * generation of every population runs in the same persistent launch.  All
  * contexts must share the stream and device and use BITS or INT8 storage. */
 ga_status ga_step_multi(ga_ctx *const *ctxs, int32_t n, int32_t generations);
+
+/* Like ga_step_multi, with the generations run as replays of one captured
+ * CUDA graph of `chunk` generations (even, 2..64): the survivor orders, the
+ * state resets and the persistent launch of a chunk are captured once and
+ * replayed generations / chunk times; generation numbers are read from
+ * device-side counters, so every replay continues where the last one
+ * stopped.  A remainder runs through ga_step_multi.  Needs BITS contexts
+ * on one non-default stream; results equal ga_step_multi. */
+ga_status ga_step_multi_graph(ga_ctx *const *ctxs, int32_t n, int32_t generations, int32_t chunk);
+
+/* Number of persistent blocks of the fused kernel for launches led by ctx
+ * (0 = one per SM, the default).  Chosen by the autotuner. */
+ga_status ga_set_fused_grid(ga_ctx *ctx, int32_t blocks);
 
 /* 1 if ga_step runs the fused kernel for this context, 0 if it falls back. */
 int32_t ga_step_is_fused(const ga_ctx *ctx);

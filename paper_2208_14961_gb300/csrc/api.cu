@@ -50,7 +50,8 @@ struct ga_ctx {
     uint32_t *bits[2] = {nullptr, nullptr};  // bit-storage ping-pong (int8 contexts)
     uint32_t *ffit = nullptr;                 // second fitness buffer
     uint32_t *fstate = nullptr;               // kFusedStateWords selection state
-    uint32_t *fmisc = nullptr;                // [0] grid-barrier counter, [1] generations done
+    uint32_t *fmisc = nullptr;                // [0] grid-barrier counter, [1] generations done, [2] generation
+    int fused_blocks = 0;                     // persistent blocks (0: one per SM)
     unsigned long long *ftmask = nullptr;
     uint32_t *fperm = nullptr;                // [chunk][2N] survivor orders
     int fused_ok = 0;
@@ -114,6 +115,22 @@ ga_status check_storage_m(ga_ctx *c, int32_t storage, int32_t m)
 // are computed together before the persistent launch.
 constexpr int kChunk = 64;
 
+// GA_PATH_AUTO by storage, order and fitness, from the measured Gram sweep
+// on GB300 (8 and 32 GiB populations, m = 32..256): bit storage always takes
+// popcount; int8 takes the int8 tensor-core row Gram for F_sq up to m = 128
+// (at m = 256 the legacy int8 MMA rate falls behind popcount) and popcount
+// otherwise; e4m3 / bf16 storage take the tcgen05 paths.
+int auto_path(int storage, int m, int kind)
+{
+    if (storage == GA_STORE_E4M3)
+        return GA_PATH_FP8;
+    if (storage == GA_STORE_BF16)
+        return GA_PATH_BF16;
+    if (storage == GA_STORE_INT8 && kind == GA_FIT_SQ && m % 32 == 0 && m <= 128)
+        return GA_PATH_IMMA;
+    return GA_PATH_POPC;
+}
+
 } // namespace
 
 extern "C" {
@@ -153,7 +170,7 @@ ga_status ga_create(const ga_config *cfg, void *pop_dev, uint32_t *fit_dev, void
         return set_error(nullptr, GA_EINVAL, "traj_cap must be >= 1");
     if (cfg->reserved != 0)
         return set_error(nullptr, GA_EINVAL, "reserved must be 0");
-    int path = cfg->path == GA_PATH_AUTO ? GA_PATH_POPC : cfg->path;
+    int path = cfg->path == GA_PATH_AUTO ? auto_path(cfg->storage, cfg->m, cfg->fitness) : cfg->path;
     if (!fitness_path_supported(cfg->storage, cfg->m, path))
         return set_error(nullptr, GA_EINVAL, "Gram path %d does not read storage %d", cfg->path, cfg->storage);
     if (!pop_dev || !fit_dev)
@@ -372,7 +389,8 @@ int32_t ga_step_is_fused(const ga_ctx *ctx) { return ctx ? ctx->fused_ok : 0; }
 
 // Runs `generations` generations of ctxs[0..n) with the persistent kernel,
 // in chunks of kChunk generations (survivor orders of a chunk first).
-static ga_status fused_run(ga_ctx *const *ctxs, int n, int32_t generations, int stop_at_zero, int32_t *done_out)
+static ga_status fused_run(ga_ctx *const *ctxs, int n, int32_t generations, int stop_at_zero, int32_t *done_out,
+                           bool sync_gen = true, bool tail = true)
 {
     ga_ctx *c0 = ctxs[0];
     FusedParams prm;
@@ -392,6 +410,7 @@ static ga_status fused_run(ga_ctx *const *ctxs, int n, int32_t generations, int 
         p.tmask = c->ftmask;
         p.perm = c->fperm;
         p.traj = c->traj;
+        p.gen_dev = c->fmisc + 2;
         p.m = c->m;
         p.W = c->W;
         p.NC = c->cfg.NC;
@@ -417,6 +436,11 @@ static ga_status fused_run(ga_ctx *const *ctxs, int n, int32_t generations, int 
             if (e != cudaSuccess)
                 return cuda_check(c0, e, "convert to bit storage");
         }
+        if (sync_gen) {
+            cudaError_t e = launch_set_u32(c->fmisc + 2, c->gen, c0->stream);
+            if (e != cudaSuccess)
+                return cuda_check(c0, e, "generation counter");
+        }
     }
     if (tiles > kFusedMaxTiles)
         return set_error(c0, GA_EUNSUPPORTED, "populations too large for one persistent launch");
@@ -433,6 +457,8 @@ static ga_status fused_run(ga_ctx *const *ctxs, int n, int32_t generations, int 
     cudaError_t e = fused_grid(smem, &grid);
     if (e != cudaSuccess)
         return cuda_check(c0, e, "fused kernel occupancy");
+    if (c0->fused_blocks > 0 && c0->fused_blocks < grid)
+        grid = c0->fused_blocks;
 
     int cur = 0;
     int32_t total_done = 0;
@@ -447,7 +473,7 @@ static ga_status fused_run(ga_ctx *const *ctxs, int n, int32_t generations, int 
                 cudaEventRecord(ev[0], c0->stream);
             }
             e = launch_perm_table((uint32_t)(2 * c->N), c->cfg.seed, c->cfg.pop_id, c->gen + 1u, chunk, c->fperm,
-                                  c0->stream);
+                                  c0->stream, c->fmisc + 2);
             if (c->profiling) {
                 cudaEventRecord(ev[1], c0->stream);
                 c->prof_perm.push_back(ev[0]);
@@ -461,7 +487,6 @@ static ga_status fused_run(ga_ctx *const *ctxs, int n, int32_t generations, int 
         e = cudaMemsetAsync(c0->fmisc, 0, 2 * sizeof(uint32_t), c0->stream);
         if (e != cudaSuccess)
             return cuda_check(c0, e, "barrier reset");
-        prm.gen0 = c0->gen;
         prm.ngen = chunk;
         prm.src = cur;
         cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -498,7 +523,7 @@ static ga_status fused_run(ga_ctx *const *ctxs, int n, int32_t generations, int 
         if (ran < chunk)
             break;
     }
-    for (int i = 0; i < n; ++i) {
+    for (int i = 0; i < n && tail; ++i) {
         ga_ctx *c = ctxs[i];
         const bool int8 = c->cfg.storage == GA_STORE_INT8;
         if (int8) {
@@ -620,6 +645,79 @@ ga_status ga_profile_read(ga_ctx *ctx, float *perm_ms, float *fused_ms, int32_t 
     *perm_ms = sum_pairs(ctx->prof_perm);
     *fused_ms = sum_pairs(ctx->prof_fused);
     *fused_launches = (int32_t)(ctx->prof_fused.size() / 2);
+    return GA_OK;
+}
+
+ga_status ga_step_multi_graph(ga_ctx *const *ctxs, int32_t n, int32_t generations, int32_t chunk)
+{
+    if (!ctxs || n < 1 || n > kMaxPops)
+        return set_error(nullptr, GA_EINVAL, "ctxs must hold 1..%d contexts", kMaxPops);
+    if (generations < 0 || chunk < 2 || chunk > kChunk || (chunk & 1))
+        return set_error(nullptr, GA_EINVAL, "chunk must be even and in [2, %d]", kChunk);
+    for (int32_t i = 0; i < n; ++i) {
+        if (!ctxs[i])
+            return set_error(nullptr, GA_EINVAL, "context %d is NULL", i);
+        if (ctxs[i]->stream != ctxs[0]->stream || ctxs[i]->device != ctxs[0]->device)
+            return set_error(nullptr, GA_EINVAL, "contexts must share stream and device");
+        if (!ctxs[i]->fused_ok || ctxs[i]->cfg.storage != GA_STORE_BITS)
+            return set_error(nullptr, GA_EUNSUPPORTED, "graph replay needs fused-capable BITS contexts");
+        if (!ctxs[i]->stream)
+            return set_error(nullptr, GA_EINVAL, "graph capture needs a non-default stream");
+    }
+    ga_status st = begin(ctxs[0]);
+    if (st != GA_OK)
+        return st;
+    ga_ctx *c0 = ctxs[0];
+    const int32_t reps = generations / chunk, rem = generations % chunk;
+    if (reps > 0) {
+        // device generation counters take over from here
+        for (int32_t i = 0; i < n; ++i) {
+            cudaError_t e = launch_set_u32(ctxs[i]->fmisc + 2, ctxs[i]->gen, c0->stream);
+            if (e != cudaSuccess)
+                return set_error(nullptr, GA_ECUDA, "generation counter: %s", cudaGetErrorString(e));
+        }
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(c0->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess)
+            return set_error(nullptr, GA_ECUDA, "begin capture: %s", cudaGetErrorString(e));
+        // one chunk, even length: the ping-pong buffers end where they started
+        st = fused_run(ctxs, n, chunk, 0, nullptr, false, false);
+        e = cudaStreamEndCapture(c0->stream, &graph);
+        if (st != GA_OK || e != cudaSuccess) {
+            if (graph)
+                cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return set_error(nullptr, st != GA_OK ? st : GA_ECUDA, "capture of a chunk failed: %s",
+                             st != GA_OK ? ga_last_error(c0) : cudaGetErrorString(e));
+        }
+        // the capture advanced the host counters without running; undo that
+        for (int32_t i = 0; i < n; ++i)
+            ctxs[i]->gen -= (uint32_t)chunk;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e == cudaSuccess) {
+            for (int32_t r = 0; r < reps && e == cudaSuccess; ++r)
+                e = cudaGraphLaunch(exec, c0->stream);
+            cudaGraphExecDestroy(exec);
+        }
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess)
+            return set_error(nullptr, GA_ECUDA, "graph replay: %s", cudaGetErrorString(e));
+        // the capture counted one chunk's kernels once; every replay runs them
+        note_launches((reps - 1) * (n + 1));
+        for (int32_t i = 0; i < n; ++i)
+            ctxs[i]->gen += (uint32_t)(reps * chunk);
+    }
+    if (rem > 0)
+        return ga_step_multi(ctxs, n, rem);
+    return GA_OK;
+}
+
+ga_status ga_set_fused_grid(ga_ctx *ctx, int32_t blocks)
+{
+    if (!ctx || blocks < 0)
+        return set_error(nullptr, GA_EINVAL, "bad context or block count");
+    ctx->fused_blocks = blocks;
     return GA_OK;
 }
 
@@ -784,7 +882,7 @@ ga_status ga_fitness_batch(const void *pop_dev, int32_t storage, int32_t m, int6
     if (kind < GA_FIT_SQ || kind > GA_FIT_NNZ)
         return set_error(nullptr, GA_EINVAL, "unknown fitness %d", kind);
     if (path == GA_PATH_AUTO)
-        path = (storage == GA_STORE_E4M3) ? GA_PATH_FP8 : (storage == GA_STORE_BF16) ? GA_PATH_BF16 : GA_PATH_POPC;
+        path = auto_path(storage, m, kind);
     cudaStream_t s = (cudaStream_t)stream;
     if (path == GA_PATH_FP8 || path == GA_PATH_BF16) {
         if ((path == GA_PATH_FP8) != (storage == GA_STORE_E4M3) || (path == GA_PATH_BF16) != (storage == GA_STORE_BF16))

@@ -46,6 +46,7 @@ struct PopSel {
     uint32_t lb, eb;      // joint (F < T, F == T) counts before the first tile of the population
     uint32_t capn, shiftn;  // histogram parameters of the next generation
     uint32_t boff;          // offset of this population's block histogram (~0: none)
+    uint32_t gen0;          // generation of the population before this launch
     uint32_t bor;           // block OR of the new fitness values
     unsigned long long bbest;  // block minimum of the new best keys
 };
@@ -535,7 +536,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
 
     // ---- pre-pass: max and OR of the current fitness of every population -----
     {
-        const int par0 = (int)((prm.gen0 + 1u) & 1u);
+        const int par0 = 0;  // buffers alternate with the generation index inside the launch
+        if (tid < npop)
+            S[tid].gen0 = ldcg32(prm.p[tid].gen_dev);
         for (int i = 0; i < npop; ++i) {
             const FusedPop &p = prm.p[i];
             const uint32_t P = (uint32_t)(4 * p.N);
@@ -581,8 +584,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
 
     uint32_t ref_level = 0;
     for (int t = 0; t < prm.ngen; ++t) {
-        const uint32_t gen = prm.gen0 + 1u + (uint32_t)t;
-        const int par = (int)(gen & 1u);
+        const int par = t & 1;
 
         // ---- phase A: threshold of the 2N smallest ---------------------------------
         // first tile of this warp: its fitness is loaded now, with the histograms
@@ -607,7 +609,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
         if (blockIdx.x == 0 && tid < npop) {
             const FusedPop &p = prm.p[tid];
             stat_of(p)[1 + (par ^ 1)] = 0u;
-            p.traj[(gen - 1u) % (uint32_t)p.traj_cap] = ~0ull;
+            p.traj[(S[tid].gen0 + (uint32_t)t) % (uint32_t)p.traj_cap] = ~0ull;
         }
         // histograms staged in shared memory (groups of populations that fit),
         // scanned in one block-wide pass, crossing of 2N located per population
@@ -742,7 +744,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                 const FusedPop &p = prm.p[i];
                 const uint32_t local = u - p.work_base, k = local >> 1;
                 if (k < (uint32_t)p.N)
-                    pre0 = make_pre(p, gen, (uint32_t)t, k, (int)(local & 1u));
+                    pre0 = make_pre(p, S[i].gen0 + 1u + (uint32_t)t, (uint32_t)t, k, (int)(local & 1u));
             }
         }
         // tile masks: F < T and F == T per 32 slots
@@ -815,6 +817,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             const uint32_t k = local >> 1;
             const int half = (int)(local & 1u);
             const bool valid = i >= 0 && k < (uint32_t)p.N;
+            const uint32_t gen = S[i < 0 ? 0 : i].gen0 + 1u + (uint32_t)t;
             Pre pre = pre0;
             if (w != gwarp && valid)
                 pre = make_pre(p, gen, (uint32_t)t, k, half);
@@ -865,6 +868,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             const FusedPop &p = prm.p[i];
             const uint32_t k = pr - p.work_base;
             uint32_t *hn = hist_of(p, par ^ 1);
+            const uint32_t gen = S[i].gen0 + 1u + (uint32_t)t;
             switch (p.W) {
             case 2: pair_warp<2>(p, S[i], src, gen, (uint32_t)t, k, sv, err, wbuf, hn, bhist); break;
             case 3: pair_warp<3>(p, S[i], src, gen, (uint32_t)t, k, sv, err, wbuf, hn, bhist); break;
@@ -891,7 +895,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             if (S[tid].bor)
                 atomicOr(stat_of(p) + 1 + (par ^ 1), S[tid].bor);
             if (S[tid].bbest != ~0ull)
-                atomicMin(p.traj + (gen - 1u) % (uint32_t)p.traj_cap, S[tid].bbest);
+                atomicMin(p.traj + (S[tid].gen0 + (uint32_t)t) % (uint32_t)p.traj_cap, S[tid].bbest);
         }
         if (!grid_barrier(prm.bar, nblocks, epoch, err))
             return;
@@ -903,7 +907,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
         done = t + 1;
         if (prm.stop_at_zero) {
             const FusedPop &p = prm.p[0];
-            const unsigned long long key = ldcg64(p.traj + (gen - 1u) % (uint32_t)p.traj_cap);
+            const unsigned long long key = ldcg64(p.traj + (S[0].gen0 + (uint32_t)t) % (uint32_t)p.traj_cap);
             if ((key >> 32) == 0ull)
                 break;
         }
@@ -911,6 +915,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
     }
     if (blockIdx.x == 0 && tid == 0)
         *prm.done = done;
+    if (blockIdx.x == 0 && tid < npop)
+        *prm.p[tid].gen_dev = S[tid].gen0 + (uint32_t)done;
 }
 
 size_t fused_smem_bytes(const FusedParams &p)

@@ -175,12 +175,22 @@ __device__ void perm_block(uint32_t n, uint32_t seed, uint32_t pop_id, uint32_t 
 }
 
 __global__ void __launch_bounds__(1024) k_perm_smem(uint32_t n, uint32_t seed, uint32_t pop_id, uint32_t gen0,
-                                                    uint32_t *out)
+                                                    uint32_t *out, const uint32_t *gen_dev)
 {
     extern __shared__ __align__(16) unsigned long long s_keys[];
     __shared__ uint32_t s_cnt[1 << kPermSmemBits], s_off[1 << kPermSmemBits], s_tmp[33];
-    perm_block(n, seed, pop_id, gen0 + blockIdx.x, out + (size_t)blockIdx.x * n, s_keys, s_cnt, s_off,
+    const uint32_t g0 = gen_dev ? *gen_dev + 1u : gen0;
+    perm_block(n, seed, pop_id, g0 + blockIdx.x, out + (size_t)blockIdx.x * n, s_keys, s_cnt, s_off,
                kPermSmemBits, s_tmp);
+}
+
+__global__ void k_set_u32(uint32_t *p, uint32_t v) { *p = v; }
+
+cudaError_t launch_set_u32(uint32_t *p, uint32_t v, cudaStream_t s)
+{
+    k_set_u32<<<1, 1, 0, s>>>(p, v);
+    note_launches(1);
+    return cudaGetLastError();
 }
 
 __global__ void __launch_bounds__(1024) k_perm_global(uint32_t n, uint32_t seed, uint32_t pop_id, uint32_t gen,
@@ -201,7 +211,7 @@ int perm_global_bits(uint32_t n)
 }
 
 cudaError_t launch_perm_table(uint32_t n, uint32_t seed, uint32_t pop_id, uint32_t gen0, int ngen, uint32_t *out,
-                              cudaStream_t s)
+                              cudaStream_t s, const uint32_t *gen_dev)
 {
     if (n > kPermSmemMax || ngen <= 0)
         return cudaErrorInvalidValue;
@@ -210,7 +220,7 @@ cudaError_t launch_perm_table(uint32_t n, uint32_t seed, uint32_t pop_id, uint32
                                          (int)(kPermSmemMax * sizeof(unsigned long long)));
     if (e != cudaSuccess)
         return e;
-    k_perm_smem<<<ngen, 1024, smem, s>>>(n, seed, pop_id, gen0, out);
+    k_perm_smem<<<ngen, 1024, smem, s>>>(n, seed, pop_id, gen0, out, gen_dev);
     note_launches(1);
     return cudaGetLastError();
 }

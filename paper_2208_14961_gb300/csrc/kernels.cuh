@@ -80,10 +80,14 @@ struct SelWork {
 cudaError_t launch_select(const void *pop, const uint32_t *fit, int64_t N, size_t mat_bytes, uint32_t seed,
                           uint32_t pop_id, uint32_t gen, const SelWork &w, void *scratch_pop, uint32_t *scratch_fit,
                           cudaStream_t s);
-// Survivor orders pi of `ngen` consecutive generations gen0.. into out[ngen][n]
-// (n <= kPermSmemMax), one block per generation.
+// Survivor orders pi of `ngen` consecutive generations into out[ngen][n]
+// (n <= kPermSmemMax), one block per generation.  The first generation is
+// gen0, or *gen_dev + 1 when gen_dev is not null (a device-side counter, so
+// that a captured launch sequence can be replayed).
 cudaError_t launch_perm_table(uint32_t n, uint32_t seed, uint32_t pop_id, uint32_t gen0, int ngen, uint32_t *out,
-                              cudaStream_t s);
+                              cudaStream_t s, const uint32_t *gen_dev = nullptr);
+// *p = v, as a one-thread kernel (stream-ordered, capturable).
+cudaError_t launch_set_u32(uint32_t *p, uint32_t v, cudaStream_t s);
 int perm_global_bits(uint32_t n);
 
 // ---- fused persistent generation kernel (k_fused.cu) -------------------------
@@ -106,6 +110,7 @@ struct FusedPop {
     unsigned long long *tmask; // [ntiles] (F < T) | (F == T) << 32 per tile
     const uint32_t *perm;      // [ngen][2N] survivor orders of the chunk
     unsigned long long *traj;  // [traj_cap] best keys (F << 32 | slot)
+    uint32_t *gen_dev;         // generation counter: read at start, advanced at exit
     int32_t m, W, NC, NR, kind, traj_cap;
     int64_t N;
     uint32_t seed, pop_id;
@@ -119,7 +124,6 @@ struct FusedParams {
     uint32_t total_tiles;
     uint32_t thread_slots;   // joint space of m <= 32 populations, 2 threads per pair, padded to 32
     uint32_t warp_pairs;     // joint pair space of m > 32 populations
-    uint32_t gen0;           // generation number before the chunk
     int32_t ngen;            // generations to run
     int32_t stop_at_zero;    // stop after a generation whose best fitness (population 0) is 0
     int32_t src;             // ping-pong buffer holding the current population

@@ -64,6 +64,8 @@ SIGNATURES = {
     "ga_step": (_i32, [_vp, _i32, _i32, ctypes.POINTER(_i32)]),
     "ga_step_multi": (_i32, [ctypes.POINTER(_vp), _i32, _i32]),
     "ga_step_is_fused": (_i32, [_vp]),
+    "ga_step_multi_graph": (_i32, [ctypes.POINTER(_vp), _i32, _i32, _i32]),
+    "ga_set_fused_grid": (_i32, [_vp, _i32]),
     "ga_best": (_i32, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_u32)]),
     "ga_trajectory": (_i32, [_vp, _vp, _vp, _i32, ctypes.POINTER(_i32)]),
     "ga_generation": (_i32, [_vp, ctypes.POINTER(_u32)]),
@@ -315,3 +317,12 @@ class Population:
 def step_multi(pops, generations: int):
     arr = (ctypes.c_void_p * len(pops))(*[p.ctx for p in pops])
     check(load().ga_step_multi(arr, len(pops), generations))
+
+
+def step_multi_graph(pops, generations: int, chunk: int = 50):
+    arr = (ctypes.c_void_p * len(pops))(*[p.ctx for p in pops])
+    check(load().ga_step_multi_graph(arr, len(pops), generations, chunk))
+
+
+def set_fused_grid(pop, blocks: int):
+    check(load().ga_set_fused_grid(pop.ctx, blocks))

@@ -136,3 +136,53 @@ def test_multi_population_mixed_orders_one_launch():
         assert np.array_equal(p.fitness_host(), F)
         gtf, gts = p.trajectory()
         assert np.array_equal(gtf.astype(np.uint64), tf) and np.array_equal(gts, ts)
+
+
+def test_graph_replay_equals_oracle():
+    """CUDA-graph replays of 10-generation chunks (device generation
+    counters), then a plain remainder, equal the oracle run."""
+    h = need_gpu()
+    stream = torch.cuda.Stream()
+    specs = [(12, 50), (20, 61), (36, 23)]
+    pops = []
+    for i, (m, N) in enumerate(specs):
+        p = h.Population(m, N, seed=4, pop_id=i, fitness=0, storage=1, traj_cap=64, stream=stream)
+        p.init_population()
+        p.fitness()
+        pops.append(p)
+    h.step_multi_graph(pops, 35, 10)     # 3 replays of 10 + 5 through ga_step_multi
+    for p in pops:
+        p.step_plain(2)
+    torch.cuda.synchronize()
+    for i, ((m, N), p) in enumerate(zip(specs, pops)):
+        ref = oracle.init_population(m, 4 * N, 4, i)
+        F = oracle.fitness(ref, 0)
+        _, tf, ts = oracle.run(ref, F, N, 1, 1, 0, 4, i, 0, 37)
+        assert p.generation() == 37
+        assert np.array_equal(p.as_int8(), ref)
+        assert np.array_equal(p.fitness_host(), F)
+        gtf, gts = p.trajectory()
+        assert np.array_equal(gtf.astype(np.uint64), tf) and np.array_equal(gts, ts)
+
+
+def test_fused_grid_setting_does_not_change_results():
+    h = need_gpu()
+    out = []
+    for blocks in (0, 37):
+        p = h.Population(20, 700, seed=8, storage=1, traj_cap=16)
+        h.set_fused_grid(p, blocks)
+        p.init_population()
+        p.fitness()
+        p.step(16)
+        p.sync()
+        out.append((p.as_int8(), p.fitness_host()))
+        p.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_config2_full_1000_generations_fused():
+    """m = 20, P = 40,000, seed 1: all 1,000 generations, fused kernel,
+    bit-exact with the oracle (population, fitness, best trajectory)."""
+    h = need_gpu()
+    gpu = _run_gpu(h, 20, 10000, 1, 1000, 1, "fused")
+    _assert_same(gpu, _run_oracle(20, 10000, 1, 1000))
