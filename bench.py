@@ -314,6 +314,81 @@ def mixed_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def incremental_workload(args):
+    """Incremental Gram-delta fitness (a7) on m=100, P=20,000 bit-packed
+    balanced matrices (seed 4, F_sq, NC = NR = 1) for `--inc-gens`
+    generations (default 10,000) in ga_step calls of 100 generations.  After
+    every call a full recomputation of every slot's Gram and fitness on the
+    GPU is compared with the incrementally kept values; the population after
+    the first 100 generations is compared with the oracle's; the same run
+    with full recomputation gives the comparison rate and must produce the
+    same best-fitness trajectory.  Prints one JSON line."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2208_14961_gb300.build import build
+    build()
+    from paper_2208_14961_gb300 import hadga as h
+
+    m, N, seed, every = 100, 5000, 4, 100
+    gens = max(every, args.inc_gens // every * every)
+    stream = torch.cuda.Stream()
+
+    def fresh(inc):
+        p = h.Population(m, N, seed=seed, fitness=h.FIT_SQ, storage=h.STORE_BITS, traj_cap=gens, stream=stream)
+        p.init_population()
+        p.fitness()
+        if inc:
+            p.set_incremental(True)
+        p.sync()
+        return p
+
+    w = fresh(True)
+    w.step(every)
+    w.sync()
+    w.close()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out, trajs, snap = {}, {}, None
+    checks, mismatches = 0, 0
+    for mode in ("incremental", "full"):
+        p = fresh(mode == "incremental")
+        ms = 0.0
+        for c in range(gens // every):
+            e0.record(stream)
+            p.step(every)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            if mode == "incremental":
+                ent, fit = p.check_incremental()
+                checks += 1
+                mismatches += ent + fit
+                if c == 0:
+                    snap = (p.as_int8(), p.fitness_host())
+        trajs[mode] = p.trajectory()[0].astype(np.uint64)
+        out[mode] = {"ms": ms, "generations_per_s": gens / (ms / 1e3),
+                     "evals_per_s": gens * 2 * N / (ms / 1e3)}
+        p.close()
+    ref = oracle.init_population(m, 4 * N, seed, 0)
+    F = oracle.fitness(ref, oracle.FIT_SQ)
+    oracle.run(ref, F, N, 1, 1, oracle.FIT_SQ, seed, 0, 0, every)
+    exact_prefix = bool((snap[0] == ref).all()) and bool((snap[1] == F).all())
+    t = trajs["incremental"]
+    marks = [g for g in (1, 10, 100, 1000, 10000, gens) if g <= len(t)]
+    line = {"workload": "m=100, P=20,000, bit storage, F_sq, NC=NR=1, seed 4, incremental Gram-delta fitness",
+            "generations": gens, "check_every": every,
+            "incremental": out["incremental"], "full_recompute": out["full"],
+            "incremental_over_full": out["full"]["ms"] / out["incremental"]["ms"],
+            "full_rechecks": checks, "recheck_mismatches": mismatches,
+            "oracle_prefix_generations": every, "exact_vs_oracle_prefix": exact_prefix,
+            "trajectories_equal": bool(np.array_equal(trajs["incremental"], trajs["full"])),
+            "best_fitness_at": {str(g): int(t[g - 1]) for g in sorted(set(marks))},
+            "gram_bytes": 4 * N * ((m * (m - 1) // 2 + 15) // 16 * 16),
+            "l2": "not flushed; population 32 MB + Gram 99 MB resident across calls"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -329,12 +404,17 @@ def main():
     ap.add_argument("--mixed", action="store_true", help="mixed-order multi-population workload")
     ap.add_argument("--mixed-gens", type=int, default=500)
     ap.add_argument("--mixed-check", action="store_true")
+    ap.add_argument("--incremental", action="store_true", help="incremental Gram-delta workload (m=100)")
+    ap.add_argument("--inc-gens", type=int, default=10000)
     args = ap.parse_args()
     if args.gram_sweep:
         gram_sweep(args)
         return
     if args.mixed:
         mixed_workload(args)
+        return
+    if args.incremental:
+        incremental_workload(args)
         return
     args.warmup = max(args.warmup, 3)
 
@@ -465,7 +545,7 @@ def main():
         per_launch_bytes = bytes_per_generation() * STEP_GENS
         achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_fused_generation", "peak_source": peak_kind,
+                "traffic": None, "kernel": "k_fused", "peak_source": peak_kind,
                 "launch_ms": per_launch_ms, "perm_table_ms_per_launch": perm_ms / max(fused_launches, 1)}
 
     cpu = None

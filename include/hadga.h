@@ -182,6 +182,36 @@ ga_status ga_step_multi(ga_ctx *const *ctxs, int32_t n, int32_t generations);
  * on one non-default stream; results equal ga_step_multi. */
 ga_status ga_step_multi_graph(ga_ctx *const *ctxs, int32_t n, int32_t generations, int32_t chunk);
 
+/* a7 -- incremental Gram-delta fitness.  The paper recomputes G = Q^T Q in
+ * full; this mode derives the same G from the operators' structure (the
+ * fitness of Sec. 3.2 under the crossover of Sec. 3.4 and the mutation of
+ * Sec. 3.5): a pair flip in column c changes only row and column c of G, by
+ * -2s(Q[r1][j] - Q[r2][j]) with s = Q[r1][c]; a column exchange at cut c
+ * keeps the blocks of G inside each parent's part.
+ * When enabled, the context keeps every individual's Gram (upper triangle
+ * of G / 2 as int8, m(m-1)/2 bytes rounded up to 16, in a separate device
+ * allocation of P times that) and the fused kernel builds each offspring's
+ * Gram from its parents' (only the c(m - c) cross entries recomputed) and
+ * applies each flip as an O(m) update of row/column c, with the fitness
+ * updated by the same deltas.  Results stay bit-identical to the full
+ * recomputation.  Needs BITS storage and 32 < m <= 128 on a fused-capable
+ * context (GA_EUNSUPPORTED otherwise).  Enabling (re)builds the Gram of the
+ * current population; ga_init_population, ga_set_slot and the one-kernel-
+ * per-operator calls mark it stale and the next ga_step rebuilds it.  After
+ * writing the population buffer directly, enable again.  enable = 0 frees
+ * the Gram storage. */
+ga_status ga_set_incremental(ga_ctx *ctx, int32_t enable);
+
+/* Full recomputation check of the incremental state: recomputes every
+ * slot's Gram entries and fitness from the population and counts the
+ * stored Gram entries (*entry_mismatch) and fitness words (*fit_mismatch)
+ * that differ.  Synchronises.  GA_EINVAL unless incremental mode is on. */
+ga_status ga_check_incremental(ga_ctx *ctx, uint64_t *entry_mismatch, uint64_t *fit_mismatch);
+
+/* Stored Gram of one slot in incremental mode, expanded to the full m x m
+ * int32 matrix G (diagonal m, symmetric) in host memory.  Synchronises. */
+ga_status ga_get_gram(ga_ctx *ctx, int64_t slot, int32_t *host_G);
+
 /* Number of persistent blocks of the fused kernel for launches led by ctx
  * (0 = one per SM, the default).  Chosen by the autotuner. */
 ga_status ga_set_fused_grid(ga_ctx *ctx, int32_t blocks);

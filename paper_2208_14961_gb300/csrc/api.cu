@@ -55,6 +55,14 @@ struct ga_ctx {
     unsigned long long *ftmask = nullptr;
     uint32_t *fperm = nullptr;                // [chunk][2N] survivor orders
     int fused_ok = 0;
+    // incremental Gram-delta mode (BITS, 32 < m <= 128)
+    int incremental = 0;
+    int gram_valid = 0;
+    int dpad = 0;
+    void *gram_mem = nullptr;                 // gram | gidx[0] | gidx[1] | counts
+    int8_t *gram = nullptr;
+    uint32_t *gidx[2] = {nullptr, nullptr};
+    unsigned long long *gcounts = nullptr;
 
     // opt-in event profile of ga_step's kernels
     int profiling = 0;
@@ -271,6 +279,7 @@ ga_status ga_destroy(ga_ctx *ctx)
     cudaStreamSynchronize(ctx->stream);
     drop_events(ctx->prof_perm);
     drop_events(ctx->prof_fused);
+    cudaFree(ctx->gram_mem);
     cudaFree(ctx->ws);
     delete ctx;
     return GA_OK;
@@ -296,6 +305,7 @@ ga_status ga_init_population(ga_ctx *ctx)
     if (st != GA_OK)
         return st;
     ctx->gen = 0;
+    ctx->gram_valid = 0;
     return cuda_check(ctx, cudaMemsetAsync(ctx->traj, 0xFF, (size_t)ctx->cfg.traj_cap * 8u, ctx->stream),
                       "trajectory reset");
 }
@@ -320,6 +330,7 @@ ga_status ga_select(ga_ctx *ctx)
     if (st != GA_OK)
         return st;
     const uint32_t g = ctx->gen + 1u;
+    ctx->gram_valid = 0;
     st = cuda_check(ctx,
                     launch_select(ctx->pop, ctx->fit, ctx->N, ctx->mat_bytes, ctx->cfg.seed, ctx->cfg.pop_id, g,
                                   ctx->sel, ctx->scratch_pop, ctx->scratch_fit, ctx->stream),
@@ -342,6 +353,7 @@ ga_status ga_crossover(ga_ctx *ctx)
     ga_status st = begin(ctx);
     if (st != GA_OK)
         return st;
+    ctx->gram_valid = 0;
     return cuda_check(ctx,
                       launch_crossover(ctx->pop, ctx->cfg.storage, ctx->m, ctx->N, ctx->cfg.seed, ctx->cfg.pop_id,
                                        ctx->gen, ctx->stream),
@@ -353,6 +365,7 @@ ga_status ga_mutate(ga_ctx *ctx)
     ga_status st = begin(ctx);
     if (st != GA_OK)
         return st;
+    ctx->gram_valid = 0;
     return cuda_check(ctx,
                       launch_mutate(ctx->pop, ctx->cfg.storage, ctx->m, ctx->N, ctx->cfg.NC, ctx->cfg.NR,
                                     ctx->cfg.seed, ctx->cfg.pop_id, ctx->gen, ctx->stream),
@@ -435,6 +448,20 @@ static ga_status fused_run(ga_ctx *const *ctxs, int n, int32_t generations, int 
             cudaError_t e = launch_convert(c->pop, GA_STORE_INT8, c->bits[0], GA_STORE_BITS, c->m, c->P, c0->stream);
             if (e != cudaSuccess)
                 return cuda_check(c0, e, "convert to bit storage");
+        }
+        p.gram = nullptr;
+        if (c->incremental) {
+            if (!c->gram_valid) {
+                cudaError_t e = launch_gram_store((const uint32_t *)c->pop, c->m, c->P, c->gram, c->dpad, c->gidx[0],
+                                                  c0->stream);
+                if (e != cudaSuccess)
+                    return cuda_check(c0, e, "Gram store");
+                c->gram_valid = 1;
+            }
+            p.gram = c->gram;
+            p.gidx[0] = c->gidx[0];
+            p.gidx[1] = c->gidx[1];
+            p.dpad = c->dpad;
         }
         if (sync_gen) {
             cudaError_t e = launch_set_u32(c->fmisc + 2, c->gen, c0->stream);
@@ -534,6 +561,8 @@ static ga_status fused_run(ga_ctx *const *ctxs, int n, int32_t generations, int 
         }
         if (e == cudaSuccess && cur == 1)
             e = cudaMemcpyAsync(c->fit, c->ffit, (size_t)c->P * 4u, cudaMemcpyDeviceToDevice, c0->stream);
+        if (e == cudaSuccess && cur == 1 && c->incremental)
+            e = cudaMemcpyAsync(c->gidx[0], c->gidx[1], (size_t)c->P * 4u, cudaMemcpyDeviceToDevice, c0->stream);
         if (e != cudaSuccess)
             return cuda_check(c0, e, "copy-back of the final population");
     }
@@ -670,6 +699,17 @@ ga_status ga_step_multi_graph(ga_ctx *const *ctxs, int32_t n, int32_t generation
     ga_ctx *c0 = ctxs[0];
     const int32_t reps = generations / chunk, rem = generations % chunk;
     if (reps > 0) {
+        // stale incremental Gram storage is rebuilt outside the captured chunk
+        for (int32_t i = 0; i < n; ++i) {
+            ga_ctx *c = ctxs[i];
+            if (c->incremental && !c->gram_valid) {
+                cudaError_t e = launch_gram_store((const uint32_t *)c->pop, c->m, c->P, c->gram, c->dpad, c->gidx[0],
+                                                  c0->stream);
+                if (e != cudaSuccess)
+                    return set_error(nullptr, GA_ECUDA, "Gram store: %s", cudaGetErrorString(e));
+                c->gram_valid = 1;
+            }
+        }
         // device generation counters take over from here
         for (int32_t i = 0; i < n; ++i) {
             cudaError_t e = launch_set_u32(ctxs[i]->fmisc + 2, ctxs[i]->gen, c0->stream);
@@ -710,6 +750,110 @@ ga_status ga_step_multi_graph(ga_ctx *const *ctxs, int32_t n, int32_t generation
     }
     if (rem > 0)
         return ga_step_multi(ctxs, n, rem);
+    return GA_OK;
+}
+
+ga_status ga_set_incremental(ga_ctx *ctx, int32_t enable)
+{
+    ga_status st = begin(ctx);
+    if (st != GA_OK)
+        return st;
+    if (!enable) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->gram_mem);
+        ctx->gram_mem = nullptr;
+        ctx->gram = nullptr;
+        ctx->gidx[0] = ctx->gidx[1] = nullptr;
+        ctx->gcounts = nullptr;
+        ctx->incremental = 0;
+        ctx->gram_valid = 0;
+        return GA_OK;
+    }
+    if (ctx->cfg.storage != GA_STORE_BITS || ctx->m <= 32 || ctx->m > 128 || !ctx->fused_ok)
+        return set_error(ctx, GA_EUNSUPPORTED,
+                         "incremental Gram mode needs BITS storage, 32 < m <= 128 and a fused-capable context");
+    if (!ctx->gram_mem) {
+        const int D = ctx->m * (ctx->m - 1) / 2;
+        const int dpad = (D + 15) / 16 * 16;
+        const size_t gbytes = align_up((size_t)ctx->P * dpad, 256), ibytes = align_up((size_t)ctx->P * 4u, 256);
+        void *mem = nullptr;
+        cudaError_t e = cudaMalloc(&mem, gbytes + 2 * ibytes + 256);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(ctx, e == cudaErrorMemoryAllocation ? GA_ENOMEM : GA_ECUDA,
+                             "Gram storage of %zu bytes: %s", gbytes + 2 * ibytes + 256, cudaGetErrorString(e));
+        }
+        ctx->gram_mem = mem;
+        ctx->dpad = dpad;
+        ctx->gram = (int8_t *)mem;
+        ctx->gidx[0] = (uint32_t *)((char *)mem + gbytes);
+        ctx->gidx[1] = (uint32_t *)((char *)mem + gbytes + ibytes);
+        ctx->gcounts = (unsigned long long *)((char *)mem + gbytes + 2 * ibytes);
+    }
+    ctx->incremental = 1;
+    st = cuda_check(ctx,
+                    launch_gram_store((const uint32_t *)ctx->pop, ctx->m, ctx->P, ctx->gram, ctx->dpad, ctx->gidx[0],
+                                      ctx->stream),
+                    "Gram store");
+    ctx->gram_valid = st == GA_OK;
+    return st;
+}
+
+ga_status ga_check_incremental(ga_ctx *ctx, uint64_t *entry_mismatch, uint64_t *fit_mismatch)
+{
+    ga_status st = begin(ctx);
+    if (st != GA_OK)
+        return st;
+    if (!entry_mismatch || !fit_mismatch)
+        return set_error(ctx, GA_EINVAL, "NULL output");
+    if (!ctx->incremental)
+        return set_error(ctx, GA_EINVAL, "incremental mode is off");
+    if (!ctx->gram_valid)
+        return set_error(ctx, GA_EINVAL, "the Gram storage is stale (population changed outside ga_step)");
+    cudaError_t e = cudaMemsetAsync(ctx->gcounts, 0, 16, ctx->stream);
+    if (e == cudaSuccess)
+        e = launch_gram_check((const uint32_t *)ctx->pop, ctx->m, ctx->P, ctx->cfg.fitness, ctx->gram, ctx->dpad,
+                              ctx->gidx[0], ctx->fit, ctx->gcounts, ctx->stream);
+    unsigned long long h[2] = {0, 0};
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h, ctx->gcounts, 16, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess)
+        return cuda_check(ctx, e, "incremental check");
+    *entry_mismatch = h[0];
+    *fit_mismatch = h[1];
+    return GA_OK;
+}
+
+ga_status ga_get_gram(ga_ctx *ctx, int64_t slot, int32_t *host_G)
+{
+    ga_status st = begin(ctx);
+    if (st != GA_OK)
+        return st;
+    if (!host_G || slot < 0 || slot >= ctx->P)
+        return set_error(ctx, GA_EINVAL, "bad slot %lld or NULL output", (long long)slot);
+    if (!ctx->incremental || !ctx->gram_valid)
+        return set_error(ctx, GA_EINVAL, "no current incremental Gram storage");
+    uint32_t g = 0;
+    cudaError_t e = cudaMemcpyAsync(&g, ctx->gidx[0] + slot, 4, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess)
+        return cuda_check(ctx, e, "Gram index read");
+    if ((int64_t)g >= ctx->P)
+        return set_error(ctx, GA_ECUDA, "Gram index %u of slot %lld out of range", g, (long long)slot);
+    const int m = ctx->m, D = m * (m - 1) / 2;
+    std::vector<int8_t> h(D);
+    e = cudaMemcpy(h.data(), ctx->gram + (size_t)g * ctx->dpad, (size_t)D, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess)
+        return cuda_check(ctx, e, "Gram read");
+    int idx = 0;
+    for (int i = 0; i < m; ++i) {
+        host_G[i * m + i] = m;
+        for (int j = i + 1; j < m; ++j, ++idx)
+            host_G[i * m + j] = host_G[j * m + i] = 2 * (int32_t)h[idx];
+    }
     return GA_OK;
 }
 
@@ -813,6 +957,7 @@ ga_status ga_set_slot(ga_ctx *ctx, int64_t slot, const int8_t *host_matrix)
     if (!host_matrix || slot < 0 || slot >= ctx->P)
         return set_error(ctx, GA_EINVAL, "bad slot %lld or NULL matrix", (long long)slot);
     const int m = ctx->m;
+    ctx->gram_valid = 0;
     for (int i = 0; i < m * m; ++i)
         if (host_matrix[i] != 1 && host_matrix[i] != -1)
             return set_error(ctx, GA_EINVAL, "entry %d of the matrix is %d, not +1 or -1", i, host_matrix[i]);

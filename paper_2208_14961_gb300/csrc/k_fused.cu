@@ -198,6 +198,35 @@ __device__ __forceinline__ uint32_t survivor_of(uint32_t d, const FusedPop &p, c
     return slot < P ? slot : P - 1;
 }
 
+// Slot of non-survivor number o (in slot order): tiles hold 32t slots before
+// tile t, of which surv_before(t) survive.
+__device__ __forceinline__ uint32_t nonsurvivor_of(uint32_t o, const FusedPop &p, const PopSel &S, const Surv &sv,
+                                                   uint32_t *err)
+{
+    const uint32_t tb = p.tile_base;
+    uint32_t lo = 0, hi = p.ntiles - 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (32u * mid - surv_before(sv, tb + mid, S) <= o)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const unsigned long long m64 = sv.tm[tb + lo];
+    const uint32_t eqb = min((uint32_t)sv.ex[tb + lo] - S.eb, S.take);
+    const uint32_t surv = (uint32_t)m64 | lowest_set_bits((uint32_t)(m64 >> 32), (int)(S.take - eqb));
+    const uint32_t P = (uint32_t)(4 * p.N);
+    const uint32_t tail = P - 32u * lo;
+    const uint32_t valid = tail >= 32u ? 0xFFFFFFFFu : ((1u << tail) - 1u);
+    const uint32_t mask = valid & ~surv;
+    const uint32_t r = o - (32u * lo - surv_before(sv, tb + lo, S));
+    if (r >= (uint32_t)__popc(mask)) {
+        atomicOr(err, ERR_INTERNAL);
+        return P - 1;
+    }
+    return 32u * lo + (uint32_t)nth_set_bit(mask, (int)r);
+}
+
 // Draws of one build item that do not depend on the selection: survivor
 // number d, cut point c and (for NC = NR = 1) the mutated column and rows.
 struct Pre {
@@ -352,6 +381,97 @@ __device__ __forceinline__ void pair_thread(const FusedPop &p, const PopSel &S, 
 }
 
 // ---------------------------------------------------------------------------
+// a7 -- incremental fitness of one offspring (warp-wide; not in the paper,
+// which recomputes G: derived from the fitness of Sec. 3.2 under the
+// operators of Sec. 3.4 and 3.5).  Its Gram / 2, h,
+// is assembled in its own buffer from the parents' buffers: entries with
+// j < c from the parent giving the first c columns (gt), entries with i >= c
+// from the other (gbm), the c(m - c) cross entries recomputed from the column
+// bits (ct: first-part columns, cb: second-part columns).  Then the mutation
+// runs flip by flip: a successful flip of rows r1, r2 in column cc changes
+// only row/column cc of G (by -2s(Q[r1][j] - Q[r2][j]), s = Q[r1][cc]), so
+// those m - 1 entries and the fitness are updated and the two bits flipped
+// in the offspring's columns `bo` (which hold the crossover result on entry).
+// The fitness is the sum of the per-entry terms, kept up to date on the way.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int tri_index(int i, int j, int m) { return i * (m - 1) - (i * (i - 1)) / 2 + (j - i - 1); }
+
+__device__ __forceinline__ uint32_t mutation_word(const FusedPop &p, uint32_t gen, uint32_t o, int w)
+{
+    return word_of(philox_block(p.seed, p.pop_id, OP_MUTATE, gen, o, 0u, (uint32_t)(w >> 2)), w & 3);
+}
+
+template <int W, int KIND>
+__device__ uint32_t offspring_incremental(const FusedPop &p, uint32_t *bo, const uint32_t *ct, const uint32_t *cb,
+                                          int c, uint32_t gt, uint32_t gbm, uint32_t go, uint32_t gen, uint32_t o,
+                                          int lane)
+{
+    const int m = p.m, half_m = m >> 1;
+    const int8_t *Gt = p.gram + (size_t)gt * p.dpad;
+    const int8_t *Gb = p.gram + (size_t)gbm * p.dpad;
+    int8_t *Go = p.gram + (size_t)go * p.dpad;
+    uint32_t acc = 0;
+    int base = 0;
+    for (int i = 0; i < m - 1; ++i) {
+        const int L = m - 1 - i;
+        for (int jj = lane; jj < L; jj += 32) {
+            const int j = i + 1 + jj;
+            int h;
+            if (j < c) {
+                h = (int)__ldcg(reinterpret_cast<const signed char *>(Gt + base + jj));
+            } else if (i >= c) {
+                h = (int)__ldcg(reinterpret_cast<const signed char *>(Gb + base + jj));
+            } else {
+                int d = 0;
+#pragma unroll
+                for (int w = 0; w < W; ++w)
+                    d += __popc(ct[i * W + w] ^ cb[j * W + w]);
+                h = half_m - d;
+            }
+            __stcg(reinterpret_cast<signed char *>(Go) + base + jj, (signed char)h);
+            acc += fit_term<KIND>(2 * h);
+        }
+        base += L;
+    }
+    __syncwarp();
+    // mutation, flip by flip; draw word w of offspring o (NC columns, then NR
+    // first rows, then NR second rows) is word w mod 4 of block w / 4
+    const int NC = p.NC, NR = p.NR;
+    for (int jc = 0; jc < NC; ++jc) {
+        const int cc = (int)uniform_int(mutation_word(p, gen, o, jc), 1u, (uint32_t)(m - 1));
+        uint32_t *col = bo + cc * W;
+        for (int ir = 0; ir < NR; ++ir) {
+            const int ra = (int)uniform_int(mutation_word(p, gen, o, NC + ir), 0u, (uint32_t)(m - 1));
+            const int rb = (int)uniform_int(mutation_word(p, gen, o, NC + NR + ir), 0u, (uint32_t)(m - 1));
+            const int ba = (int)((col[ra >> 5] >> (ra & 31)) & 1u), bb = (int)((col[rb >> 5] >> (rb & 31)) & 1u);
+            if (ba == bb)
+                continue;  // equal entries: no flip (the same on every lane)
+            const int s = ba ? -1 : 1;  // Q[r1][cc] before the flip
+            for (int j = lane; j < m; j += 32) {
+                if (j == cc)
+                    continue;
+                const int qa = ((bo[j * W + (ra >> 5)] >> (ra & 31)) & 1u) ? -1 : 1;
+                const int qb = ((bo[j * W + (rb >> 5)] >> (rb & 31)) & 1u) ? -1 : 1;
+                if (qa == qb)
+                    continue;
+                signed char *e = reinterpret_cast<signed char *>(Go) + (cc < j ? tri_index(cc, j, m) : tri_index(j, cc, m));
+                const int h0 = (int)__ldcg(e);
+                const int h1 = h0 - s * (qa - qb);  // G moves by -2s(qa - qb)
+                __stcg(e, (signed char)h1);
+                acc += fit_term<KIND>(2 * h1) - fit_term<KIND>(2 * h0);
+            }
+            __syncwarp();
+            if (lane == 0) {
+                col[ra >> 5] ^= 1u << (ra & 31);
+                col[rb >> 5] ^= 1u << (rb & 31);
+            }
+            __syncwarp();
+        }
+    }
+    return fit_finish<KIND>(warp_sum(acc));
+}
+
+// ---------------------------------------------------------------------------
 // 32 < m <= 128: a warp per pair, matrices staged in shared memory.
 // ---------------------------------------------------------------------------
 template <int W>
@@ -374,6 +494,34 @@ __device__ void pair_warp(const FusedPop &p, PopSel &S, int src, uint32_t gen, u
     s1 = __shfl_sync(FULL, s1, 0);
     s2 = __shfl_sync(FULL, s2, 0);
     c = __shfl_sync(FULL, c, 0);
+    // incremental mode: parents keep their Gram buffers, offspring take the
+    // buffers of the non-survivors k and k + N (in slot order)
+    const bool inc = p.gram != nullptr;
+    uint32_t gb1 = 0, gb2 = 0, go0 = 0, go1 = 0;
+    if (inc && lane == 0) {
+        gb1 = ldcg32(p.gidx[src] + s1);
+        gb2 = ldcg32(p.gidx[src] + s2);
+        go0 = ldcg32(p.gidx[src] + nonsurvivor_of(k, p, S, sv, err));
+        go1 = ldcg32(p.gidx[src] + nonsurvivor_of(k + N, p, S, sv, err));
+        const uint32_t P = (uint32_t)(4 * p.N);
+        if ((gb1 | gb2 | go0 | go1) >= P && (gb1 >= P || gb2 >= P || go0 >= P || go1 >= P)) {
+            atomicOr(err, ERR_INTERNAL);  // never expected: indices stay a permutation of [0, P)
+            gb1 = gb1 < P ? gb1 : 0u;
+            gb2 = gb2 < P ? gb2 : 0u;
+            go0 = go0 < P ? go0 : 0u;
+            go1 = go1 < P ? go1 : 0u;
+        }
+        p.gidx[src ^ 1][k] = gb1;
+        p.gidx[src ^ 1][k + N] = gb2;
+        p.gidx[src ^ 1][2u * N + k] = go0;
+        p.gidx[src ^ 1][3u * N + k] = go1;
+    }
+    if (inc) {
+        gb1 = __shfl_sync(FULL, gb1, 0);
+        gb2 = __shfl_sync(FULL, gb2, 0);
+        go0 = __shfl_sync(FULL, go0, 0);
+        go1 = __shfl_sync(FULL, go1, 0);
+    }
     uint32_t *b1 = buf, *b2 = buf + words, *bo = buf + 2 * words;
     const uint32_t *sp = p.pop[src];
     uint32_t *dp = p.pop[src ^ 1];
@@ -394,6 +542,21 @@ __device__ void pair_warp(const FusedPop &p, PopSel &S, int src, uint32_t gen, u
         for (uint32_t e = lane; e < words; e += 32)
             bo[e] = (((int)(e / W) < c) != (half != 0)) ? b1[e] : b2[e];
         __syncwarp();
+        if (inc) {
+            uint32_t f;
+            switch (p.kind) {
+            case FIT_SQ: f = offspring_incremental<W, FIT_SQ>(p, bo, half ? b2 : b1, half ? b1 : b2, c, half ? gb2 : gb1, half ? gb1 : gb2, half ? go1 : go0, gen, k + (half ? N : 0u), lane); break;
+            case FIT_ABS: f = offspring_incremental<W, FIT_ABS>(p, bo, half ? b2 : b1, half ? b1 : b2, c, half ? gb2 : gb1, half ? gb1 : gb2, half ? go1 : go0, gen, k + (half ? N : 0u), lane); break;
+            default: f = offspring_incremental<W, FIT_NNZ>(p, bo, half ? b2 : b1, half ? b1 : b2, c, half ? gb2 : gb1, half ? gb1 : gb2, half ? go1 : go0, gen, k + (half ? N : 0u), lane); break;
+            }
+            const uint32_t slot = 2u * N + k + (half ? N : 0u);
+            for (uint32_t e = lane; e < words; e += 32)
+                dp[(size_t)slot * words + e] = bo[e];
+            if (lane == 0)
+                p.fit[src ^ 1][slot] = f;
+            fc[half] = f;
+            continue;
+        }
         if (lane == 0) {
             Draws dr(p.seed, p.pop_id, gen, k + (half ? N : 0u));
             uint8_t cols[64], r1[64], r2[64];

@@ -271,4 +271,133 @@ cudaError_t launch_convert(const void *src, int src_storage, void *dst, int dst_
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Gram store of the incremental mode: one warp per matrix, row i of the upper
+// triangle by the lanes, entry = (m - 2 popc(b_i ^ b_j)) / 2.
+// ---------------------------------------------------------------------------
+template <int W>
+__global__ void __launch_bounds__(256) k_gram_store(const uint32_t *__restrict__ pop, int m, int64_t P, int8_t *gram,
+                                                    int dpad, uint32_t *gidx)
+{
+    extern __shared__ uint32_t s_c[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint32_t *cols = s_c + (size_t)wib * m * W;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t q = gw; q < P; q += nw) {
+        for (int e = lane; e < m * W; e += 32)
+            cols[e] = pop[(size_t)q * m * W + e];
+        __syncwarp();
+        int8_t *G = gram + (size_t)q * dpad;
+        int base = 0;
+        for (int i = 0; i < m - 1; ++i) {
+            const int L = m - 1 - i;
+            for (int jj = lane; jj < L; jj += 32) {
+                const int j = i + 1 + jj;
+                int d = 0;
+#pragma unroll
+                for (int w = 0; w < W; ++w)
+                    d += __popc(cols[i * W + w] ^ cols[j * W + w]);
+                G[base + jj] = (int8_t)(m / 2 - d);
+            }
+            base += L;
+        }
+        if (lane == 0)
+            gidx[q] = (uint32_t)q;
+        __syncwarp();
+    }
+}
+
+cudaError_t launch_gram_store(const uint32_t *pop, int m, int64_t P, int8_t *gram, int dpad, uint32_t *gidx,
+                              cudaStream_t s)
+{
+    const int W = words_per_col(m);
+    const int wpb = 8;
+    const size_t smem = (size_t)wpb * m * W * 4;
+    int64_t grid = (P + wpb - 1) / wpb;
+    if (grid > 4096)
+        grid = 4096;
+    switch (W) {
+    case 1: k_gram_store<1><<<(unsigned)grid, wpb * 32, smem, s>>>(pop, m, P, gram, dpad, gidx); break;
+    case 2: k_gram_store<2><<<(unsigned)grid, wpb * 32, smem, s>>>(pop, m, P, gram, dpad, gidx); break;
+    case 3: k_gram_store<3><<<(unsigned)grid, wpb * 32, smem, s>>>(pop, m, P, gram, dpad, gidx); break;
+    case 4: k_gram_store<4><<<(unsigned)grid, wpb * 32, smem, s>>>(pop, m, P, gram, dpad, gidx); break;
+    default: return cudaErrorInvalidValue;
+    }
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+template <int W>
+__global__ void __launch_bounds__(256) k_gram_check(const uint32_t *__restrict__ pop, int m, int64_t P, int kind,
+                                                    const int8_t *__restrict__ gram, int dpad,
+                                                    const uint32_t *__restrict__ gidx, const uint32_t *__restrict__ fit,
+                                                    unsigned long long *counts)
+{
+    extern __shared__ uint32_t s_c[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint32_t *cols = s_c + (size_t)wib * m * W;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long bad_e = 0, bad_f = 0;
+    for (int64_t q = gw; q < P; q += nw) {
+        for (int e = lane; e < m * W; e += 32)
+            cols[e] = pop[(size_t)q * m * W + e];
+        __syncwarp();
+        const uint32_t gq = gidx[q];
+        const bool in_range = (int64_t)gq < P;
+        const int8_t *G = gram + (size_t)(in_range ? gq : 0u) * dpad;
+        uint32_t acc = 0;
+        int base = 0;
+        for (int i = 0; i < m - 1; ++i) {
+            const int L = m - 1 - i;
+            for (int jj = lane; jj < L; jj += 32) {
+                const int j = i + 1 + jj;
+                int d = 0;
+#pragma unroll
+                for (int w = 0; w < W; ++w)
+                    d += __popc(cols[i * W + w] ^ cols[j * W + w]);
+                const int g = m - 2 * d;
+                acc += kind == FIT_SQ ? fit_term<FIT_SQ>(g) : kind == FIT_ABS ? fit_term<FIT_ABS>(g) : fit_term<FIT_NNZ>(g);
+                if (!in_range || (int)G[base + jj] != g / 2)
+                    ++bad_e;
+            }
+            base += L;
+        }
+        acc = warp_sum(acc);
+        const uint32_t f = kind == FIT_SQ ? acc : 2u * acc;
+        if (lane == 0 && f != fit[q])
+            ++bad_f;
+        __syncwarp();
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        bad_e += __shfl_xor_sync(0xFFFFFFFFu, bad_e, o);
+        bad_f += __shfl_xor_sync(0xFFFFFFFFu, bad_f, o);
+    }
+    if (lane == 0 && (bad_e | bad_f)) {
+        atomicAdd(counts, bad_e);
+        atomicAdd(counts + 1, bad_f);
+    }
+}
+
+cudaError_t launch_gram_check(const uint32_t *pop, int m, int64_t P, int kind, const int8_t *gram, int dpad,
+                              const uint32_t *gidx, const uint32_t *fit, unsigned long long *counts, cudaStream_t s)
+{
+    const int W = words_per_col(m);
+    const int wpb = 8;
+    const size_t smem = (size_t)wpb * m * W * 4;
+    int64_t grid = (P + wpb - 1) / wpb;
+    if (grid > 4096)
+        grid = 4096;
+    switch (W) {
+    case 1: k_gram_check<1><<<(unsigned)grid, wpb * 32, smem, s>>>(pop, m, P, kind, gram, dpad, gidx, fit, counts); break;
+    case 2: k_gram_check<2><<<(unsigned)grid, wpb * 32, smem, s>>>(pop, m, P, kind, gram, dpad, gidx, fit, counts); break;
+    case 3: k_gram_check<3><<<(unsigned)grid, wpb * 32, smem, s>>>(pop, m, P, kind, gram, dpad, gidx, fit, counts); break;
+    case 4: k_gram_check<4><<<(unsigned)grid, wpb * 32, smem, s>>>(pop, m, P, kind, gram, dpad, gidx, fit, counts); break;
+    default: return cudaErrorInvalidValue;
+    }
+    note_launches(1);
+    return cudaGetLastError();
+}
+
 } // namespace hadga

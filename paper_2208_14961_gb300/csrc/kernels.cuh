@@ -62,6 +62,15 @@ cudaError_t launch_mutate(void *pop, int storage, int m, int64_t N, int NC, int 
 cudaError_t launch_best(const uint32_t *fit, int64_t P, unsigned long long *out, cudaStream_t s);
 cudaError_t launch_convert(const void *src, int src_storage, void *dst, int dst_storage, int m, int64_t P,
                            cudaStream_t s);
+// Upper-triangle Gram / 2 (int8, entry (i, j), i < j, at i(m-1) - i(i-1)/2 + j-i-1)
+// of P bit-storage matrices into gram[q * dpad]; gidx[q] = q.
+cudaError_t launch_gram_store(const uint32_t *pop, int m, int64_t P, int8_t *gram, int dpad, uint32_t *gidx,
+                              cudaStream_t s);
+// Recomputes the Gram / 2 and fitness of P bit-storage matrices and counts,
+// into counts[0] / counts[1], stored entries gram[gidx[q]] and fitness words
+// fit[q] that differ.
+cudaError_t launch_gram_check(const uint32_t *pop, int m, int64_t P, int kind, const int8_t *gram, int dpad,
+                              const uint32_t *gidx, const uint32_t *fit, unsigned long long *counts, cudaStream_t s);
 
 // ---- selection (k_select.cu) -------------------------------------------------
 struct SelWork {
@@ -111,6 +120,9 @@ struct FusedPop {
     const uint32_t *perm;      // [ngen][2N] survivor orders of the chunk
     unsigned long long *traj;  // [traj_cap] best keys (F << 32 | slot)
     uint32_t *gen_dev;         // generation counter: read at start, advanced at exit
+    int8_t *gram;              // incremental mode: [P][dpad] upper-triangle Gram / 2, or null
+    uint32_t *gidx[2];         // incremental mode: slot -> Gram buffer, ping-pong with pop
+    int32_t dpad;              // bytes per Gram buffer (m(m-1)/2 rounded up to 16)
     int32_t m, W, NC, NR, kind, traj_cap;
     int64_t N;
     uint32_t seed, pop_id;

@@ -66,6 +66,9 @@ SIGNATURES = {
     "ga_step_is_fused": (_i32, [_vp]),
     "ga_step_multi_graph": (_i32, [ctypes.POINTER(_vp), _i32, _i32, _i32]),
     "ga_set_fused_grid": (_i32, [_vp, _i32]),
+    "ga_set_incremental": (_i32, [_vp, _i32]),
+    "ga_check_incremental": (_i32, [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
+    "ga_get_gram": (_i32, [_vp, _i64, _vp]),
     "ga_best": (_i32, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_u32)]),
     "ga_trajectory": (_i32, [_vp, _vp, _vp, _i32, ctypes.POINTER(_i32)]),
     "ga_generation": (_i32, [_vp, ctypes.POINTER(_u32)]),
@@ -200,6 +203,7 @@ class Population:
                             ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(ctx)))
         self.ctx = ctx
         self.traj_cap = traj_cap
+        self.incremental = False
 
     def close(self):
         if getattr(self, "ctx", None):
@@ -252,6 +256,24 @@ class Population:
         a, b, n = ctypes.c_float(), ctypes.c_float(), ctypes.c_int32()
         self._chk(load().ga_profile_read(self.ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)))
         return float(a.value), float(b.value), int(n.value)
+
+    def set_incremental(self, enable: bool):
+        """a7: keep each individual's Gram and update it by deltas in ga_step."""
+        self._chk(load().ga_set_incremental(self.ctx, int(enable)))
+        self.incremental = bool(enable)
+
+    def check_incremental(self):
+        """Full recomputation check: (mismatched Gram entries, mismatched fitness words)."""
+        e, f = ctypes.c_uint64(), ctypes.c_uint64()
+        self._chk(load().ga_check_incremental(self.ctx, ctypes.byref(e), ctypes.byref(f)))
+        return int(e.value), int(f.value)
+
+    def gram(self, slot: int):
+        """Stored Gram G (m x m int32) of one slot in incremental mode."""
+        import numpy as np
+        g = np.zeros((self.m, self.m), dtype=np.int32)
+        self._chk(load().ga_get_gram(self.ctx, slot, g.ctypes.data_as(ctypes.c_void_p)))
+        return g
 
     def best(self):
         s, f = ctypes.c_int64(), ctypes.c_uint32()
@@ -307,6 +329,8 @@ class Population:
         else:
             ga_convert(t, STORE_INT8, self.pop, self.storage, self.m, self.P, self.stream)
         torch.cuda.synchronize()
+        if self.incremental:
+            self.set_incremental(True)  # rebuild the Gram storage of the new population
 
     def fitness_host(self):
         import numpy as np
