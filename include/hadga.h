@@ -188,12 +188,12 @@ ga_status ga_step_multi_graph(ga_ctx *const *ctxs, int32_t n, int32_t generation
  * Sec. 3.5): a pair flip in column c changes only row and column c of G, by
  * -2s(Q[r1][j] - Q[r2][j]) with s = Q[r1][c]; a column exchange at cut c
  * keeps the blocks of G inside each parent's part.
- * When enabled, the context keeps every individual's Gram (upper triangle
- * of G / 2 as int8, m(m-1)/2 bytes rounded up to 16, in a separate device
- * allocation of P times that) and the fused kernel builds each offspring's
- * Gram from its parents' (only the c(m - c) cross entries recomputed) and
- * applies each flip as an O(m) update of row/column c, with the fitness
- * updated by the same deltas.  Results stay bit-identical to the full
+ * When enabled, the context keeps every individual's Gram (G / 2 as int8
+ * in 8 x 8 tiles of the upper triangle: 64 * t bytes, t = n(n+1)/2 tiles,
+ * n = ceil(m/8), in a separate device allocation of P times that) and the
+ * fused kernel builds each offspring's Gram from its parents' tiles: only
+ * the c(m - c) cross entries, the entries of tiles cut by c and the row and
+ * column of each flipped column (O(m) entries per flip) are recomputed.  Results stay bit-identical to the full
  * recomputation.  Needs BITS storage and 32 < m <= 128 on a fused-capable
  * context (GA_EUNSUPPORTED otherwise).  Enabling (re)builds the Gram of the
  * current population; ga_init_population, ga_set_slot and the one-kernel-
@@ -203,8 +203,8 @@ ga_status ga_step_multi_graph(ga_ctx *const *ctxs, int32_t n, int32_t generation
 ga_status ga_set_incremental(ga_ctx *ctx, int32_t enable);
 
 /* Full recomputation check of the incremental state: recomputes every
- * slot's Gram entries and fitness from the population and counts the
- * stored Gram entries (*entry_mismatch) and fitness words (*fit_mismatch)
+ * slot's Gram and fitness from the population and counts the stored
+ * 4-entry Gram words (*entry_mismatch) and fitness words (*fit_mismatch)
  * that differ.  Synchronises.  GA_EINVAL unless incremental mode is on. */
 ga_status ga_check_incremental(ga_ctx *ctx, uint64_t *entry_mismatch, uint64_t *fit_mismatch);
 

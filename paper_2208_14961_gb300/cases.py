@@ -5,6 +5,9 @@
 fused_m20   m=20, P=40,000, bit storage: init, fitness, then `generations`
             (default 8) generations in one persistent launch
 plain_m20   the same with the one-kernel-per-operator path
+inc_m100    m=100, P=20,000, bit storage, incremental Gram-delta fitness:
+            init, fitness, Gram store, then `generations` generations
+full_m100   the same workload with full fitness recomputation
 gram_m<M>_<path>  Gram + fitness of a population of ~1 GiB (int8 size) at
             order M with path int32 | imma | popc8 | popc | fp8 | bf16
 """
@@ -28,6 +31,16 @@ def main(argv):
             p.step(gens)
         else:
             p.step_plain(gens)
+        p.sync()
+        print(case, "best", p.best())
+        return
+    if case in ("inc_m100", "full_m100"):
+        p = h.Population(100, 5000, seed=4, storage=h.STORE_BITS, traj_cap=64)
+        p.init_population()
+        p.fitness()
+        if case == "inc_m100":
+            p.set_incremental(True)
+        p.step(gens)
         p.sync()
         print(case, "best", p.best())
         return

@@ -438,10 +438,10 @@ static ga_status fused_run(ga_ctx *const *ctxs, int n, int32_t generations, int 
         tiles += p.ntiles;
         if (c->m <= 32) {
             p.work_base = tslots;
-            tslots += (uint32_t)((2 * c->N + 31) / 32 * 32);
+            tslots += (uint32_t)((4 * c->N + 31) / 32 * 32);
         } else {
             p.work_base = wpairs;
-            wpairs += (uint32_t)c->N;
+            wpairs += (uint32_t)(2 * c->N);  // one warp item per offspring
             max_words = std::max(max_words, 3 * c->m * c->W);
         }
         if (int8) {
@@ -473,7 +473,7 @@ static ga_status fused_run(ga_ctx *const *ctxs, int n, int32_t generations, int 
         return set_error(c0, GA_EUNSUPPORTED, "populations too large for one persistent launch");
     prm.total_tiles = tiles;
     prm.thread_slots = tslots;
-    prm.warp_pairs = wpairs;
+    prm.warp_items = wpairs;
     prm.warp_buf_words = max_words;
     prm.stop_at_zero = stop_at_zero;
     prm.bar = c0->fmisc;
@@ -773,8 +773,7 @@ ga_status ga_set_incremental(ga_ctx *ctx, int32_t enable)
         return set_error(ctx, GA_EUNSUPPORTED,
                          "incremental Gram mode needs BITS storage, 32 < m <= 128 and a fused-capable context");
     if (!ctx->gram_mem) {
-        const int D = ctx->m * (ctx->m - 1) / 2;
-        const int dpad = (D + 15) / 16 * 16;
+        const int dpad = gram_tiles(ctx->m) * 64;  // 8 x 8 int8 tiles of the upper triangle
         const size_t gbytes = align_up((size_t)ctx->P * dpad, 256), ibytes = align_up((size_t)ctx->P * 4u, 256);
         void *mem = nullptr;
         cudaError_t e = cudaMalloc(&mem, gbytes + 2 * ibytes + 256);
@@ -843,16 +842,17 @@ ga_status ga_get_gram(ga_ctx *ctx, int64_t slot, int32_t *host_G)
         return cuda_check(ctx, e, "Gram index read");
     if ((int64_t)g >= ctx->P)
         return set_error(ctx, GA_ECUDA, "Gram index %u of slot %lld out of range", g, (long long)slot);
-    const int m = ctx->m, D = m * (m - 1) / 2;
-    std::vector<int8_t> h(D);
-    e = cudaMemcpy(h.data(), ctx->gram + (size_t)g * ctx->dpad, (size_t)D, cudaMemcpyDeviceToHost);
+    const int m = ctx->m, nb = gram_tiles_nb(m);
+    std::vector<int8_t> h((size_t)ctx->dpad);
+    e = cudaMemcpy(h.data(), ctx->gram + (size_t)g * ctx->dpad, (size_t)ctx->dpad, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess)
         return cuda_check(ctx, e, "Gram read");
-    int idx = 0;
     for (int i = 0; i < m; ++i) {
         host_G[i * m + i] = m;
-        for (int j = i + 1; j < m; ++j, ++idx)
-            host_G[i * m + j] = host_G[j * m + i] = 2 * (int32_t)h[idx];
+        for (int j = i + 1; j < m; ++j) {
+            const int I = i >> 3, J = j >> 3, t = I * nb - I * (I - 1) / 2 + (J - I);
+            host_G[i * m + j] = host_G[j * m + i] = 2 * (int32_t)h[(size_t)t * 64 + (i & 7) * 8 + (j & 7)];
+        }
     }
     return GA_OK;
 }

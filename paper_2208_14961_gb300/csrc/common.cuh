@@ -236,6 +236,47 @@ __device__ __forceinline__ uint32_t warp_fitness_cols(const uint32_t *cols, int 
 }
 
 // ---------------------------------------------------------------------------
+// Tiled half-Gram storage of the incremental fitness mode: H = G / 2 as int8
+// in 8 x 8 tiles (I <= J) of the upper triangle, tile t = I nb - I(I-1)/2 +
+// (J - I), nb = ceil(m / 8); entry (i, j) at byte 64 t + 8 (i mod 8) +
+// (j mod 8); entries with i >= j or outside m are 0.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ int gram_tiles_nb(int m) { return (m + 7) >> 3; }
+__host__ __device__ __forceinline__ int gram_tiles(int m) { return gram_tiles_nb(m) * (gram_tiles_nb(m) + 1) / 2; }
+
+// Tile-row I and tile-column J of tile t (tile-row I holds nb - I tiles).
+__device__ __forceinline__ void tile_coords(int t, int nb, int &I, int &J)
+{
+    const float b = (float)(2 * nb + 1);
+    int i = (int)((b - sqrtf(b * b - 8.0f * (float)t)) * 0.5f);
+    i = max(0, min(i, nb - 1));
+    while (i > 0 && i * nb - (i * (i - 1)) / 2 > t)
+        --i;
+    while (i + 1 < nb && (i + 1) * nb - ((i + 1) * i) / 2 <= t)
+        ++i;
+    I = i;
+    J = i + (t - (i * nb - (i * (i - 1)) / 2));
+}
+
+// Sum over the four int8 entries h of a word of the fitness term of G = 2h,
+// before the final scale (F_sq = 4 sum h^2, F1 = 4 sum |h|, F2 = 2 sum [h != 0]).
+template <int KIND>
+__device__ __forceinline__ int word_terms(uint32_t x)
+{
+    if (KIND == FIT_SQ)
+        return __dp4a((int)x, (int)x, 0);
+    if (KIND == FIT_ABS)
+        return __dp4a((int)__vabsss4(x), 0x01010101, 0);
+    return __dp4a((int)__vsetne4(x, 0u), 0x01010101, 0);
+}
+
+template <int KIND>
+__device__ __forceinline__ uint32_t word_terms_finish(uint32_t sum)
+{
+    return KIND == FIT_NNZ ? 2u * sum : 4u * sum;
+}
+
+// ---------------------------------------------------------------------------
 // Bounded waits
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned long long global_ns()

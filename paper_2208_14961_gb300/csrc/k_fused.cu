@@ -18,9 +18,9 @@
 //           (survivors in slot order), then builds pairs: parents k, k+N are
 //           survivors number pi(k), pi(k+N) of the precomputed survivor order
 //           of generation g; crossover, mutation and fitness of both
-//           offspring run in registers (m <= 32: two threads per pair, one
-//           per offspring) or in shared memory (32 < m <= 128: a warp per
-//           pair); the new population goes to the other ping-pong buffer and
+//           offspring run in registers (m <= 32: four threads per pair,
+//           two per offspring) or in shared memory (32 < m <= 128: a warp
+//           per offspring); the new population goes to the other ping-pong buffer and
 //           the histogram, OR word and best key of generation g + 1 are
 //           accumulated with warp-aggregated atomics.
 // Data written inside the launch is read with ld.global.cg (L2) so no SM
@@ -106,6 +106,62 @@ __device__ void warp_find_bucket(const uint32_t *h, uint32_t nb, uint32_t need, 
     before_out = __shfl_sync(FULL, before, owner);
 }
 
+// Whole warp, histogram h[0, n) in shared memory (n <= 4096): bucket b where
+// the running count first reaches `need` (1 <= need <= total) and the count
+// before it.  Two levels: every lane sums a contiguous chunk (visited in a
+// lane-rotated order to spread the banks), a warp scan finds the chunk, the
+// 32 lanes split that chunk four buckets each and a second scan finds the
+// bucket.  Returns false when no bucket reaches `need`.
+__device__ bool warp_find_crossing_smem(const uint32_t *h, uint32_t n, uint32_t need, uint32_t &b_out,
+                                        uint32_t &before_out)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t per = (((n + 31u) >> 5) + 3u) & ~3u;  // chunk length, a multiple of 4 (<= 128)
+    const uint32_t lo = (uint32_t)lane * per, rot = (uint32_t)lane % per;
+    uint32_t sum = 0;
+    for (uint32_t v = 0; v < per; ++v) {
+        uint32_t e = v + rot;
+        e = e >= per ? e - per : e;
+        if (lo + e < n)
+            sum += h[lo + e];
+    }
+    const uint32_t incl = warp_incl_scan(sum, lane), excl = incl - sum;
+    const uint32_t bal = __ballot_sync(FULL, excl < need && need <= incl);
+    if (bal == 0u)
+        return false;
+    const int owner = __ffs(bal) - 1;
+    const uint32_t olo = (uint32_t)owner * per;
+    const uint32_t base = __shfl_sync(FULL, excl, owner);
+    // second level: lane l takes buckets olo + 4l .. olo + 4l + 3 of the chunk
+    uint32_t c4[4];
+    uint32_t s4 = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t e = olo + 4u * (uint32_t)lane + (uint32_t)k;
+        c4[k] = (4u * (uint32_t)lane + (uint32_t)k < per && e < n) ? h[e] : 0u;
+        s4 += c4[k];
+    }
+    const uint32_t i2 = warp_incl_scan(s4, lane);
+    uint32_t run = base + i2 - s4;
+    int hit = -1;
+    uint32_t before = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (hit < 0 && run + c4[k] >= need) {
+            hit = k;
+            before = run;
+        }
+        run += c4[k];
+    }
+    const uint32_t bal2 = __ballot_sync(FULL, hit >= 0);
+    if (bal2 == 0u)
+        return false;
+    const int o2 = __ffs(bal2) - 1;
+    b_out = olo + 4u * (uint32_t)o2 + (uint32_t)__shfl_sync(FULL, hit, o2);
+    before_out = __shfl_sync(FULL, before, o2);
+    return true;
+}
+
 // Warp-aggregated histogram increment (all lanes call; ok selects the lanes
 // that add one to bucket key).
 __device__ __forceinline__ void warp_hist_add(uint32_t *h, bool ok, uint32_t key)
@@ -133,26 +189,6 @@ __device__ __forceinline__ uint32_t warp_max(uint32_t v)
     return v;
 }
 
-// Exclusive prefix sums over e in [0, n) of cnt(e) into out[e] (shared
-// memory), each thread walking one contiguous chunk: two short sequential
-// passes around a single block-wide scan.  Every thread calls.
-template <class Cnt>
-__device__ __forceinline__ void block_scan_chunks(uint32_t n, Cnt cnt, uint32_t *out, uint32_t *tmp)
-{
-    const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
-    const uint32_t lo = min(n, threadIdx.x * per), hi = min(n, lo + per);
-    uint32_t sum = 0;
-    for (uint32_t e = lo; e < hi; ++e)
-        sum += cnt(e);
-    uint32_t tot;
-    uint32_t ex = block_excl_scan(sum, tmp, &tot);
-    for (uint32_t e = lo; e < hi; ++e) {
-        const uint32_t c = cnt(e);
-        out[e] = ex;
-        ex += c;
-    }
-    __syncthreads();
-}
 
 // Survivor bookkeeping of phase B, per tile t of the joint tile space:
 //   tm[t] = (F < T mask) | (F == T mask) << 32
@@ -266,58 +302,70 @@ struct Draws {
     }
 };
 
+// Half of the upper-triangle terms of a column set, chosen so that the same
+// code on the columns rotated by one (c'[j] = c[(j + 1) mod M]) yields the
+// other half: pairs (a, a + s mod M) with a even, 1 <= s < M/2, plus
+// (a, a + M/2) with a even and a < M/2 (M is a multiple of 4).
 template <int M, int KIND>
-__device__ __forceinline__ uint32_t fitness_regs(const uint32_t (&c)[M])
+__device__ __forceinline__ uint32_t fitness_half_regs(const uint32_t (&c)[M])
 {
     uint32_t acc = 0;
 #pragma unroll
-    for (int i = 0; i < M; ++i) {
+    for (int a = 0; a < M; a += 2) {
 #pragma unroll
-        for (int j = i + 1; j < M; ++j)
-            acc += fit_term<KIND>(M - 2 * __popc(c[i] ^ c[j]));
+        for (int s = 1; s < M / 2; ++s)
+            acc += fit_term<KIND>(M - 2 * __popc(c[a] ^ c[(a + s) % M]));
+        if (a < M / 2)
+            acc += fit_term<KIND>(M - 2 * __popc(c[a] ^ c[a + M / 2]));
     }
-    return fit_finish<KIND>(acc);
+    return acc;
 }
 
 // ---------------------------------------------------------------------------
-// m <= 32: two threads per pair (lane pair 2j, 2j+1), thread `half` builds
-// offspring O_{1 + half}; its parent is P_1 (half 0) or P_2 (half 1).
+// m <= 32: four threads per pair (lanes 4j .. 4j + 3): `half` selects the
+// offspring O_{1 + half} (and the parent P_{1 + half} it carries over), `sub`
+// splits its fitness terms; thread sub = 1 places the parent, sub = 0 the
+// offspring.  Each thread returns the one (fitness, slot) it placed.
 // ---------------------------------------------------------------------------
 template <int M>
 __device__ __forceinline__ void pair_thread(const FusedPop &p, const PopSel &S, int src, uint32_t gen, const Pre &pre,
-                                            uint32_t k, int half, bool valid, const Surv &sv, uint32_t *err,
-                                            uint32_t &f_par, uint32_t &slot_par, uint32_t &f_child,
-                                            uint32_t &slot_child)
+                                            uint32_t k, int half, int sub, bool valid, const Surv &sv, uint32_t *err,
+                                            uint32_t &f_out, uint32_t &slot_out)
 {
     const uint32_t N = (uint32_t)p.N;
     uint32_t s_mine = 0;
     if (valid)
         s_mine = survivor_of(pre.d, p, S, sv, err);
-    const uint32_t s_other = __shfl_xor_sync(FULL, s_mine, 1);
-    if (!valid)
-        return;
-    const uint32_t s1 = half ? s_other : s_mine, s2 = half ? s_mine : s_other;
+    const uint32_t s_other = __shfl_xor_sync(FULL, s_mine, 2);
     const uint32_t *src_pop = p.pop[src];
     uint32_t *dst_pop = p.pop[src ^ 1];
+    const uint32_t s1 = half ? s_other : s_mine, s2 = half ? s_mine : s_other;
     uint32_t p1[M], p2[M];
-    const uint4 *a = reinterpret_cast<const uint4 *>(src_pop + (size_t)s1 * M);
-    const uint4 *b = reinterpret_cast<const uint4 *>(src_pop + (size_t)s2 * M);
+    if (valid) {
+        const uint4 *a = reinterpret_cast<const uint4 *>(src_pop + (size_t)s1 * M);
+        const uint4 *b = reinterpret_cast<const uint4 *>(src_pop + (size_t)s2 * M);
 #pragma unroll
-    for (int v = 0; v < M / 4; ++v) {
-        const uint4 x = __ldcg(a + v), y = __ldcg(b + v);
-        p1[4 * v] = x.x, p1[4 * v + 1] = x.y, p1[4 * v + 2] = x.z, p1[4 * v + 3] = x.w;
-        p2[4 * v] = y.x, p2[4 * v + 1] = y.y, p2[4 * v + 2] = y.z, p2[4 * v + 3] = y.w;
+        for (int v = 0; v < M / 4; ++v) {
+            const uint4 x = __ldcg(a + v), y = __ldcg(b + v);
+            p1[4 * v] = x.x, p1[4 * v + 1] = x.y, p1[4 * v + 2] = x.z, p1[4 * v + 3] = x.w;
+            p2[4 * v] = y.x, p2[4 * v + 1] = y.y, p2[4 * v + 2] = y.z, p2[4 * v + 3] = y.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < M; ++j)
+            p1[j] = p2[j] = 0u;
     }
-    f_par = ldcg32(p.fit[src] + s_mine);
-    slot_par = half ? k + N : k;
-    {
-        uint4 *d = reinterpret_cast<uint4 *>(dst_pop + (size_t)slot_par * M);
+    if (valid && sub) {
+        // the parent this half carries over keeps its slot order k / k + N
+        f_out = ldcg32(p.fit[src] + s_mine);
+        slot_out = half ? k + N : k;
+        uint4 *d = reinterpret_cast<uint4 *>(dst_pop + (size_t)slot_out * M);
 #pragma unroll
         for (int v = 0; v < M / 4; ++v) {
             const uint32_t *q = half ? p2 : p1;
             d[v] = make_uint4(q[4 * v], q[4 * v + 1], q[4 * v + 2], q[4 * v + 3]);
         }
-        p.fit[src ^ 1][slot_par] = f_par;
+        p.fit[src ^ 1][slot_out] = f_out;
     }
     // crossover (Sec. 3.4): O1 = P1[:, :c] | P2[:, c:], O2 = P2[:, :c] | P1[:, c:]
     const int c = (int)pre.c;
@@ -327,7 +375,6 @@ __device__ __forceinline__ void pair_thread(const FusedPop &p, const PopSel &S, 
         o[j] = ((j < c) != (half != 0)) ? p1[j] : p2[j];
     // mutation (Sec. 3.5): columns in order, pairs in order, flip iff different
     {
-        Draws dr(p.seed, p.pop_id, gen, k + (half ? N : 0u));
         const int NC = p.NC, NR = p.NR;
         if (NC == 1 && NR == 1) {
             const uint32_t cc = pre.cc, ra = pre.ra, rb = pre.rb;
@@ -339,6 +386,7 @@ __device__ __forceinline__ void pair_thread(const FusedPop &p, const PopSel &S, 
                 }
             }
         } else {
+            Draws dr(p.seed, p.pop_id, gen, k + (half ? N : 0u));
             uint8_t cols[64], r1[64], r2[64];
             for (int jc = 0; jc < NC; ++jc)
                 cols[jc] = (uint8_t)uniform_int(dr.next(), 1u, (uint32_t)(M - 1));
@@ -363,241 +411,348 @@ __device__ __forceinline__ void pair_thread(const FusedPop &p, const PopSel &S, 
             }
         }
     }
-    uint32_t f;
+    // fitness: this thread's half of the terms (columns rotated by one for sub 1)
+    uint32_t cr[M];
+#pragma unroll
+    for (int j = 0; j < M; ++j)
+        cr[j] = sub ? o[(j + 1) % M] : o[j];
+    uint32_t part;
     switch (p.kind) {
-    case FIT_SQ: f = fitness_regs<M, FIT_SQ>(o); break;
-    case FIT_ABS: f = fitness_regs<M, FIT_ABS>(o); break;
-    default: f = fitness_regs<M, FIT_NNZ>(o); break;
+    case FIT_SQ: part = fitness_half_regs<M, FIT_SQ>(cr); break;
+    case FIT_ABS: part = fitness_half_regs<M, FIT_ABS>(cr); break;
+    default: part = fitness_half_regs<M, FIT_NNZ>(cr); break;
     }
-    slot_child = 2u * N + k + (half ? N : 0u);
-    {
-        uint4 *d = reinterpret_cast<uint4 *>(dst_pop + (size_t)slot_child * M);
+    const uint32_t sum = part + __shfl_xor_sync(FULL, part, 1);
+    const uint32_t f = p.kind == FIT_SQ ? fit_finish<FIT_SQ>(sum) : fit_finish<FIT_ABS>(sum);
+    if (valid && !sub) {
+        slot_out = 2u * N + k + (half ? N : 0u);
+        uint4 *d = reinterpret_cast<uint4 *>(dst_pop + (size_t)slot_out * M);
 #pragma unroll
         for (int v = 0; v < M / 4; ++v)
             d[v] = make_uint4(o[4 * v], o[4 * v + 1], o[4 * v + 2], o[4 * v + 3]);
-        p.fit[src ^ 1][slot_child] = f;
+        p.fit[src ^ 1][slot_out] = f;
+        f_out = f;
     }
-    f_child = f;
 }
 
 // ---------------------------------------------------------------------------
 // a7 -- incremental fitness of one offspring (warp-wide; not in the paper,
 // which recomputes G: derived from the fitness of Sec. 3.2 under the
-// operators of Sec. 3.4 and 3.5).  Its Gram / 2, h,
-// is assembled in its own buffer from the parents' buffers: entries with
-// j < c from the parent giving the first c columns (gt), entries with i >= c
-// from the other (gbm), the c(m - c) cross entries recomputed from the column
-// bits (ct: first-part columns, cb: second-part columns).  Then the mutation
-// runs flip by flip: a successful flip of rows r1, r2 in column cc changes
-// only row/column cc of G (by -2s(Q[r1][j] - Q[r2][j]), s = Q[r1][cc]), so
-// those m - 1 entries and the fitness are updated and the two bits flipped
-// in the offspring's columns `bo` (which hold the crossover result on entry).
-// The fitness is the sum of the per-entry terms, kept up to date on the way.
+// operators of Sec. 3.4 and 3.5).
+//
+// Each individual keeps H = G / 2 (int8) in 8 x 8 tiles of the upper
+// triangle (common.cuh).  A word holds the four entries (i, 4q .. 4q + 3).
+// For an offspring cut at c with flipped columns M (the columns where a
+// pair flip changed signs), a valid word is "changed" when i is in M, its
+// quad holds a column of M, or it is a cross word (i < c, q >= c / 4);
+// every other word lies in G[:c, :c] (copied from the parent giving the
+// first c columns, Gt) or in G[c:, c:] (from the other parent, Gb): a column
+// exchange keeps those blocks, and a pair flip in column cc changes only
+// row and column cc.
+//  Phase 1: every lane copies 16-byte groups (two rows of a tile) from Gt
+//           or Gb, writing 0 for changed words;
+//  Phase 2: the changed words are recomputed by popcount of the final
+//           columns `bo` (cross words c (m/4 - c/4), plus O(m) words per
+//           flipped column) and stored over the zeros.
+// The fitness terms of every stored word come from SIMD byte arithmetic
+// (dp4a), each word counted once.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int tri_index(int i, int j, int m) { return i * (m - 1) - (i * (i - 1)) / 2 + (j - i - 1); }
+__device__ __forceinline__ uint32_t mut_bit(const uint32_t (&mut)[4], int i) { return (mut[i >> 5] >> (i & 31)) & 1u; }
 
-__device__ __forceinline__ uint32_t mutation_word(const FusedPop &p, uint32_t gen, uint32_t o, int w)
+// 4-bit mask of the flipped columns among 4q .. 4q + 3.
+__device__ __forceinline__ uint32_t mut_quad(const uint32_t (&mut)[4], int q)
 {
-    return word_of(philox_block(p.seed, p.pop_id, OP_MUTATE, gen, o, 0u, (uint32_t)(w >> 2)), w & 3);
+    return (mut[q >> 3] >> ((q & 7) * 4)) & 0xFu;
+}
+
+// Word index of (row i, quad q) in the tiled layout (tile-row start S(I)).
+__device__ __forceinline__ uint32_t gram_word_index(int i, int q, int nb)
+{
+    const int I = i >> 3, J = q >> 1;
+    return (uint32_t)((I * nb - (I * (I - 1)) / 2 + (J - I)) * 16 + (i & 7) * 2 + (q & 1));
+}
+
+// The four half-Gram entries (i, 4q + k) from the bit columns (0 where
+// 4q + k <= i or >= m).
+template <int W>
+__device__ __forceinline__ uint32_t quad_word(const uint32_t *bo, int i, int q, int m)
+{
+    uint32_t ci[W];
+    load_col<W>(bo + i * W, ci);
+    uint32_t x = 0u;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int j = 4 * q + k;
+        if (j > i && j < m) {
+            uint32_t cj[W];
+            load_col<W>(bo + j * W, cj);
+            int d = 0;
+#pragma unroll
+            for (int w = 0; w < W; ++w)
+                d += __popc(ci[w] ^ cj[w]);
+            x |= ((uint32_t)((m >> 1) - d) & 0xFFu) << (8 * k);
+        }
+    }
+    return x;
+}
+
+// Source of word (i, q) in phase 1: 0 = Gt, 1 = Gb, 2 = zero (changed or
+// without entries).
+__device__ __forceinline__ int word_source(int i, int q, int m, int c, int qc, const uint32_t (&mut)[4])
+{
+    if (i >= m || 4 * q >= m || 4 * q + 3 <= i)
+        return 2;
+    if (mut_bit(mut, i) || mut_quad(mut, q) || (i < c && q >= qc))
+        return 2;
+    return i >= c ? 1 : 0;
 }
 
 template <int W, int KIND>
-__device__ uint32_t offspring_incremental(const FusedPop &p, uint32_t *bo, const uint32_t *ct, const uint32_t *cb,
-                                          int c, uint32_t gt, uint32_t gbm, uint32_t go, uint32_t gen, uint32_t o,
-                                          int lane)
+__device__ uint32_t offspring_incremental(const FusedPop &p, const uint32_t *bo, const uint32_t (&mut)[4], int c,
+                                          uint32_t gt, uint32_t gbm, uint32_t go, int lane)
 {
-    const int m = p.m, half_m = m >> 1;
-    const int8_t *Gt = p.gram + (size_t)gt * p.dpad;
-    const int8_t *Gb = p.gram + (size_t)gbm * p.dpad;
-    int8_t *Go = p.gram + (size_t)go * p.dpad;
+    const int m = p.m, nb = gram_tiles_nb(m), nt = nb * (nb + 1) / 2, Q = m >> 2, qc = c >> 2;
+    const uint4 *Gt4 = reinterpret_cast<const uint4 *>(p.gram + (size_t)gt * p.dpad);
+    const uint4 *Gb4 = reinterpret_cast<const uint4 *>(p.gram + (size_t)gbm * p.dpad);
+    const uint32_t *Gt = reinterpret_cast<const uint32_t *>(Gt4), *Gb = reinterpret_cast<const uint32_t *>(Gb4);
+    uint32_t *Go = reinterpret_cast<uint32_t *>(p.gram + (size_t)go * p.dpad);
+    uint4 *Go4 = reinterpret_cast<uint4 *>(Go);
     uint32_t acc = 0;
-    int base = 0;
-    for (int i = 0; i < m - 1; ++i) {
-        const int L = m - 1 - i;
-        for (int jj = lane; jj < L; jj += 32) {
-            const int j = i + 1 + jj;
-            int h;
-            if (j < c) {
-                h = (int)__ldcg(reinterpret_cast<const signed char *>(Gt + base + jj));
-            } else if (i >= c) {
-                h = (int)__ldcg(reinterpret_cast<const signed char *>(Gb + base + jj));
-            } else {
-                int d = 0;
+
+    // ---- phase 1: groups g = 4 t + rp (tile t, row pair rp); a lane keeps
+    // its rp and walks tiles t = lane / 4 + 8 s
+    {
+        const int rp = lane & 3;
+        int I, J;
+        tile_coords(min(lane >> 2, nt - 1), nb, I, J);
+        constexpr int U = 4;
+        for (int t0 = lane >> 2; t0 < nt; t0 += 8 * U) {
+            uint4 v[U];
+            int src[U][4];
+            int tI[U], tJ[U];
 #pragma unroll
-                for (int w = 0; w < W; ++w)
-                    d += __popc(ct[i * W + w] ^ cb[j * W + w]);
-                h = half_m - d;
+            for (int u = 0; u < U; ++u) {
+                const int t = t0 + 8 * u;
+                tI[u] = I;
+                tJ[u] = J;
+                v[u] = make_uint4(0u, 0u, 0u, 0u);
+                if (t < nt) {
+                    const int i0 = 8 * I + 2 * rp;
+                    src[u][0] = word_source(i0, 2 * J, m, c, qc, mut);
+                    src[u][1] = word_source(i0, 2 * J + 1, m, c, qc, mut);
+                    src[u][2] = word_source(i0 + 1, 2 * J, m, c, qc, mut);
+                    src[u][3] = word_source(i0 + 1, 2 * J + 1, m, c, qc, mut);
+                    const size_t g = (size_t)t * 4 + rp;
+                    const int s0 = src[u][0];
+                    if (s0 != 2 && src[u][1] == s0 && src[u][2] == s0 && src[u][3] == s0) {
+                        v[u] = __ldcg((s0 ? Gb4 : Gt4) + g);
+                    } else {
+                        uint32_t x[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            x[k] = src[u][k] == 2 ? 0u : __ldcg((src[u][k] ? Gb : Gt) + g * 4 + k);
+                        v[u] = make_uint4(x[0], x[1], x[2], x[3]);
+                    }
+                    // advance 8 tiles along the tile rows
+                    J += 8;
+                    while (J >= nb && I < nb - 1) {
+                        J = J - nb + I + 1;
+                        ++I;
+                    }
+                }
             }
-            __stcg(reinterpret_cast<signed char *>(Go) + base + jj, (signed char)h);
-            acc += fit_term<KIND>(2 * h);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int t = t0 + 8 * u;
+                if (t < nt) {
+                    __stcg(Go4 + (size_t)t * 4 + rp, v[u]);
+                    acc += (uint32_t)(word_terms<KIND>(v[u].x) + word_terms<KIND>(v[u].y) +
+                                      word_terms<KIND>(v[u].z) + word_terms<KIND>(v[u].w));
+                }
+            }
+            (void)tI;
+            (void)tJ;
         }
-        base += L;
     }
     __syncwarp();
-    // mutation, flip by flip; draw word w of offspring o (NC columns, then NR
-    // first rows, then NR second rows) is word w mod 4 of block w / 4
-    const int NC = p.NC, NR = p.NR;
-    for (int jc = 0; jc < NC; ++jc) {
-        const int cc = (int)uniform_int(mutation_word(p, gen, o, jc), 1u, (uint32_t)(m - 1));
-        uint32_t *col = bo + cc * W;
-        for (int ir = 0; ir < NR; ++ir) {
-            const int ra = (int)uniform_int(mutation_word(p, gen, o, NC + ir), 0u, (uint32_t)(m - 1));
-            const int rb = (int)uniform_int(mutation_word(p, gen, o, NC + NR + ir), 0u, (uint32_t)(m - 1));
-            const int ba = (int)((col[ra >> 5] >> (ra & 31)) & 1u), bb = (int)((col[rb >> 5] >> (rb & 31)) & 1u);
-            if (ba == bb)
-                continue;  // equal entries: no flip (the same on every lane)
-            const int s = ba ? -1 : 1;  // Q[r1][cc] before the flip
-            for (int j = lane; j < m; j += 32) {
-                if (j == cc)
-                    continue;
-                const int qa = ((bo[j * W + (ra >> 5)] >> (ra & 31)) & 1u) ? -1 : 1;
-                const int qb = ((bo[j * W + (rb >> 5)] >> (rb & 31)) & 1u) ? -1 : 1;
-                if (qa == qb)
-                    continue;
-                signed char *e = reinterpret_cast<signed char *>(Go) + (cc < j ? tri_index(cc, j, m) : tri_index(j, cc, m));
-                const int h0 = (int)__ldcg(e);
-                const int h1 = h0 - s * (qa - qb);  // G moves by -2s(qa - qb)
-                __stcg(e, (signed char)h1);
-                acc += fit_term<KIND>(2 * h1) - fit_term<KIND>(2 * h0);
+
+    // ---- phase 2a: cross words (i < c, q >= qc), flattened e = i (Q - qc) + (q - qc)
+    {
+        const int nq = Q - qc;
+        if (nq > 0) {
+            int i = lane / nq, q = qc + lane % nq;
+            const int total = c * nq;
+            for (int e = lane; e < total; e += 32) {
+                const uint32_t x = quad_word<W>(bo, i, q, m);
+                __stcg(Go + gram_word_index(i, q, nb), x);
+                acc += (uint32_t)word_terms<KIND>(x);
+                q += 32;
+                while (q >= Q) {
+                    q -= nq;
+                    ++i;
+                }
             }
-            __syncwarp();
-            if (lane == 0) {
-                col[ra >> 5] ^= 1u << (ra & 31);
-                col[rb >> 5] ^= 1u << (rb & 31);
-            }
-            __syncwarp();
         }
     }
-    return fit_finish<KIND>(warp_sum(acc));
+    // ---- phase 2b: rows and quads of the flipped columns, outside the cross words
+    for (int w = 0; w < 4; ++w) {
+        uint32_t bits = mut[w];
+        while (bits) {
+            const int cc = 32 * w + __ffs(bits) - 1;
+            bits &= bits - 1u;
+            // row cc: quads with an entry right of the diagonal
+            for (int q = (cc >> 2) + lane; q < Q; q += 32) {
+                if (cc < c && q >= qc)
+                    continue;  // a cross word
+                const uint32_t x = quad_word<W>(bo, cc, q, m);
+                __stcg(Go + gram_word_index(cc, q, nb), x);
+                acc += (uint32_t)word_terms<KIND>(x);
+            }
+            // quad of column cc, rows above it; done once per quad (by its
+            // lowest flipped column), rows of M belong to their row pass
+            const int qq = cc >> 2;
+            if ((mut_quad(mut, qq) & ((1u << (cc & 3)) - 1u)) != 0u)
+                continue;
+            for (int i = lane; i < 4 * qq + 3 && i < m; i += 32) {
+                if (mut_bit(mut, i) || (i < c && qq >= qc))
+                    continue;
+                const uint32_t x = quad_word<W>(bo, i, qq, m);
+                __stcg(Go + gram_word_index(i, qq, nb), x);
+                acc += (uint32_t)word_terms<KIND>(x);
+            }
+        }
+    }
+    return word_terms_finish<KIND>(warp_sum(acc));
 }
 
 // ---------------------------------------------------------------------------
-// 32 < m <= 128: a warp per pair, matrices staged in shared memory.
+// 32 < m <= 128: a warp per offspring, matrices staged in shared memory.
 // ---------------------------------------------------------------------------
-template <int W>
-__device__ void pair_warp(const FusedPop &p, PopSel &S, int src, uint32_t gen, uint32_t tch, uint32_t k,
-                          const Surv &sv, uint32_t *err, uint32_t *buf, uint32_t *hist_next, uint32_t *bhist)
+template <int W, bool INC>
+__device__ void offspring_warp(const FusedPop &p, PopSel &S, int src, uint32_t gen, uint32_t tch, uint32_t k,
+                               int half, const Surv &sv, uint32_t *err, uint32_t *buf, uint32_t *hist_next,
+                               uint32_t *bhist)
 {
     const int lane = threadIdx.x & 31;
     const int m = p.m;
     const uint32_t N = (uint32_t)p.N, words = (uint32_t)(m * W);
-    uint32_t s1 = 0, s2 = 0, F1 = 0, F2 = 0;
-    int c = 1;
-    if (lane == 0) {
-        const uint32_t *row = p.perm + (size_t)tch * 2u * N;
-        s1 = survivor_of(__ldg(row + k), p, S, sv, err);
-        s2 = survivor_of(__ldg(row + k + N), p, S, sv, err);
-        F1 = ldcg32(p.fit[src] + s1);
-        F2 = ldcg32(p.fit[src] + s2);
-        c = cut_point(p.seed, p.pop_id, gen, k, m);
-    }
-    s1 = __shfl_sync(FULL, s1, 0);
-    s2 = __shfl_sync(FULL, s2, 0);
-    c = __shfl_sync(FULL, c, 0);
-    // incremental mode: parents keep their Gram buffers, offspring take the
-    // buffers of the non-survivors k and k + N (in slot order)
-    const bool inc = p.gram != nullptr;
-    uint32_t gb1 = 0, gb2 = 0, go0 = 0, go1 = 0;
-    if (inc && lane == 0) {
-        gb1 = ldcg32(p.gidx[src] + s1);
-        gb2 = ldcg32(p.gidx[src] + s2);
-        go0 = ldcg32(p.gidx[src] + nonsurvivor_of(k, p, S, sv, err));
-        go1 = ldcg32(p.gidx[src] + nonsurvivor_of(k + N, p, S, sv, err));
-        const uint32_t P = (uint32_t)(4 * p.N);
-        if ((gb1 | gb2 | go0 | go1) >= P && (gb1 >= P || gb2 >= P || go0 >= P || go1 >= P)) {
-            atomicOr(err, ERR_INTERNAL);  // never expected: indices stay a permutation of [0, P)
-            gb1 = gb1 < P ? gb1 : 0u;
-            gb2 = gb2 < P ? gb2 : 0u;
-            go0 = go0 < P ? go0 : 0u;
-            go1 = go1 < P ? go1 : 0u;
+    const uint32_t oh = half ? N : 0u;  // slot offset of this half: parent k + oh, offspring 2N + k + oh
+    const bool inc = INC && p.gram != nullptr;
+    // lanes 0, 1: slots of the parents (survivors pi(k), pi(k + N)) and
+    // their fitness; lane 2 (incremental mode): slot of non-survivor k + oh,
+    // whose Gram buffer the offspring takes over
+    uint32_t look = 0, lf = 0;
+    if (lane < (inc ? 3 : 2)) {
+        if (lane < 2) {
+            look = survivor_of(__ldg(p.perm + (size_t)tch * 2u * N + k + (lane ? N : 0u)), p, S, sv, err);
+            lf = ldcg32(p.fit[src] + look);
+        } else {
+            look = nonsurvivor_of(k + oh, p, S, sv, err);
         }
-        p.gidx[src ^ 1][k] = gb1;
-        p.gidx[src ^ 1][k + N] = gb2;
-        p.gidx[src ^ 1][2u * N + k] = go0;
-        p.gidx[src ^ 1][3u * N + k] = go1;
     }
+    const uint32_t s1 = __shfl_sync(FULL, look, 0), s2 = __shfl_sync(FULL, look, 1);
+    const uint32_t Fp = __shfl_sync(FULL, lf, half);  // fitness of the parent this half carries over
+    const int c = cut_point(p.seed, p.pop_id, gen, k, m);
+    // incremental mode: parents keep their Gram buffers, offspring take the
+    // buffers of the non-survivors
+    uint32_t gb1 = 0, gb2 = 0, go = 0;
     if (inc) {
-        gb1 = __shfl_sync(FULL, gb1, 0);
-        gb2 = __shfl_sync(FULL, gb2, 0);
-        go0 = __shfl_sync(FULL, go0, 0);
-        go1 = __shfl_sync(FULL, go1, 0);
+        const uint32_t P = (uint32_t)(4 * p.N);
+        uint32_t g = lane < 3 ? ldcg32(p.gidx[src] + look) : 0u;
+        if (g >= P) {
+            atomicOr(err, ERR_INTERNAL);  // never expected: indices stay a permutation of [0, P)
+            g = 0u;
+        }
+        if (lane == half)
+            p.gidx[src ^ 1][k + oh] = g;
+        if (lane == 2)
+            p.gidx[src ^ 1][2u * N + k + oh] = g;
+        gb1 = __shfl_sync(FULL, g, 0);
+        gb2 = __shfl_sync(FULL, g, 1);
+        go = __shfl_sync(FULL, g, 2);
     }
     uint32_t *b1 = buf, *b2 = buf + words, *bo = buf + 2 * words;
     const uint32_t *sp = p.pop[src];
     uint32_t *dp = p.pop[src ^ 1];
-    for (uint32_t e = lane; e < words; e += 32) {
-        const uint32_t x = ldcg32(sp + (size_t)s1 * words + e), y = ldcg32(sp + (size_t)s2 * words + e);
-        b1[e] = x;
-        b2[e] = y;
-        dp[(size_t)k * words + e] = x;
-        dp[(size_t)(k + N) * words + e] = y;
-    }
-    if (lane == 0) {
-        p.fit[src ^ 1][k] = F1;
-        p.fit[src ^ 1][k + N] = F2;
-    }
-    uint32_t fc[2] = {0, 0};
-    for (int half = 0; half < 2; ++half) {
-        __syncwarp();
-        for (uint32_t e = lane; e < words; e += 32)
-            bo[e] = (((int)(e / W) < c) != (half != 0)) ? b1[e] : b2[e];
-        __syncwarp();
-        if (inc) {
-            uint32_t f;
-            switch (p.kind) {
-            case FIT_SQ: f = offspring_incremental<W, FIT_SQ>(p, bo, half ? b2 : b1, half ? b1 : b2, c, half ? gb2 : gb1, half ? gb1 : gb2, half ? go1 : go0, gen, k + (half ? N : 0u), lane); break;
-            case FIT_ABS: f = offspring_incremental<W, FIT_ABS>(p, bo, half ? b2 : b1, half ? b1 : b2, c, half ? gb2 : gb1, half ? gb1 : gb2, half ? go1 : go0, gen, k + (half ? N : 0u), lane); break;
-            default: f = offspring_incremental<W, FIT_NNZ>(p, bo, half ? b2 : b1, half ? b1 : b2, c, half ? gb2 : gb1, half ? gb1 : gb2, half ? go1 : go0, gen, k + (half ? N : 0u), lane); break;
-            }
-            const uint32_t slot = 2u * N + k + (half ? N : 0u);
-            for (uint32_t e = lane; e < words; e += 32)
-                dp[(size_t)slot * words + e] = bo[e];
-            if (lane == 0)
-                p.fit[src ^ 1][slot] = f;
-            fc[half] = f;
-            continue;
+    {
+        // both parents as 16-byte loads (words is a multiple of 4); this
+        // half's parent keeps its place k + oh in the next population
+        const uint32_t w4 = words >> 2;
+        const uint4 *pa = reinterpret_cast<const uint4 *>(sp) + (size_t)s1 * w4;
+        const uint4 *pb = reinterpret_cast<const uint4 *>(sp) + (size_t)s2 * w4;
+        uint4 *d4 = reinterpret_cast<uint4 *>(dp) + (size_t)(k + oh) * w4;
+        for (uint32_t e = lane; e < w4; e += 32) {
+            const uint4 x = __ldcg(pa + e), y = __ldcg(pb + e);
+            reinterpret_cast<uint4 *>(b1)[e] = x;
+            reinterpret_cast<uint4 *>(b2)[e] = y;
+            d4[e] = half ? y : x;
         }
-        if (lane == 0) {
-            Draws dr(p.seed, p.pop_id, gen, k + (half ? N : 0u));
-            uint8_t cols[64], r1[64], r2[64];
-            for (int jc = 0; jc < p.NC; ++jc)
-                cols[jc] = (uint8_t)uniform_int(dr.next(), 1u, (uint32_t)(m - 1));
-            for (int ir = 0; ir < p.NR; ++ir)
-                r1[ir] = (uint8_t)uniform_int(dr.next(), 0u, (uint32_t)(m - 1));
-            for (int ir = 0; ir < p.NR; ++ir)
-                r2[ir] = (uint8_t)uniform_int(dr.next(), 0u, (uint32_t)(m - 1));
-            for (int jc = 0; jc < p.NC; ++jc) {
-                uint32_t *col = bo + cols[jc] * W;
-                for (int ir = 0; ir < p.NR; ++ir) {
-                    const int ra = r1[ir], rb = r2[ir];
-                    const uint32_t ba = (col[ra >> 5] >> (ra & 31)) & 1u, bb = (col[rb >> 5] >> (rb & 31)) & 1u;
-                    if (ba != bb) {
-                        col[ra >> 5] ^= 1u << (ra & 31);
-                        col[rb >> 5] ^= 1u << (rb & 31);
-                    }
+    }
+    if (lane == 0)
+        p.fit[src ^ 1][k + oh] = Fp;
+    __syncwarp();
+    // crossover (Sec. 3.4): O1 = P1[:, :c] | P2[:, c:], O2 = P2[:, :c] | P1[:, c:]
+    for (uint32_t e = lane; e < words; e += 32)
+        bo[e] = (((int)(e / W) < c) != (half != 0)) ? b1[e] : b2[e];
+    __syncwarp();
+    // mutation (Sec. 3.5) in lane 0, sequential semantics; mut marks the
+    // columns where a flip happened
+    uint32_t mut[4] = {0u, 0u, 0u, 0u};
+    if (lane == 0) {
+        Draws dr(p.seed, p.pop_id, gen, k + oh);
+        uint8_t cols[64], r1[64], r2[64];
+        for (int jc = 0; jc < p.NC; ++jc)
+            cols[jc] = (uint8_t)uniform_int(dr.next(), 1u, (uint32_t)(m - 1));
+        for (int ir = 0; ir < p.NR; ++ir)
+            r1[ir] = (uint8_t)uniform_int(dr.next(), 0u, (uint32_t)(m - 1));
+        for (int ir = 0; ir < p.NR; ++ir)
+            r2[ir] = (uint8_t)uniform_int(dr.next(), 0u, (uint32_t)(m - 1));
+        for (int jc = 0; jc < p.NC; ++jc) {
+            const int cc = cols[jc];
+            uint32_t *col = bo + cc * W;
+            for (int ir = 0; ir < p.NR; ++ir) {
+                const int ra = r1[ir], rb = r2[ir];
+                const uint32_t ba = (col[ra >> 5] >> (ra & 31)) & 1u, bb = (col[rb >> 5] >> (rb & 31)) & 1u;
+                if (ba != bb) {
+                    col[ra >> 5] ^= 1u << (ra & 31);
+                    col[rb >> 5] ^= 1u << (rb & 31);
+                    mut[cc >> 5] |= 1u << (cc & 31);
                 }
             }
         }
-        __syncwarp();
-        uint32_t f;
+    }
+    __syncwarp();
+    uint32_t f = 0;
+    if constexpr (INC) {
+        if (inc) {
+#pragma unroll
+            for (int w = 0; w < 4; ++w)
+                mut[w] = __shfl_sync(FULL, mut[w], 0);
+            const uint32_t gt = half ? gb2 : gb1, gbm = half ? gb1 : gb2;
+            switch (p.kind) {
+            case FIT_SQ: f = offspring_incremental<W, FIT_SQ>(p, bo, mut, c, gt, gbm, go, lane); break;
+            case FIT_ABS: f = offspring_incremental<W, FIT_ABS>(p, bo, mut, c, gt, gbm, go, lane); break;
+            default: f = offspring_incremental<W, FIT_NNZ>(p, bo, mut, c, gt, gbm, go, lane); break;
+            }
+        }
+    }
+    if (!inc) {
         switch (p.kind) {
         case FIT_SQ: f = warp_fitness_cols<W, FIT_SQ>(bo, m, lane); break;
         case FIT_ABS: f = warp_fitness_cols<W, FIT_ABS>(bo, m, lane); break;
         default: f = warp_fitness_cols<W, FIT_NNZ>(bo, m, lane); break;
         }
-        const uint32_t slot = 2u * N + k + (half ? N : 0u);
-        for (uint32_t e = lane; e < words; e += 32)
-            dp[(size_t)slot * words + e] = bo[e];
-        if (lane == 0)
-            p.fit[src ^ 1][slot] = f;
-        fc[half] = f;
     }
+    const uint32_t slot = 2u * N + k + oh;
+    for (uint32_t e = lane; e < (words >> 2); e += 32)
+        reinterpret_cast<uint4 *>(dp)[(size_t)slot * (words >> 2) + e] = reinterpret_cast<const uint4 *>(bo)[e];
     if (lane == 0) {
-        const uint32_t fv[4] = {F1, F2, fc[0], fc[1]};
-        const uint32_t slots[4] = {k, k + N, 2u * N + k, 3u * N + k};
+        p.fit[src ^ 1][slot] = f;
+        const uint32_t fv[2] = {Fp, f};
+        const uint32_t slots[2] = {k + oh, slot};
         unsigned long long bk = ~0ull;
         uint32_t orr = 0;
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < 2; ++i) {
             if (fv[i] <= S.capn)
                 atomicAdd((S.boff != 0xFFFFFFFFu ? bhist + S.boff : hist_next) + (fv[i] >> S.shiftn), 1u);
             orr |= fv[i];
@@ -665,11 +820,14 @@ __device__ __forceinline__ int owner_of(uint32_t x, int npop, Base base)
 
 } // namespace
 
+// INC: compiled with the incremental Gram path of the warp-per-pair build
+// (launched when a population keeps its Gram), so that its register needs
+// stay out of the other instantiation.
+template <bool INC>
 __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constant__ FusedParams prm)
 {
     extern __shared__ __align__(16) uint32_t dyn[];
     __shared__ PopSel S[kMaxPops];
-    __shared__ uint32_t s_tmp[33];
     __shared__ unsigned long long s_tmp64[32];
     __shared__ uint32_t hoff[kMaxPops];
     __shared__ int s_flag;
@@ -687,7 +845,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
     const uint32_t r1 = max(4u * TT, 2u * kHistSmem);
     unsigned long long *tm = reinterpret_cast<unsigned long long *>(dyn);
     unsigned long long *ex = tm + TT;
-    uint32_t *hcnt = dyn, *hpre = dyn + kHistSmem;
+    uint32_t *hcnt = dyn;
     uint32_t *bhist = dyn + r1;  // block-local histograms of the next generation
     uint32_t *wbuf = bhist + kHistSmem + wib * prm.warp_buf_words;
     const Surv sv{tm, ex};
@@ -750,6 +908,37 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
         const int par = t & 1;
 
         // ---- phase A: threshold of the 2N smallest ---------------------------------
+        // loads first: the OR word of the current fitness values and the
+        // first group's histogram buckets (populations [0, g1) whose buckets
+        // fit the staging area), held in registers while the
+        // selection-independent draws are computed
+        const uint32_t vload = tid < npop ? ldcg32(stat_of(prm.p[tid]) + 1 + par) : 0u;
+        int g1 = 0;
+        uint32_t goff = 0;
+        while (g1 < npop) {
+            const uint32_t nb = (S[g1].cap >> S[g1].shift) + 1u;
+            if (g1 > 0 && goff + nb > kHistSmem)
+                break;
+            goff += nb;
+            ++g1;
+        }
+        constexpr int kStageRegs = 8;  // buckets per thread staged through registers
+        uint32_t hv[kStageRegs];
+#pragma unroll
+        for (int r = 0; r < kStageRegs; ++r) {
+            const uint32_t e = (uint32_t)tid + (uint32_t)r * kFusedThreads;
+            hv[r] = 0u;
+            if (e < goff) {
+                int i = 0;
+                uint32_t base = 0, nb = (S[0].cap >> S[0].shift) + 1u;
+                while (i + 1 < g1 && e >= base + nb) {
+                    base += nb;
+                    ++i;
+                    nb = (S[i].cap >> S[i].shift) + 1u;
+                }
+                hv[r] = ldcg32(hist_of(prm.p[i], par) + (e - base));
+            }
+        }
         // first tile of this warp: its fitness is loaded now, with the histograms
         uint32_t f_pre = 0;
         int i_pre = 0;
@@ -759,10 +948,21 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             const uint32_t q = (gwarp - p.tile_base) * 32u + lane;
             f_pre = q < (uint32_t)(4 * p.N) ? ldcg32(p.fit[src] + q) : 0u;
         }
-        if (tid < npop) {
-            PopSel &s = S[tid];
-            s.v = ctz_or(ldcg32(stat_of(prm.p[tid]) + 1 + par));
-            s.need = 0xFFFFFFFFu;  // marks "crossing not found"
+        // selection-independent draws of this warp's first build item
+        Pre pre0{0u, 1u, 1u, 0u, 0u};
+        const uint32_t nwork_t = prm.thread_slots >> 5;
+        if (gwarp < nwork_t) {
+            const uint32_t u = gwarp * 32u + (uint32_t)lane;
+            int i = -1;
+            for (int j = 0; j < npop; ++j)
+                if (prm.p[j].m <= 32 && u >= prm.p[j].work_base)
+                    i = (i < 0 || prm.p[j].work_base >= prm.p[i].work_base) ? j : i;
+            if (i >= 0) {
+                const FusedPop &p = prm.p[i];
+                const uint32_t local = u - p.work_base, k = local >> 2;
+                if (k < (uint32_t)p.N)
+                    pre0 = make_pre(p, S[i].gen0 + 1u + (uint32_t)t, (uint32_t)t, k, (int)((local >> 1) & 1u));
+            }
         }
         for (int i = 0; i < npop; ++i) {
             uint32_t *hn = hist_of(prm.p[i], par ^ 1);
@@ -774,8 +974,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             stat_of(p)[1 + (par ^ 1)] = 0u;
             p.traj[(S[tid].gen0 + (uint32_t)t) % (uint32_t)p.traj_cap] = ~0ull;
         }
-        // histograms staged in shared memory (groups of populations that fit),
-        // scanned in one block-wide pass, crossing of 2N located per population
+        if (tid == 0)
+            s_flag = 0;
+        // histograms staged in shared memory (groups of populations that
+        // fit); one warp per population finds the crossing of 2N and, when
+        // its bucket holds a single value, fixes the threshold right away
         for (int i0 = 0; i0 < npop;) {
             uint32_t off = 0;
             int i1 = i0;
@@ -788,127 +991,126 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                 off += nb;
                 ++i1;
             }
-            __syncthreads();
-            for (uint32_t e = tid; e < off; e += blockDim.x) {
-                int i = i0;
-                while (i + 1 < i1 && e >= hoff[i + 1])
-                    ++i;
-                hcnt[e] = ldcg32(hist_of(prm.p[i], par) + (e - hoff[i]));
+            if (i0 == 0) {
+                // the first group: from the registers, and beyond them directly
+#pragma unroll
+                for (int r = 0; r < kStageRegs; ++r) {
+                    const uint32_t e = (uint32_t)tid + (uint32_t)r * kFusedThreads;
+                    if (e < off)
+                        hcnt[e] = hv[r];
+                }
+                if (tid < npop) {
+                    S[tid].v = ctz_or(vload);
+                    S[tid].need = 0xFFFFFFFFu;  // marks "crossing not found"
+                }
+                __syncthreads();
+                for (uint32_t e = (uint32_t)tid + kStageRegs * kFusedThreads; e < off; e += blockDim.x) {
+                    int i = 0;
+                    while (i + 1 < i1 && e >= hoff[i + 1])
+                        ++i;
+                    hcnt[e] = ldcg32(hist_of(prm.p[i], par) + (e - hoff[i]));
+                }
+            } else {
+                __syncthreads();
+                for (uint32_t e = tid; e < off; e += blockDim.x) {
+                    int i = i0;
+                    while (i + 1 < i1 && e >= hoff[i + 1])
+                        ++i;
+                    hcnt[e] = ldcg32(hist_of(prm.p[i], par) + (e - hoff[i]));
+                }
             }
             __syncthreads();
-            block_scan_chunks(off, [&](uint32_t e) { return hcnt[e]; }, hpre, s_tmp);
-            for (uint32_t e = tid; e < off; e += blockDim.x) {
-                int i = i0;
-                while (i + 1 < i1 && e >= hoff[i + 1])
-                    ++i;
-                const uint32_t need = (uint32_t)(2 * prm.p[i].N);
-                const uint32_t x = hpre[e] - hpre[hoff[i]], h = hcnt[e];
-                if (h && x < need && need <= x + h) {
-                    S[i].lo = (e - hoff[i]) << S[i].shift;
-                    S[i].need = need - x;
+            if (wib < i1 - i0) {
+                const int i = i0 + wib;
+                PopSel &s = S[i];
+                const uint32_t nb = (s.cap >> s.shift) + 1u;
+                const uint32_t need2 = (uint32_t)(2 * prm.p[i].N);
+                uint32_t b = 0, before = 0;
+                const bool found = warp_find_crossing_smem(hcnt + hoff[i], nb, need2, b, before);
+                if (lane == 0) {
+                    if (found) {
+                        s.lo = b << s.shift;
+                        s.need = need2 - before;
+                    } else {
+                        atomicOr(err, ERR_INTERNAL);
+                        s.lo = 0;
+                        s.need = 1;
+                    }
+                    s.sr = s.shift;
+                    s.exact = s.shift <= s.v ? 1u : 0u;
+                    if (s.exact) {
+                        s.T = s.lo;
+                        s.take = s.need;
+                        s.capn = s.T;
+                        s.shiftn = max(s.v, shift_for(s.T));
+                        s.bor = 0u;
+                        s.bbest = ~0ull;
+                    } else {
+                        atomicOr(&s_flag, 1);
+                    }
                 }
             }
             __syncthreads();
             i0 = i1;
         }
-        if (tid == 0)
-            s_flag = 0;
-        if (tid < npop) {
-            PopSel &s = S[tid];
-            if (s.need == 0xFFFFFFFFu) {
-                atomicOr(err, ERR_INTERNAL);
-                s.lo = 0;
-                s.need = 1;
-            }
-            s.sr = s.shift;
-            s.exact = s.shift <= s.v ? 1u : 0u;
-        }
-        __syncthreads();
-        if (tid < npop && !S[tid].exact)
-            atomicOr(&s_flag, 1);
-        __syncthreads();
         // refinement passes while a candidate bucket may hold several values
-        while (s_flag) {
-            const int rl = (int)(ref_level % 3u), rz = (int)((ref_level + 1u) % 3u);
-            for (int i = 0; i < npop; ++i) {
-                const FusedPop &p = prm.p[i];
-                uint32_t *hz = ref_of(p, rz);
-                for (uint32_t e = gtid; e < (uint32_t)kHistR; e += gthreads)
-                    hz[e] = 0u;
-                if (S[i].exact)
-                    continue;
-                const uint32_t P = (uint32_t)(4 * p.N);
-                const uint32_t lo = S[i].lo, sr = S[i].sr;
-                const uint32_t sn = max(S[i].v, sr > 12u ? sr - 12u : 0u);
-                uint32_t *h = ref_of(p, rl);
-                const uint32_t span = (P + 31u) & ~31u;
-                for (uint32_t q = gtid; q < ((span + gthreads - 1) / gthreads) * gthreads; q += gthreads) {
-                    const bool in = q < P;
-                    const uint32_t f = in ? ldcg32(p.fit[src] + q) : 0u;
-                    const bool hit = in && f >= lo && ((uint64_t)(f - lo) >> sr) == 0u;
-                    warp_hist_add(h, hit, hit ? (f - lo) >> sn : 0u);
+        if (s_flag) {
+            while (s_flag) {
+                const int rl = (int)(ref_level % 3u), rz = (int)((ref_level + 1u) % 3u);
+                for (int i = 0; i < npop; ++i) {
+                    const FusedPop &p = prm.p[i];
+                    uint32_t *hz = ref_of(p, rz);
+                    for (uint32_t e = gtid; e < (uint32_t)kHistR; e += gthreads)
+                        hz[e] = 0u;
+                    if (S[i].exact)
+                        continue;
+                    const uint32_t P = (uint32_t)(4 * p.N);
+                    const uint32_t lo = S[i].lo, sr = S[i].sr;
+                    const uint32_t sn = max(S[i].v, sr > 12u ? sr - 12u : 0u);
+                    uint32_t *h = ref_of(p, rl);
+                    const uint32_t span = (P + 31u) & ~31u;
+                    for (uint32_t q = gtid; q < ((span + gthreads - 1) / gthreads) * gthreads; q += gthreads) {
+                        const bool in = q < P;
+                        const uint32_t f = in ? ldcg32(p.fit[src] + q) : 0u;
+                        const bool hit = in && f >= lo && ((uint64_t)(f - lo) >> sr) == 0u;
+                        warp_hist_add(h, hit, hit ? (f - lo) >> sn : 0u);
+                    }
                 }
-            }
-            if (!grid_barrier(prm.bar, nblocks, epoch, err))
-                return;
-            if (wib < npop && !S[wib].exact) {
-                const FusedPop &p = prm.p[wib];
-                PopSel &s = S[wib];
-                const uint32_t sn = max(s.v, s.sr > 12u ? s.sr - 12u : 0u);
-                uint32_t b, before;
-                warp_find_bucket(ref_of(p, rl), 1u << (s.sr - sn), s.need, err, b, before);
-                if (lane == 0) {
-                    s.lo += b << sn;
-                    s.need -= before;
-                    s.sr = sn;
-                    s.exact = sn <= s.v ? 1u : 0u;
+                if (!grid_barrier(prm.bar, nblocks, epoch, err))
+                    return;
+                if (wib < npop && !S[wib].exact) {
+                    const FusedPop &p = prm.p[wib];
+                    PopSel &s = S[wib];
+                    const uint32_t sn = max(s.v, s.sr > 12u ? s.sr - 12u : 0u);
+                    uint32_t b, before;
+                    warp_find_bucket(ref_of(p, rl), 1u << (s.sr - sn), s.need, err, b, before);
+                    if (lane == 0) {
+                        s.lo += b << sn;
+                        s.need -= before;
+                        s.sr = sn;
+                        s.exact = sn <= s.v ? 1u : 0u;
+                    }
                 }
+                ++ref_level;
+                __syncthreads();
+                if (tid == 0) {
+                    int any = 0;
+                    for (int i = 0; i < npop; ++i)
+                        any |= S[i].exact ? 0 : 1;
+                    s_flag = any;
+                }
+                __syncthreads();
             }
-            ++ref_level;
+            if (tid < npop) {
+                PopSel &s = S[tid];
+                s.T = s.lo;
+                s.take = s.need;
+                s.capn = s.T;
+                s.shiftn = max(s.v, shift_for(s.T));
+                s.bor = 0u;
+                s.bbest = ~0ull;
+            }
             __syncthreads();
-            if (tid == 0) {
-                int any = 0;
-                for (int i = 0; i < npop; ++i)
-                    any |= S[i].exact ? 0 : 1;
-                s_flag = any;
-            }
-            __syncthreads();
-        }
-        if (tid < npop) {
-            PopSel &s = S[tid];
-            s.T = s.lo;
-            s.take = s.need;
-            s.capn = s.T;
-            s.shiftn = max(s.v, shift_for(s.T));
-            s.bor = 0u;
-            s.bbest = ~0ull;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            uint32_t off = 0;
-            for (int i = 0; i < npop; ++i) {
-                const uint32_t nb = (S[i].capn >> S[i].shiftn) + 1u;
-                S[i].boff = off + nb <= kHistSmem ? off : 0xFFFFFFFFu;
-                if (off + nb <= kHistSmem)
-                    off += nb;
-            }
-        }
-        // selection-independent draws of this warp's first build item, computed
-        // while the other blocks catch up
-        Pre pre0{0u, 1u, 1u, 0u, 0u};
-        const uint32_t nwork_t = prm.thread_slots >> 5;
-        if (gwarp < nwork_t) {
-            const uint32_t u = gwarp * 32u + (uint32_t)lane;
-            int i = -1;
-            for (int j = 0; j < npop; ++j)
-                if (prm.p[j].m <= 32 && u >= prm.p[j].work_base)
-                    i = (i < 0 || prm.p[j].work_base >= prm.p[i].work_base) ? j : i;
-            if (i >= 0) {
-                const FusedPop &p = prm.p[i];
-                const uint32_t local = u - p.work_base, k = local >> 1;
-                if (k < (uint32_t)p.N)
-                    pre0 = make_pre(p, S[i].gen0 + 1u + (uint32_t)t, (uint32_t)t, k, (int)(local & 1u));
-            }
         }
         // tile masks: F < T and F == T per 32 slots
         for (uint32_t tl = gwarp; tl < TT; tl += gwarps) {
@@ -921,6 +1123,17 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             const uint32_t eq = __ballot_sync(FULL, q < P && f == T);
             if (lane == 0)
                 p.tmask[tl - p.tile_base] = (unsigned long long)lt | ((unsigned long long)eq << 32);
+        }
+        // block-local histogram offsets of the next generation (read after
+        // the barrier's bar.sync)
+        if (tid == 0) {
+            uint32_t off = 0;
+            for (int i = 0; i < npop; ++i) {
+                const uint32_t nb = (S[i].capn >> S[i].shiftn) + 1u;
+                S[i].boff = off + nb <= kHistSmem ? off : 0xFFFFFFFFu;
+                if (off + nb <= kHistSmem)
+                    off += nb;
+            }
         }
         if (!grid_barrier(prm.bar, nblocks, epoch, err))
             return;
@@ -967,7 +1180,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                 atomicOr(err, ERR_INTERNAL);
         }
         __syncthreads();
-        // m <= 32: two threads per pair
+        // m <= 32: four threads per pair
         for (uint32_t w = gwarp; w < nwork_t; w += gwarps) {
             const uint32_t u = w * 32u;
             // the population whose (32-aligned) thread range holds this warp
@@ -977,19 +1190,19 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                     i = (i < 0 || prm.p[j].work_base >= prm.p[i].work_base) ? j : i;
             const FusedPop &p = prm.p[i < 0 ? 0 : i];
             const uint32_t local = u + (uint32_t)lane - p.work_base;
-            const uint32_t k = local >> 1;
-            const int half = (int)(local & 1u);
+            const uint32_t k = local >> 2;
+            const int half = (int)((local >> 1) & 1u), sub = (int)(local & 1u);
             const bool valid = i >= 0 && k < (uint32_t)p.N;
             const uint32_t gen = S[i < 0 ? 0 : i].gen0 + 1u + (uint32_t)t;
             Pre pre = pre0;
             if (w != gwarp && valid)
                 pre = make_pre(p, gen, (uint32_t)t, k, half);
-            uint32_t fpar = 0, spar = 0, fch = 0, sch = 0;
+            uint32_t fv = 0, sl = 0;
             const PopSel &s = S[i < 0 ? 0 : i];
             switch (p.m) {
 #define HADGA_PT(MM)                                                                                        \
     case MM:                                                                                                \
-        pair_thread<MM>(p, s, src, gen, pre, k, half, valid, sv, err, fpar, spar, fch, sch);                \
+        pair_thread<MM>(p, s, src, gen, pre, k, half, sub, valid, sv, err, fv, sl);                         \
         break;
                 HADGA_PT(4) HADGA_PT(8) HADGA_PT(12) HADGA_PT(16) HADGA_PT(20) HADGA_PT(24) HADGA_PT(28) HADGA_PT(32)
 #undef HADGA_PT
@@ -997,45 +1210,37 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                 break;
             }
             if (s.boff != 0xFFFFFFFFu) {
-                uint32_t *bh = bhist + s.boff;
-                if (valid && fpar <= s.capn)
-                    atomicAdd(bh + (fpar >> s.shiftn), 1u);
-                if (valid && fch <= s.capn)
-                    atomicAdd(bh + (fch >> s.shiftn), 1u);
+                if (valid && fv <= s.capn)
+                    atomicAdd(bhist + s.boff + (fv >> s.shiftn), 1u);
             } else {
-                uint32_t *hn = hist_of(p, par ^ 1);
-                warp_hist_add(hn, valid && fpar <= s.capn, fpar >> s.shiftn);
-                warp_hist_add(hn, valid && fch <= s.capn, fch >> s.shiftn);
+                warp_hist_add(hist_of(p, par ^ 1), valid && fv <= s.capn, fv >> s.shiftn);
             }
-            const uint32_t orr = warp_or(valid ? (fpar | fch) : 0u);
-            unsigned long long key = ~0ull;
-            if (valid) {
-                const unsigned long long k1 = ((unsigned long long)fpar << 32) | spar;
-                const unsigned long long k2 = ((unsigned long long)fch << 32) | sch;
-                key = k1 < k2 ? k1 : k2;
-            }
+            const uint32_t orr = warp_or(valid ? fv : 0u);
+            unsigned long long key = valid ? (((unsigned long long)fv << 32) | sl) : ~0ull;
             key = warp_min_u64(key);
             if (lane == 0 && i >= 0) {
                 atomicOr(&S[i].bor, orr);
                 atomicMin(&S[i].bbest, key);
             }
         }
-        // 32 < m <= 128: a warp per pair
-        for (uint32_t pr = gwarp; pr < prm.warp_pairs; pr += gwarps) {
+        // 32 < m <= 128: a warp per offspring (items 2k + half)
+        for (uint32_t it = gwarp; it < prm.warp_items; it += gwarps) {
             int i = -1;
             for (int j = 0; j < npop; ++j)
-                if (prm.p[j].m > 32 && pr >= prm.p[j].work_base && pr < prm.p[j].work_base + (uint32_t)prm.p[j].N)
+                if (prm.p[j].m > 32 && it >= prm.p[j].work_base &&
+                    it < prm.p[j].work_base + 2u * (uint32_t)prm.p[j].N)
                     i = j;
             if (i < 0)
                 continue;
             const FusedPop &p = prm.p[i];
-            const uint32_t k = pr - p.work_base;
+            const uint32_t item = it - p.work_base, k = item >> 1;
+            const int half = (int)(item & 1u);
             uint32_t *hn = hist_of(p, par ^ 1);
             const uint32_t gen = S[i].gen0 + 1u + (uint32_t)t;
             switch (p.W) {
-            case 2: pair_warp<2>(p, S[i], src, gen, (uint32_t)t, k, sv, err, wbuf, hn, bhist); break;
-            case 3: pair_warp<3>(p, S[i], src, gen, (uint32_t)t, k, sv, err, wbuf, hn, bhist); break;
-            case 4: pair_warp<4>(p, S[i], src, gen, (uint32_t)t, k, sv, err, wbuf, hn, bhist); break;
+            case 2: offspring_warp<2, INC>(p, S[i], src, gen, (uint32_t)t, k, half, sv, err, wbuf, hn, bhist); break;
+            case 3: offspring_warp<3, INC>(p, S[i], src, gen, (uint32_t)t, k, half, sv, err, wbuf, hn, bhist); break;
+            case 4: offspring_warp<4, INC>(p, S[i], src, gen, (uint32_t)t, k, half, sv, err, wbuf, hn, bhist); break;
             default: break;
             }
         }
@@ -1090,16 +1295,20 @@ size_t fused_smem_bytes(const FusedParams &p)
 
 cudaError_t fused_grid(size_t smem, int *grid)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    int dev = 0, sms = 0, per = 0;
+    int dev = 0, sms = 0, per0 = 0, per1 = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused, kFusedThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per0, k_fused<false>, kFusedThreads, smem);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, k_fused<true>, kFusedThreads, smem);
     if (e != cudaSuccess)
         return e;
-    if (per < 1)
+    if (per0 < 1 || per1 < 1)
         return cudaErrorCooperativeLaunchTooLarge;
     *grid = sms;  // one resident block per SM
     return cudaSuccess;
@@ -1107,8 +1316,12 @@ cudaError_t fused_grid(size_t smem, int *grid)
 
 cudaError_t launch_fused(const FusedParams &p, int grid, size_t smem, cudaStream_t s)
 {
+    bool inc = false;
+    for (int i = 0; i < p.npop; ++i)
+        inc = inc || p.p[i].gram != nullptr;
     void *args[] = {(void *)&p};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_fused, dim3(grid), dim3(kFusedThreads), args, smem, s);
+    const void *fn = inc ? (const void *)k_fused<true> : (const void *)k_fused<false>;
+    cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kFusedThreads), args, smem, s);
     if (e == cudaSuccess)
         note_launches(1);
     return e;

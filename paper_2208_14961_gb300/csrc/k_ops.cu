@@ -272,9 +272,29 @@ cudaError_t launch_convert(const void *src, int src_storage, void *dst, int dst_
 }
 
 // ---------------------------------------------------------------------------
-// Gram store of the incremental mode: one warp per matrix, row i of the upper
-// triangle by the lanes, entry = (m - 2 popc(b_i ^ b_j)) / 2.
+// Tiled half-Gram of the incremental mode, recomputed from the bit columns:
+// one warp per matrix, a half-warp per 8 x 8 tile, a lane per word of four
+// entries (i, j..j+3); 0 where i >= j or outside m.
 // ---------------------------------------------------------------------------
+template <int W>
+__device__ __forceinline__ uint32_t tile_word(const uint32_t *cols, int m, int I, int J, int wi)
+{
+    const int i = 8 * I + (wi >> 1), j0 = 8 * J + (wi & 1) * 4;
+    uint32_t x = 0u;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int j = j0 + k;
+        if (i < j && j < m) {
+            int d = 0;
+#pragma unroll
+            for (int w = 0; w < W; ++w)
+                d += __popc(cols[i * W + w] ^ cols[j * W + w]);
+            x |= ((uint32_t)(m / 2 - d) & 0xFFu) << (8 * k);
+        }
+    }
+    return x;
+}
+
 template <int W>
 __global__ void __launch_bounds__(256) k_gram_store(const uint32_t *__restrict__ pop, int m, int64_t P, int8_t *gram,
                                                     int dpad, uint32_t *gidx)
@@ -284,23 +304,16 @@ __global__ void __launch_bounds__(256) k_gram_store(const uint32_t *__restrict__
     uint32_t *cols = s_c + (size_t)wib * m * W;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int nb = gram_tiles_nb(m), nt = gram_tiles(m);
     for (int64_t q = gw; q < P; q += nw) {
         for (int e = lane; e < m * W; e += 32)
             cols[e] = pop[(size_t)q * m * W + e];
         __syncwarp();
-        int8_t *G = gram + (size_t)q * dpad;
-        int base = 0;
-        for (int i = 0; i < m - 1; ++i) {
-            const int L = m - 1 - i;
-            for (int jj = lane; jj < L; jj += 32) {
-                const int j = i + 1 + jj;
-                int d = 0;
-#pragma unroll
-                for (int w = 0; w < W; ++w)
-                    d += __popc(cols[i * W + w] ^ cols[j * W + w]);
-                G[base + jj] = (int8_t)(m / 2 - d);
-            }
-            base += L;
+        uint32_t *G = reinterpret_cast<uint32_t *>(gram + (size_t)q * dpad);
+        for (int t = lane >> 4; t < nt; t += 2) {
+            int I, J;
+            tile_coords(t, nb, I, J);
+            G[(size_t)t * 16 + (lane & 15)] = tile_word<W>(cols, m, I, J, lane & 15);
         }
         if (lane == 0)
             gidx[q] = (uint32_t)q;
@@ -328,6 +341,9 @@ cudaError_t launch_gram_store(const uint32_t *pop, int m, int64_t P, int8_t *gra
     return cudaGetLastError();
 }
 
+// Full recomputation check: every stored word against the recomputed one
+// (counted per word that differs), and every fitness word against the sum
+// of the recomputed terms.
 template <int W>
 __global__ void __launch_bounds__(256) k_gram_check(const uint32_t *__restrict__ pop, int m, int64_t P, int kind,
                                                     const int8_t *__restrict__ gram, int dpad,
@@ -339,6 +355,7 @@ __global__ void __launch_bounds__(256) k_gram_check(const uint32_t *__restrict__
     uint32_t *cols = s_c + (size_t)wib * m * W;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int nb = gram_tiles_nb(m), nt = gram_tiles(m);
     unsigned long long bad_e = 0, bad_f = 0;
     for (int64_t q = gw; q < P; q += nw) {
         for (int e = lane; e < m * W; e += 32)
@@ -346,26 +363,21 @@ __global__ void __launch_bounds__(256) k_gram_check(const uint32_t *__restrict__
         __syncwarp();
         const uint32_t gq = gidx[q];
         const bool in_range = (int64_t)gq < P;
-        const int8_t *G = gram + (size_t)(in_range ? gq : 0u) * dpad;
+        const uint32_t *G = reinterpret_cast<const uint32_t *>(gram + (size_t)(in_range ? gq : 0u) * dpad);
         uint32_t acc = 0;
-        int base = 0;
-        for (int i = 0; i < m - 1; ++i) {
-            const int L = m - 1 - i;
-            for (int jj = lane; jj < L; jj += 32) {
-                const int j = i + 1 + jj;
-                int d = 0;
-#pragma unroll
-                for (int w = 0; w < W; ++w)
-                    d += __popc(cols[i * W + w] ^ cols[j * W + w]);
-                const int g = m - 2 * d;
-                acc += kind == FIT_SQ ? fit_term<FIT_SQ>(g) : kind == FIT_ABS ? fit_term<FIT_ABS>(g) : fit_term<FIT_NNZ>(g);
-                if (!in_range || (int)G[base + jj] != g / 2)
-                    ++bad_e;
-            }
-            base += L;
+        for (int t = lane >> 4; t < nt; t += 2) {
+            int I, J;
+            tile_coords(t, nb, I, J);
+            const uint32_t x = tile_word<W>(cols, m, I, J, lane & 15);
+            acc += (uint32_t)(kind == FIT_SQ ? word_terms<FIT_SQ>(x)
+                                             : kind == FIT_ABS ? word_terms<FIT_ABS>(x) : word_terms<FIT_NNZ>(x));
+            if (!in_range || G[(size_t)t * 16 + (lane & 15)] != x)
+                ++bad_e;
         }
         acc = warp_sum(acc);
-        const uint32_t f = kind == FIT_SQ ? acc : 2u * acc;
+        const uint32_t f = kind == FIT_SQ ? word_terms_finish<FIT_SQ>(acc)
+                                          : kind == FIT_ABS ? word_terms_finish<FIT_ABS>(acc)
+                                                            : word_terms_finish<FIT_NNZ>(acc);
         if (lane == 0 && f != fit[q])
             ++bad_f;
         __syncwarp();

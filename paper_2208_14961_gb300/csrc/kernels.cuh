@@ -62,8 +62,8 @@ cudaError_t launch_mutate(void *pop, int storage, int m, int64_t N, int NC, int 
 cudaError_t launch_best(const uint32_t *fit, int64_t P, unsigned long long *out, cudaStream_t s);
 cudaError_t launch_convert(const void *src, int src_storage, void *dst, int dst_storage, int m, int64_t P,
                            cudaStream_t s);
-// Upper-triangle Gram / 2 (int8, entry (i, j), i < j, at i(m-1) - i(i-1)/2 + j-i-1)
-// of P bit-storage matrices into gram[q * dpad]; gidx[q] = q.
+// Tiled half-Gram (common.cuh: 8 x 8 int8 tiles of the upper triangle of
+// G / 2) of P bit-storage matrices into gram[q * dpad]; gidx[q] = q.
 cudaError_t launch_gram_store(const uint32_t *pop, int m, int64_t P, int8_t *gram, int dpad, uint32_t *gidx,
                               cudaStream_t s);
 // Recomputes the Gram / 2 and fitness of P bit-storage matrices and counts,
@@ -120,9 +120,9 @@ struct FusedPop {
     const uint32_t *perm;      // [ngen][2N] survivor orders of the chunk
     unsigned long long *traj;  // [traj_cap] best keys (F << 32 | slot)
     uint32_t *gen_dev;         // generation counter: read at start, advanced at exit
-    int8_t *gram;              // incremental mode: [P][dpad] upper-triangle Gram / 2, or null
+    int8_t *gram;              // incremental mode: [P][dpad] tiled half-Gram (common.cuh), or null
     uint32_t *gidx[2];         // incremental mode: slot -> Gram buffer, ping-pong with pop
-    int32_t dpad;              // bytes per Gram buffer (m(m-1)/2 rounded up to 16)
+    int32_t dpad;              // bytes per Gram buffer (64 per tile)
     int32_t m, W, NC, NR, kind, traj_cap;
     int64_t N;
     uint32_t seed, pop_id;
@@ -135,7 +135,7 @@ struct FusedParams {
     int32_t npop;
     uint32_t total_tiles;
     uint32_t thread_slots;   // joint space of m <= 32 populations, 2 threads per pair, padded to 32
-    uint32_t warp_pairs;     // joint pair space of m > 32 populations
+    uint32_t warp_items;     // joint offspring space of m > 32 populations (one warp item each)
     int32_t ngen;            // generations to run
     int32_t stop_at_zero;    // stop after a generation whose best fitness (population 0) is 0
     int32_t src;             // ping-pong buffer holding the current population
