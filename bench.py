@@ -169,6 +169,14 @@ GRAM_PATHS = [  # name, storage, path
 ]
 
 
+def popc_per_dot(m):
+    """Population counts per column pair of the popcount Gram: W = ceil(m/32)
+    XOR words, reduced by carry-save adders for W >= 3 (2 counts at W = 3,
+    3 at W = 4..7, 4 at W = 8)."""
+    W = (m + 31) // 32
+    return W if W <= 2 else 2 if W == 3 else 3 if W <= 7 else 4
+
+
 def gram_sweep(args):
     """Precision sweep of the batched Gram + F_sq alone: balanced +-1
     populations of `--gram-gb` GiB of int8 (seed 2) at each order, every
@@ -231,7 +239,7 @@ def gram_sweep(args):
             nbytes = P * h.storage_bytes(storage, m)
             t_mem = nbytes / (hbm * 1e9)
             if name == "popc_bits" or name == "popc_int8":
-                ops, peak, unit = P * D * W, rates["popc_chain"], "popc"
+                ops, peak, unit = P * D * popc_per_dot(m), rates["popc_chain"], "popc"
             elif name == "int32":
                 ops, peak, unit = P * D * (m // 4), rates["dp4a"], "dp4a"
             elif name == "imma" and m % 32 == 0:

@@ -426,6 +426,7 @@ static ga_status fused_run(ga_ctx *const *ctxs, int n, int32_t generations, int 
         p.gen_dev = c->fmisc + 2;
         p.m = c->m;
         p.W = c->W;
+        p.nch = warp_gram_chunks(c->m);
         p.NC = c->cfg.NC;
         p.NR = c->cfg.NR;
         p.kind = c->cfg.fitness;
@@ -442,7 +443,7 @@ static ga_status fused_run(ga_ctx *const *ctxs, int n, int32_t generations, int 
         } else {
             p.work_base = wpairs;
             wpairs += (uint32_t)(2 * c->N);  // one warp item per offspring
-            max_words = std::max(max_words, 3 * c->m * c->W);
+            max_words = std::max(max_words, 2 * c->m * c->W + col_set_words(c->m, c->W));
         }
         if (int8) {
             cudaError_t e = launch_convert(c->pop, GA_STORE_INT8, c->bits[0], GA_STORE_BITS, c->m, c->P, c0->stream);

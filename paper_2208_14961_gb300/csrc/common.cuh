@@ -183,8 +183,7 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *tmp, u
 
 // ---------------------------------------------------------------------------
 // Warp-level fitness of one matrix whose bit columns (W words each) sit in
-// shared memory.  Lane a pairs column a with (a + s) mod m for s = 1..m/2,
-// the s = m/2 pair only when a < m/2, so each unordered pair is visited once.
+// shared memory (warp_fitness_cols below).
 // ---------------------------------------------------------------------------
 // One column of W words from shared memory with the widest aligned vector
 // loads (consecutive lanes reading consecutive columns stay bank-conflict
@@ -211,25 +210,162 @@ __device__ __forceinline__ void load_col(const uint32_t *col, uint32_t (&c)[W])
     }
 }
 
+// Carry-save adder: per bit, a + b + c = s + 2 * carry.
+__device__ __forceinline__ void csa(uint32_t a, uint32_t b, uint32_t c, uint32_t &s, uint32_t &carry)
+{
+    s = a ^ b ^ c;
+    carry = (a & b) | (c & (a | b));
+}
+
+// Rows where two bit columns differ, d = popc(a ^ b) over W words.  For
+// W >= 3 groups of three XOR words go through a carry-save adder first
+// (Harley and Seal's population-count method): popc(x0) + popc(x1) +
+// popc(x2) = popc(s) + 2 popc(carry), so W = 3, 4, 5 take W - 1 population
+// counts, W = 6, 7 take W - 2 and W = 8 takes 5 (a third adder joins the two
+// sums and x6).  The count is exact.  The population count unit issues at a
+// quarter of the integer ALU rate, so one adder (two logic operations)
+// per saved count pays.
+template <int W>
+__device__ __forceinline__ int xor_popc(const uint32_t (&a)[W], const uint32_t (&b)[W])
+{
+    uint32_t x[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k)
+        x[k] = a[k] ^ b[k];
+    if constexpr (W >= 3 && W <= 5) {
+        uint32_t s0, c0;
+        csa(x[0], x[1], x[2], s0, c0);
+        int d = __popc(s0) + 2 * __popc(c0);
+#pragma unroll
+        for (int k = 3; k < W; ++k)
+            d += __popc(x[k]);
+        return d;
+    } else if constexpr (W >= 6 && W <= 7) {
+        uint32_t s0, c0, s1, c1;
+        csa(x[0], x[1], x[2], s0, c0);
+        csa(x[3], x[4], x[5], s1, c1);
+        int d = __popc(s0) + __popc(s1) + 2 * (__popc(c0) + __popc(c1));
+        if constexpr (W == 7)
+            d += __popc(x[6]);
+        return d;
+    } else if constexpr (W == 8) {
+        uint32_t s0, c0, s1, c1, s2, c2;
+        csa(x[0], x[1], x[2], s0, c0);
+        csa(x[3], x[4], x[5], s1, c1);
+        csa(s0, s1, x[6], s2, c2);
+        return __popc(s2) + __popc(x[7]) + 2 * (__popc(c0) + __popc(c1) + __popc(c2));
+    } else {
+        int d = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w)
+            d += __popc(x[w]);
+        return d;
+    }
+}
+
+// Chunks per column of the warp-level Gram below: column a's pairs
+// (a, a + s mod m), s = 1..m/2, are split into `nch` runs of consecutive s
+// so that the m * nch work units spread evenly over the 32 lanes (cost of
+// a choice: rounds * (run length + 2), the 2 standing for the per-unit
+// set-up).  Evaluated once per kernel (or on the host), not per matrix.
+__host__ __device__ __forceinline__ int warp_gram_chunks(int m)
+{
+    const int half = m >> 1;
+    int best = 1, best_cost = 0x7FFFFFFF;
+    for (int n = 1; n <= 16 && n <= half; ++n) {
+        const int rounds = (m * n + 31) >> 5, run = (half + n - 1) / n;
+        const int cost = rounds * (run + 2);
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = n;
+        }
+    }
+    return best;
+}
+
+// A column set in shared memory holds the m bit columns followed by copies
+// of columns 0 .. m/2 - 2 (column m + j equals column j), so that the pairs
+// (a, a + s mod m), s <= m/2, of the warp-level Gram below read columns
+// a + s without wrapping: every lane runs the same trip count.
+__host__ __device__ __forceinline__ int col_set_cols(int m) { return m + m / 2; }
+
+// Words of a column set of order m with W words per column.
+__host__ __device__ __forceinline__ int col_set_words(int m, int W)
+{
+    return W <= 4 ? col_set_cols(m) * W : col_set_cols(m) * 4 * ((W + 3) / 4);
+}
+
+// Word w of column j of a column set.  W <= 4: column j at words
+// [jW, jW + W).  W > 4: planes of four words (plane p holds words 4p .. 4p+3
+// of every column, mc = col_set_cols(m) columns per plane), so that lanes
+// reading consecutive columns issue 16-byte loads at a 16-byte stride (no
+// bank conflicts).
+template <int W>
+__device__ __forceinline__ int col_word_index(int j, int w, int mc)
+{
+    return W <= 4 ? j * W + w : (w >> 2) * 4 * mc + j * 4 + (w & 3);
+}
+
+template <int W>
+__device__ __forceinline__ void load_col_any(const uint32_t *cols, int j, int mc, uint32_t (&c)[W])
+{
+    if constexpr (W <= 4) {
+        load_col<W>(cols + j * W, c);
+    } else {
+#pragma unroll
+        for (int p = 0; p < (W + 3) / 4; ++p) {
+            const uint4 x = reinterpret_cast<const uint4 *>(cols + p * 4 * mc)[j];
+            c[4 * p] = x.x;
+            if (4 * p + 1 < W)
+                c[(4 * p + 1) % W] = x.y;
+            if (4 * p + 2 < W)
+                c[(4 * p + 2) % W] = x.z;
+            if (4 * p + 3 < W)
+                c[(4 * p + 3) % W] = x.w;
+        }
+    }
+}
+
+// Stores word w of column j of a column set, and of its copy m + j.
+template <int W>
+__device__ __forceinline__ void store_col_word(uint32_t *cols, int j, int w, int m, uint32_t v)
+{
+    const int mc = col_set_cols(m);
+    cols[col_word_index<W>(j, w, mc)] = v;
+    if (j < (m >> 1) - 1)
+        cols[col_word_index<W>(j + m, w, mc)] = v;
+}
+
+// Every unordered pair once: pairs (a, a + s) for s = 1..m/2 (column a + s
+// >= m is the copy of column a + s - m), the s = m/2 pair only when
+// a < m/2.  Work units (run r of column a) are enumerated run-major, so
+// consecutive lanes read consecutive columns.  nch = warp_gram_chunks(m).
 template <int W, int KIND>
-__device__ __forceinline__ uint32_t warp_fitness_cols(const uint32_t *cols, int m, int lane)
+__device__ __forceinline__ uint32_t warp_fitness_cols(const uint32_t *cols, int m, int lane, int nch)
 {
     uint32_t acc = 0;
-    const int half = m >> 1;
-    for (int a = lane; a < m; a += 32) {
+    const int half = m >> 1, mc = col_set_cols(m);
+    const int run = (half + nch - 1) / nch, units = m * nch;
+    int r = 0, a = lane;
+    while (a >= m) {
+        a -= m;
+        ++r;
+    }
+    for (int u = lane; u < units; u += 32) {
+        const int s0 = r * run + 1;
+        const int s1 = min(s0 + run - 1, a < half ? half : half - 1);
         uint32_t ca[W];
-        load_col<W>(cols + a * W, ca);
-        const int smax = a < half ? half : half - 1;
-        int b = a;
-        for (int s = 1; s <= smax; ++s) {
-            b = (b + 1 == m) ? 0 : b + 1;
+        load_col_any<W>(cols, a, mc, ca);
+#pragma unroll 4
+        for (int b = a + s0; b <= a + s1; ++b) {
             uint32_t cb[W];
-            load_col<W>(cols + b * W, cb);
-            int d = 0;
-#pragma unroll
-            for (int w = 0; w < W; ++w)
-                d += __popc(ca[w] ^ cb[w]);
-            acc += fit_term<KIND>(m - 2 * d);
+            load_col_any<W>(cols, b, mc, cb);
+            acc += fit_term<KIND>(m - 2 * xor_popc<W>(ca, cb));
+        }
+        a += 32;
+        while (a >= m) {
+            a -= m;
+            ++r;
         }
     }
     return fit_finish<KIND>(warp_sum(acc));

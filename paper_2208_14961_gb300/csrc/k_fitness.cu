@@ -58,16 +58,16 @@ __global__ void __launch_bounds__(256) k_fit_bits_warp(const uint32_t *__restric
 {
     extern __shared__ uint32_t s_cols[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    uint32_t *cols = s_cols + (size_t)wib * m * W;
+    uint32_t *cols = s_cols + (size_t)wib * col_set_words(m, W);
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int words = m * W;
+    const int words = m * W, nch = warp_gram_chunks(m);
     for (int64_t q = first + gw; q < first + count; q += nw) {
         const uint32_t *src = pop + (size_t)q * words;
         for (int e = lane; e < words; e += 32)
-            cols[e] = __ldg(src + e);
+            store_col_word<W>(cols, e / W, e % W, m, __ldg(src + e));
         __syncwarp();
-        const uint32_t f = warp_fitness_cols<W, KIND>(cols, m, lane);
+        const uint32_t f = warp_fitness_cols<W, KIND>(cols, m, lane, nch);
         if (lane == 0)
             fit[q] = f;
         __syncwarp();
@@ -77,8 +77,10 @@ __global__ void __launch_bounds__(256) k_fit_bits_warp(const uint32_t *__restric
 // ---------------------------------------------------------------------------
 // POPC on int8 storage: sign bits -> column words by ballot
 // ---------------------------------------------------------------------------
-// Builds the W-word bit columns of an int8 row-major matrix in `cols`.
-__device__ __forceinline__ void int8_to_cols(const int8_t *Q, int m, int W, uint32_t *cols, int lane)
+// Builds the W-word bit columns of an int8 row-major matrix in `cols`
+// (column-set layout of col_word_index).
+template <int W>
+__device__ __forceinline__ void int8_to_cols(const int8_t *Q, int m, uint32_t *cols, int lane)
 {
     for (int rg = 0; rg < W; ++rg) {
         const int r = rg * 32 + lane;
@@ -90,7 +92,7 @@ __device__ __forceinline__ void int8_to_cols(const int8_t *Q, int m, int W, uint
                 const uint32_t bal = __ballot_sync(0xFFFFFFFFu, (x >> (8 * k + 7)) & 1u);
                 const int j = 4 * cw + k;
                 if (lane == (j & 31))
-                    cols[j * W + rg] = bal;
+                    store_col_word<W>(cols, j, rg, m, bal);
             }
         }
     }
@@ -102,13 +104,14 @@ __global__ void __launch_bounds__(256) k_fit_int8_popc(const int8_t *__restrict_
 {
     extern __shared__ uint32_t s_cols[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    uint32_t *cols = s_cols + (size_t)wib * m * W;
+    uint32_t *cols = s_cols + (size_t)wib * col_set_words(m, W);
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int nch = warp_gram_chunks(m);
     for (int64_t q = first + gw; q < first + count; q += nw) {
-        int8_to_cols(pop + (size_t)q * m * m, m, W, cols, lane);
+        int8_to_cols<W>(pop + (size_t)q * m * m, m, cols, lane);
         __syncwarp();
-        const uint32_t f = warp_fitness_cols<W, KIND>(cols, m, lane);
+        const uint32_t f = warp_fitness_cols<W, KIND>(cols, m, lane, nch);
         if (lane == 0)
             fit[q] = f;
         __syncwarp();
@@ -444,7 +447,7 @@ static cudaError_t fitness_kind(const void *pop, int storage, int m, int64_t fir
     }
     if (path == 5) {
         const int wpb = 8;
-        const size_t smem = (size_t)wpb * m * W * 4;  // at most 64 KiB (m = 256)
+        const size_t smem = (size_t)wpb * col_set_words(m, W) * 4;  // at most 64 KiB (m = 256)
         const int grid = grid_for_warps(count, wpb);
         switch (W) {
 #define HADGA_FW(WW)                                                                                        \

@@ -441,184 +441,193 @@ __device__ __forceinline__ void pair_thread(const FusedPop &p, const PopSel &S, 
 // operators of Sec. 3.4 and 3.5).
 //
 // Each individual keeps H = G / 2 (int8) in 8 x 8 tiles of the upper
-// triangle (common.cuh).  A word holds the four entries (i, 4q .. 4q + 3).
-// For an offspring cut at c with flipped columns M (the columns where a
-// pair flip changed signs), a valid word is "changed" when i is in M, its
-// quad holds a column of M, or it is a cross word (i < c, q >= c / 4);
-// every other word lies in G[:c, :c] (copied from the parent giving the
-// first c columns, Gt) or in G[c:, c:] (from the other parent, Gb): a column
-// exchange keeps those blocks, and a pair flip in column cc changes only
-// row and column cc.
-//  Phase 1: every lane copies 16-byte groups (two rows of a tile) from Gt
-//           or Gb, writing 0 for changed words;
-//  Phase 2: the changed words are recomputed by popcount of the final
-//           columns `bo` (cross words c (m/4 - c/4), plus O(m) words per
-//           flipped column) and stored over the zeros.
-// The fitness terms of every stored word come from SIMD byte arithmetic
-// (dp4a), each word counted once.
+// triangle (common.cuh); a tile row (i, J) is the 8 bytes H[i][8J .. 8J+7].
+// The offspring O takes columns [0, c) from parent Pt and [c, m) from Pb,
+// then pair flips change the columns of the set M.  A column exchange keeps
+// H[:c, :c] of Pt and H[c:, c:] of Pb, and a pair flip in column cc changes
+// only row and column cc, so:
+//  Phase 1: the tiles wholly inside H[:c, :c] (tile columns J < c/8) are
+//           copied from Pt, the tiles wholly inside H[c:, c:] (tile rows
+//           8I >= c, one contiguous run) from Pb, through a per-warp ring
+//           of 16-byte cp.async copies (four in flight per lane, no
+//           registers held); the tile rows i >= c of the tile row cut by c
+//           are copied from Pb with 8-byte loads;
+//  Phase 2: the remaining tile rows (i < c, 8J + 8 > c) hold the c (m - c)
+//           cross entries: computed by popcount from the final columns `bo`,
+//           their bytes j < c taken from Pt; work items (i, J) enumerated
+//           row-fastest so every lane carries the same number of dot
+//           products and the 8 columns of a tile column are broadcast reads;
+//  Phase 3: entries of rows and columns of M outside the cross block still
+//           hold the parents' values: recomputed from `bo` and stored byte
+//           by byte, and the fitness sum corrected by term(new) - term(old),
+//           old from the parents' columns.
+// The fitness terms of every stored entry come from SIMD byte arithmetic
+// (dp4a).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t mut_bit(const uint32_t (&mut)[4], int i) { return (mut[i >> 5] >> (i & 31)) & 1u; }
-
-// 4-bit mask of the flipped columns among 4q .. 4q + 3.
-__device__ __forceinline__ uint32_t mut_quad(const uint32_t (&mut)[4], int q)
+__device__ __forceinline__ uint32_t mut_word(const uint32_t (&mut)[4], int w)
 {
-    return (mut[q >> 3] >> ((q & 7) * 4)) & 0xFu;
+    return w == 0 ? mut[0] : w == 1 ? mut[1] : w == 2 ? mut[2] : mut[3];
 }
 
-// Word index of (row i, quad q) in the tiled layout (tile-row start S(I)).
-__device__ __forceinline__ uint32_t gram_word_index(int i, int q, int nb)
+__device__ __forceinline__ uint32_t mut_bit(const uint32_t (&mut)[4], int i)
 {
-    const int I = i >> 3, J = q >> 1;
-    return (uint32_t)((I * nb - (I * (I - 1)) / 2 + (J - I)) * 16 + (i & 7) * 2 + (q & 1));
+    return (mut_word(mut, i >> 5) >> (i & 31)) & 1u;
 }
 
-// The four half-Gram entries (i, 4q + k) from the bit columns (0 where
-// 4q + k <= i or >= m).
-template <int W>
-__device__ __forceinline__ uint32_t quad_word(const uint32_t *bo, int i, int q, int m)
+// Index of tile row (i, J) in 8-byte units: tile t(I, J) holds units 8t .. 8t+7.
+__device__ __forceinline__ uint32_t tile_row_unit(int i, int J, int nb)
 {
-    uint32_t ci[W];
-    load_col<W>(bo + i * W, ci);
-    uint32_t x = 0u;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int j = 4 * q + k;
-        if (j > i && j < m) {
-            uint32_t cj[W];
-            load_col<W>(bo + j * W, cj);
-            int d = 0;
-#pragma unroll
-            for (int w = 0; w < W; ++w)
-                d += __popc(ci[w] ^ cj[w]);
-            x |= ((uint32_t)((m >> 1) - d) & 0xFFu) << (8 * k);
-        }
-    }
-    return x;
+    const int I = i >> 3;
+    return (uint32_t)((I * nb - (I * (I - 1)) / 2 + (J - I)) * 8 + (i & 7));
 }
 
-// Source of word (i, q) in phase 1: 0 = Gt, 1 = Gb, 2 = zero (changed or
-// without entries).
-__device__ __forceinline__ int word_source(int i, int q, int m, int c, int qc, const uint32_t (&mut)[4])
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
 {
-    if (i >= m || 4 * q >= m || 4 * q + 3 <= i)
-        return 2;
-    if (mut_bit(mut, i) || mut_quad(mut, q) || (i < c && q >= qc))
-        return 2;
-    return i >= c ? 1 : 0;
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
 }
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+constexpr int kIncStage = 4;  // 16-byte copies in flight per lane in phase 1
+// shared words of the copy rings of all warps of a block
+constexpr uint32_t kIncStageWords = (kFusedThreads / 32) * 32 * kIncStage * 4;
 
 template <int W, int KIND>
-__device__ uint32_t offspring_incremental(const FusedPop &p, const uint32_t *bo, const uint32_t (&mut)[4], int c,
-                                          uint32_t gt, uint32_t gbm, uint32_t go, int lane)
+__device__ uint32_t offspring_incremental(const FusedPop &p, const uint32_t *bo, const uint32_t *bt,
+                                          const uint32_t *bb, const uint32_t (&mut)[4], int c, uint32_t gt,
+                                          uint32_t gbm, uint32_t go, uint4 *stage, int lane)
 {
-    const int m = p.m, nb = gram_tiles_nb(m), nt = nb * (nb + 1) / 2, Q = m >> 2, qc = c >> 2;
-    const uint4 *Gt4 = reinterpret_cast<const uint4 *>(p.gram + (size_t)gt * p.dpad);
-    const uint4 *Gb4 = reinterpret_cast<const uint4 *>(p.gram + (size_t)gbm * p.dpad);
-    const uint32_t *Gt = reinterpret_cast<const uint32_t *>(Gt4), *Gb = reinterpret_cast<const uint32_t *>(Gb4);
-    uint32_t *Go = reinterpret_cast<uint32_t *>(p.gram + (size_t)go * p.dpad);
-    uint4 *Go4 = reinterpret_cast<uint4 *>(Go);
+    const int m = p.m, nb = gram_tiles_nb(m), nt = nb * (nb + 1) / 2, hm = m >> 1;
+    const int8_t *gt8 = p.gram + (size_t)gt * p.dpad, *gb8 = p.gram + (size_t)gbm * p.dpad;
+    const uint2 *Gt = reinterpret_cast<const uint2 *>(gt8), *Gb = reinterpret_cast<const uint2 *>(gb8);
+    uint2 *Go = reinterpret_cast<uint2 *>(p.gram + (size_t)go * p.dpad);
     uint32_t acc = 0;
 
-    // ---- phase 1: groups g = 4 t + rp (tile t, row pair rp); a lane keeps
-    // its rp and walks tiles t = lane / 4 + 8 s
-    {
-        const int rp = lane & 3;
-        int I, J;
-        tile_coords(min(lane >> 2, nt - 1), nb, I, J);
-        constexpr int U = 4;
-        for (int t0 = lane >> 2; t0 < nt; t0 += 8 * U) {
-            uint4 v[U];
-            int src[U][4];
-            int tI[U], tJ[U];
+    // ---- phase 1: whole tiles of H[:c, :c] (tile columns J < J0) and of
+    // H[c:, c:] (tiles t >= tBR); group e: 16 bytes 16e' of tile t
+    const int J0 = c >> 3, I1 = (c + 7) >> 3;
+    const int nTL = J0 * (J0 + 1) / 2, tBR = I1 * nb - (I1 * (I1 - 1)) / 2;
+    const int nG = 4 * (nTL + (nt - tBR));
+    for (int base = 0; base < nG; base += 32 * kIncStage) {
+        uint32_t unit[kIncStage];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int t = t0 + 8 * u;
-                tI[u] = I;
-                tJ[u] = J;
-                v[u] = make_uint4(0u, 0u, 0u, 0u);
-                if (t < nt) {
-                    const int i0 = 8 * I + 2 * rp;
-                    src[u][0] = word_source(i0, 2 * J, m, c, qc, mut);
-                    src[u][1] = word_source(i0, 2 * J + 1, m, c, qc, mut);
-                    src[u][2] = word_source(i0 + 1, 2 * J, m, c, qc, mut);
-                    src[u][3] = word_source(i0 + 1, 2 * J + 1, m, c, qc, mut);
-                    const size_t g = (size_t)t * 4 + rp;
-                    const int s0 = src[u][0];
-                    if (s0 != 2 && src[u][1] == s0 && src[u][2] == s0 && src[u][3] == s0) {
-                        v[u] = __ldcg((s0 ? Gb4 : Gt4) + g);
-                    } else {
-                        uint32_t x[4];
-#pragma unroll
-                        for (int k = 0; k < 4; ++k)
-                            x[k] = src[u][k] == 2 ? 0u : __ldcg((src[u][k] ? Gb : Gt) + g * 4 + k);
-                        v[u] = make_uint4(x[0], x[1], x[2], x[3]);
-                    }
-                    // advance 8 tiles along the tile rows
-                    J += 8;
-                    while (J >= nb && I < nb - 1) {
-                        J = J - nb + I + 1;
-                        ++I;
-                    }
+        for (int u = 0; u < kIncStage; ++u) {
+            const int e = base + 32 * u + lane;
+            unit[u] = 0xFFFFFFFFu;
+            if (e < nG) {
+                const int8_t *src;
+                if (e < 4 * nTL) {
+                    int I, J;
+                    tile_coords(e >> 2, J0, I, J);  // TL tiles form the triangle of side J0
+                    unit[u] = (uint32_t)(((e >> 2) + I * (nb - J0)) * 4 + (e & 3));
+                    src = gt8;
+                } else {
+                    unit[u] = (uint32_t)(tBR * 4 + (e - 4 * nTL));
+                    src = gb8;
                 }
+                cp_async16(stage + u * 32 + lane, src + (size_t)unit[u] * 16u);
             }
+        }
+        cp_async_wait_all();
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int t = t0 + 8 * u;
-                if (t < nt) {
-                    __stcg(Go4 + (size_t)t * 4 + rp, v[u]);
-                    acc += (uint32_t)(word_terms<KIND>(v[u].x) + word_terms<KIND>(v[u].y) +
-                                      word_terms<KIND>(v[u].z) + word_terms<KIND>(v[u].w));
-                }
+        for (int u = 0; u < kIncStage; ++u) {
+            if (unit[u] != 0xFFFFFFFFu) {
+                const uint4 v = stage[u * 32 + lane];
+                __stcg(reinterpret_cast<uint4 *>(Go) + unit[u], v);
+                acc += (uint32_t)(word_terms<KIND>(v.x) + word_terms<KIND>(v.y) + word_terms<KIND>(v.z) +
+                                  word_terms<KIND>(v.w));
             }
-            (void)tI;
-            (void)tJ;
         }
     }
-    __syncwarp();
+    // tile rows i >= c of the tile row I0 = c / 8 cut by c (from Pb)
+    if (c & 7) {
+        const int I0 = c >> 3, r0 = c & 7, nr = 8 - r0, tot = nr * (nb - I0);
+        for (int e = lane; e < tot; e += 32) {
+            const int J = I0 + e / nr, i = 8 * I0 + r0 + e % nr;
+            const uint32_t un = tile_row_unit(i, J, nb);
+            const uint2 v = __ldcg(Gb + un);
+            __stcg(Go + un, v);
+            acc += (uint32_t)(word_terms<KIND>(v.x) + word_terms<KIND>(v.y));
+        }
+    }
 
-    // ---- phase 2a: cross words (i < c, q >= qc), flattened e = i (Q - qc) + (q - qc)
+    // ---- phase 2: tile rows (i, J), i < c, J >= J0; item e = (J - J0) c + i
     {
-        const int nq = Q - qc;
-        if (nq > 0) {
-            int i = lane / nq, q = qc + lane % nq;
-            const int total = c * nq;
-            for (int e = lane; e < total; e += 32) {
-                const uint32_t x = quad_word<W>(bo, i, q, m);
-                __stcg(Go + gram_word_index(i, q, nb), x);
-                acc += (uint32_t)word_terms<KIND>(x);
-                q += 32;
-                while (q >= Q) {
-                    q -= nq;
-                    ++i;
+        const int total = c * (nb - J0);
+        for (int e = lane; e < total; e += 32) {
+            const int jq = e / c, i = e - jq * c, J = J0 + jq, j0 = 8 * J;
+            const uint32_t un = tile_row_unit(i, J, nb);
+            uint2 x = j0 < c ? __ldcg(Gt + un) : make_uint2(0u, 0u);
+            uint32_t ci[W];
+            load_col<W>(bo + i * W, ci);
+            // one 4-byte word at a time (keeps the column loads of a word in flight)
+#pragma unroll 1
+            for (int hw = 0; hw < 2; ++hw) {
+                uint32_t xw = hw ? x.y : x.x;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int j = j0 + 4 * hw + k;
+                    if (j >= c && j < m) {
+                        uint32_t cj[W];
+                        load_col<W>(bo + j * W, cj);
+                        const uint32_t h = (uint32_t)(hm - xor_popc<W>(ci, cj)) & 0xFFu;
+                        xw = (xw & ~(0xFFu << (8 * k))) | (h << (8 * k));
+                    }
                 }
+                if (hw)
+                    x.y = xw;
+                else
+                    x.x = xw;
             }
+            __stcg(Go + un, x);
+            acc += (uint32_t)(word_terms<KIND>(x.x) + word_terms<KIND>(x.y));
         }
     }
-    // ---- phase 2b: rows and quads of the flipped columns, outside the cross words
-    for (int w = 0; w < 4; ++w) {
-        uint32_t bits = mut[w];
-        while (bits) {
-            const int cc = 32 * w + __ffs(bits) - 1;
-            bits &= bits - 1u;
-            // row cc: quads with an entry right of the diagonal
-            for (int q = (cc >> 2) + lane; q < Q; q += 32) {
-                if (cc < c && q >= qc)
-                    continue;  // a cross word
-                const uint32_t x = quad_word<W>(bo, cc, q, m);
-                __stcg(Go + gram_word_index(cc, q, nb), x);
-                acc += (uint32_t)word_terms<KIND>(x);
-            }
-            // quad of column cc, rows above it; done once per quad (by its
-            // lowest flipped column), rows of M belong to their row pass
-            const int qq = cc >> 2;
-            if ((mut_quad(mut, qq) & ((1u << (cc & 3)) - 1u)) != 0u)
-                continue;
-            for (int i = lane; i < 4 * qq + 3 && i < m; i += 32) {
-                if (mut_bit(mut, i) || (i < c && qq >= qc))
-                    continue;
-                const uint32_t x = quad_word<W>(bo, i, qq, m);
-                __stcg(Go + gram_word_index(i, qq, nb), x);
-                acc += (uint32_t)word_terms<KIND>(x);
+
+    // ---- phase 3: rows and columns of the flipped columns, outside the
+    // cross block (which phase 2 computed from the final columns)
+    if ((mut[0] | mut[1] | mut[2] | mut[3]) != 0u) {
+        __syncwarp();
+        int8_t *Gob = reinterpret_cast<int8_t *>(Go);
+        // column x before the mutation: the parent column at its place
+        auto old_col = [&](int x) { return (x < c ? bt : bb) + x * W; };
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            uint32_t bits = mut[w];
+            while (bits) {
+                const int cc = 32 * w + __ffs(bits) - 1;
+                bits &= bits - 1u;
+                uint32_t cn[W], co[W];
+                load_col<W>(bo + cc * W, cn);
+                load_col<W>(old_col(cc), co);
+                // column cc: entries (i, cc), i < cc (rows of M included)
+                for (int i = lane; i < cc; i += 32) {
+                    if (i < c && cc >= c)
+                        continue;  // a cross entry
+                    uint32_t xn[W], xo[W];
+                    load_col<W>(bo + i * W, xn);
+                    load_col<W>(mut_bit(mut, i) ? old_col(i) : bo + i * W, xo);
+                    const uint32_t hn = (uint32_t)(hm - xor_popc<W>(xn, cn)) & 0xFFu;
+                    const uint32_t ho = (uint32_t)(hm - xor_popc<W>(xo, co)) & 0xFFu;
+                    __stcg(Gob + (size_t)tile_row_unit(i, cc >> 3, nb) * 8u + (cc & 7), (int8_t)hn);
+                    acc += (uint32_t)(word_terms<KIND>(hn) - word_terms<KIND>(ho));
+                }
+                // row cc: entries (cc, j), j > cc, j not in M (those are
+                // handled by column j's pass)
+                for (int j = cc + 1 + lane; j < m; j += 32) {
+                    if (mut_bit(mut, j) || (cc < c && j >= c))
+                        continue;
+                    uint32_t xj[W];
+                    load_col<W>(bo + j * W, xj);
+                    const uint32_t hn = (uint32_t)(hm - xor_popc<W>(cn, xj)) & 0xFFu;
+                    const uint32_t ho = (uint32_t)(hm - xor_popc<W>(co, xj)) & 0xFFu;
+                    __stcg(Gob + (size_t)tile_row_unit(cc, j >> 3, nb) * 8u + (j & 7), (int8_t)hn);
+                    acc += (uint32_t)(word_terms<KIND>(hn) - word_terms<KIND>(ho));
+                }
             }
         }
     }
@@ -630,8 +639,8 @@ __device__ uint32_t offspring_incremental(const FusedPop &p, const uint32_t *bo,
 // ---------------------------------------------------------------------------
 template <int W, bool INC>
 __device__ void offspring_warp(const FusedPop &p, PopSel &S, int src, uint32_t gen, uint32_t tch, uint32_t k,
-                               int half, const Surv &sv, uint32_t *err, uint32_t *buf, uint32_t *hist_next,
-                               uint32_t *bhist)
+                               int half, const Surv &sv, uint32_t *err, uint32_t *buf, uint4 *stage,
+                               uint32_t *hist_next, uint32_t *bhist)
 {
     const int lane = threadIdx.x & 31;
     const int m = p.m;
@@ -729,18 +738,23 @@ __device__ void offspring_warp(const FusedPop &p, PopSel &S, int src, uint32_t g
             for (int w = 0; w < 4; ++w)
                 mut[w] = __shfl_sync(FULL, mut[w], 0);
             const uint32_t gt = half ? gb2 : gb1, gbm = half ? gb1 : gb2;
+            const uint32_t *bt = half ? b2 : b1, *bb = half ? b1 : b2;  // parents giving [0, c) and [c, m)
             switch (p.kind) {
-            case FIT_SQ: f = offspring_incremental<W, FIT_SQ>(p, bo, mut, c, gt, gbm, go, lane); break;
-            case FIT_ABS: f = offspring_incremental<W, FIT_ABS>(p, bo, mut, c, gt, gbm, go, lane); break;
-            default: f = offspring_incremental<W, FIT_NNZ>(p, bo, mut, c, gt, gbm, go, lane); break;
+            case FIT_SQ: f = offspring_incremental<W, FIT_SQ>(p, bo, bt, bb, mut, c, gt, gbm, go, stage, lane); break;
+            case FIT_ABS: f = offspring_incremental<W, FIT_ABS>(p, bo, bt, bb, mut, c, gt, gbm, go, stage, lane); break;
+            default: f = offspring_incremental<W, FIT_NNZ>(p, bo, bt, bb, mut, c, gt, gbm, go, stage, lane); break;
             }
         }
     }
     if (!inc) {
+        // the warp-level Gram reads copies of columns 0 .. m/2 - 2 after column m - 1
+        for (int e = lane; e < ((m >> 1) - 1) * W; e += 32)
+            bo[words + e] = bo[e];
+        __syncwarp();
         switch (p.kind) {
-        case FIT_SQ: f = warp_fitness_cols<W, FIT_SQ>(bo, m, lane); break;
-        case FIT_ABS: f = warp_fitness_cols<W, FIT_ABS>(bo, m, lane); break;
-        default: f = warp_fitness_cols<W, FIT_NNZ>(bo, m, lane); break;
+        case FIT_SQ: f = warp_fitness_cols<W, FIT_SQ>(bo, m, lane, p.nch); break;
+        case FIT_ABS: f = warp_fitness_cols<W, FIT_ABS>(bo, m, lane, p.nch); break;
+        default: f = warp_fitness_cols<W, FIT_NNZ>(bo, m, lane, p.nch); break;
         }
     }
     const uint32_t slot = 2u * N + k + oh;
@@ -831,6 +845,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
     __shared__ unsigned long long s_tmp64[32];
     __shared__ uint32_t hoff[kMaxPops];
     __shared__ int s_flag;
+    __shared__ uint32_t s_next;  // next warp item of the block (phase B)
 
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
     const int npop = prm.npop;
@@ -840,12 +855,13 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
     // different SMs
     const uint32_t gwarp = (uint32_t)wib * nblocks + blockIdx.x, gwarps = gthreads >> 5;
     const uint32_t TT = prm.total_tiles;
-    // shared layout: [tile masks and their prefix (phase B) | staged
-    // histograms (phase A)] [warp buffers]
-    const uint32_t r1 = max(4u * TT, 2u * kHistSmem);
+    // [tile masks and their prefix (phase B) | incremental copy ring (phase B)
+    //  | staged histograms (phase A, overlapping both)] [bhist] [warp buffers]
+    const uint32_t r1 = max(4u * TT + (INC ? kIncStageWords : 0u), 2u * kHistSmem);
     unsigned long long *tm = reinterpret_cast<unsigned long long *>(dyn);
     unsigned long long *ex = tm + TT;
     uint32_t *hcnt = dyn;
+    uint4 *stage = reinterpret_cast<uint4 *>(dyn + 4u * TT) + wib * 32 * kIncStage;
     uint32_t *bhist = dyn + r1;  // block-local histograms of the next generation
     uint32_t *wbuf = bhist + kHistSmem + wib * prm.warp_buf_words;
     const Surv sv{tm, ex};
@@ -1158,6 +1174,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
         }
         for (uint32_t e = tid; e < kHistSmem; e += blockDim.x)
             bhist[e] = 0u;
+        if (tid == 0)
+            s_next = 0u;
         __syncthreads();
         block_scan_chunks_u64(
             TT,
@@ -1223,8 +1241,19 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                 atomicMin(&S[i].bbest, key);
             }
         }
-        // 32 < m <= 128: a warp per offspring (items 2k + half)
-        for (uint32_t it = gwarp; it < prm.warp_items; it += gwarps) {
+        // 32 < m <= 128: a warp per offspring (items 2k + half).  The block
+        // owns items blockIdx.x + q * nblocks, q = 0, 1, ...; its warps take
+        // the next q from a shared counter, so offspring of uneven cost (the
+        // incremental path's cross block grows with c (m - c)) even out
+        // within the block.
+        for (;;) {
+            uint32_t q = 0;
+            if (lane == 0)
+                q = atomicAdd(&s_next, 1u);
+            q = __shfl_sync(FULL, q, 0);
+            const uint32_t it = blockIdx.x + q * nblocks;
+            if (it >= prm.warp_items)
+                break;
             int i = -1;
             for (int j = 0; j < npop; ++j)
                 if (prm.p[j].m > 32 && it >= prm.p[j].work_base &&
@@ -1238,9 +1267,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             uint32_t *hn = hist_of(p, par ^ 1);
             const uint32_t gen = S[i].gen0 + 1u + (uint32_t)t;
             switch (p.W) {
-            case 2: offspring_warp<2, INC>(p, S[i], src, gen, (uint32_t)t, k, half, sv, err, wbuf, hn, bhist); break;
-            case 3: offspring_warp<3, INC>(p, S[i], src, gen, (uint32_t)t, k, half, sv, err, wbuf, hn, bhist); break;
-            case 4: offspring_warp<4, INC>(p, S[i], src, gen, (uint32_t)t, k, half, sv, err, wbuf, hn, bhist); break;
+            case 2: offspring_warp<2, INC>(p, S[i], src, gen, (uint32_t)t, k, half, sv, err, wbuf, stage, hn, bhist); break;
+            case 3: offspring_warp<3, INC>(p, S[i], src, gen, (uint32_t)t, k, half, sv, err, wbuf, stage, hn, bhist); break;
+            case 4: offspring_warp<4, INC>(p, S[i], src, gen, (uint32_t)t, k, half, sv, err, wbuf, stage, hn, bhist); break;
             default: break;
             }
         }
@@ -1289,7 +1318,10 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
 
 size_t fused_smem_bytes(const FusedParams &p)
 {
-    const size_t r1 = std::max((size_t)4 * p.total_tiles, (size_t)2 * kHistSmem);
+    bool inc = false;
+    for (int i = 0; i < p.npop; ++i)
+        inc = inc || p.p[i].gram != nullptr;
+    const size_t r1 = std::max((size_t)4 * p.total_tiles + (inc ? kIncStageWords : 0u), (size_t)2 * kHistSmem);
     return (r1 + kHistSmem + (size_t)(kFusedThreads / 32) * p.warp_buf_words) * 4u;
 }
 

@@ -124,6 +124,7 @@ struct FusedPop {
     uint32_t *gidx[2];         // incremental mode: slot -> Gram buffer, ping-pong with pop
     int32_t dpad;              // bytes per Gram buffer (64 per tile)
     int32_t m, W, NC, NR, kind, traj_cap;
+    int32_t nch;                 // chunks per column of the warp-level Gram (warp_gram_chunks)
     int64_t N;
     uint32_t seed, pop_id;
     uint32_t tile_base, ntiles;  // tiles of 32 slots in the joint tile space

@@ -45,6 +45,23 @@ def test_fitness_paths_match_oracle(m, path, storage):
         assert np.array_equal(fit_u64(fit), oracle.fitness(host, kind)), (m, path, storage, kind)
 
 
+@pytest.mark.parametrize("m", [68, 96, 132, 200, 252])
+@pytest.mark.parametrize("storage", [1, 0])
+def test_popc_word_counts_match_oracle(m, storage):
+    """Column widths W = 3, 5, 7 and 8 words: the carry-save population
+    count takes the tree's partial levels there."""
+    h = need_gpu()
+    P = 9
+    host = np.concatenate([random_pm1(P - 3, m, seed=m), balanced_pm1(3, m, seed=m + 1)])
+    src = to_device_int8(host)
+    pop = h.empty_population(storage, m, P)
+    h.ga_convert(src, 0, pop, storage, m, P)
+    for kind in KINDS:
+        fit = torch.zeros(P, dtype=torch.int32, device="cuda")
+        h.ga_fitness_batch(pop, storage, m, P, kind, 5, fit)
+        assert np.array_equal(fit_u64(fit), oracle.fitness(host, kind)), (m, storage, kind)
+
+
 @pytest.mark.parametrize("path,storage", [(5, 1), (5, 0), (1, 0), (2, 0)])
 def test_known_hadamard_matrices_score_zero(path, storage):
     h = need_gpu()
