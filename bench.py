@@ -322,6 +322,69 @@ def mixed_workload(args):
     print(json.dumps(line), flush=True)
 
 
+# Sec. 4.2, Table 2 of the paper: seconds for 10^4 generations at P = 40,000,
+# NC = 4, NR = 2 on an RTX 3080 (CuPy, int8 matmul), fitness F1 and F2.
+PAPER_TABLE_SECONDS = {20: (60.50, 59.38), 40: (103.15, 99.84), 60: (176.28, 170.20),
+                       80: (275.92, 256.59), 100: (416.68, 381.38)}
+
+
+def table3_workload(args):
+    """The paper's fitness-comparison workload (Sec. 4.2): m in {20, 40, 60,
+    80, 100}, P = 40,000 balanced +-1 matrices (seed 5), NC = 4 columns and
+    NR = 2 row pairs per mutation, fitness F1 and F2.  Each (m, fitness) runs
+    `--t3-gens` generations of the fused path (bit storage) in ga_step calls
+    of 50 after a warm-up call; the first 50 generations are also run by the
+    one-kernel-per-operator path and must give the same population and
+    fitness.  One JSON line per (m, fitness) with generations/s, evaluations/s
+    in the paper's convention (all P per generation) and the paper's RTX 3080
+    rate for the same m and fitness (context: other hardware)."""
+    import numpy as np
+    import torch
+
+    from paper_2208_14961_gb300.build import build
+    build()
+    from paper_2208_14961_gb300 import hadga as h
+
+    N, seed, chunk = 10_000, 5, 50
+    gens = max(chunk, args.t3_gens // chunk * chunk)
+    stream = torch.cuda.Stream()
+    for m in [int(x) for x in args.t3_ms.split(",")]:
+        for kind, kname in ((h.FIT_ABS, "F1"), (h.FIT_NNZ, "F2")):
+            def fresh():
+                p = h.Population(m, N, seed=seed, NC=4, NR=2, fitness=kind, storage=h.STORE_BITS,
+                                 traj_cap=chunk, stream=stream)
+                p.init_population()
+                p.fitness()
+                return p
+            a, b = fresh(), fresh()
+            a.step(chunk)
+            b.step_plain(chunk)
+            a.sync()
+            b.sync()
+            exact = bool(np.array_equal(a.as_int8(), b.as_int8())) and bool(
+                np.array_equal(a.fitness_host(), b.fitness_host()))
+            b.close()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(gens // chunk):
+                a.step(chunk)
+            e1.record(stream)
+            e1.synchronize()
+            sec = e0.elapsed_time(e1) / 1e3
+            best = a.best()
+            a.close()
+            gps = gens / sec
+            paper_s = PAPER_TABLE_SECONDS.get(m, (None, None))[0 if kind == h.FIT_ABS else 1]
+            paper_gps = 1e4 / paper_s if paper_s else None
+            line = {"workload": "paper Sec. 4.2 fitness comparison", "m": m, "P": 4 * N, "NC": 4, "NR": 2,
+                    "fitness": kname, "generations": gens, "ms": sec * 1e3, "generations_per_s": gps,
+                    "evals_per_s_paper_convention": gps * 4 * N, "fused_equals_plain_50": exact,
+                    "best_fitness": int(best[1]),
+                    "paper_rtx3080_generations_per_s": paper_gps,
+                    "over_paper": (gps / paper_gps) if paper_gps else None}
+            print(json.dumps(line), flush=True)
+
+
 def incremental_workload(args):
     """Incremental Gram-delta fitness (a7) on m=100, P=20,000 bit-packed
     balanced matrices (seed 4, F_sq, NC = NR = 1) for `--inc-gens`
@@ -414,6 +477,9 @@ def main():
     ap.add_argument("--mixed-check", action="store_true")
     ap.add_argument("--incremental", action="store_true", help="incremental Gram-delta workload (m=100)")
     ap.add_argument("--inc-gens", type=int, default=10000)
+    ap.add_argument("--table3", action="store_true", help="the paper's fitness-comparison workload (Sec. 4.2)")
+    ap.add_argument("--t3-ms", default="20,40,60,80,100")
+    ap.add_argument("--t3-gens", type=int, default=1000)
     args = ap.parse_args()
     if args.gram_sweep:
         gram_sweep(args)
@@ -423,6 +489,9 @@ def main():
         return
     if args.incremental:
         incremental_workload(args)
+        return
+    if args.table3:
+        table3_workload(args)
         return
     args.warmup = max(args.warmup, 3)
 

@@ -443,7 +443,8 @@ static ga_status fused_run(ga_ctx *const *ctxs, int n, int32_t generations, int 
         } else {
             p.work_base = wpairs;
             wpairs += (uint32_t)(2 * c->N);  // one warp item per offspring
-            max_words = std::max(max_words, 2 * c->m * c->W + col_set_words(c->m, c->W));
+            // 16-byte aligned per warp (cp.async and vector copies of the parents)
+            max_words = std::max(max_words, (2 * c->m * c->W + col_set_words(c->m, c->W) + 3) & ~3);
         }
         if (int8) {
             cudaError_t e = launch_convert(c->pop, GA_STORE_INT8, c->bits[0], GA_STORE_BITS, c->m, c->P, c0->stream);
@@ -480,6 +481,7 @@ static ga_status fused_run(ga_ctx *const *ctxs, int n, int32_t generations, int 
     prm.bar = c0->fmisc;
     prm.done = (int32_t *)(c0->fmisc + 1);
     prm.err = c0->err;
+    fused_plan_ring(prm);
     const size_t smem = fused_smem_bytes(prm);
     int grid = 0;
     cudaError_t e = fused_grid(smem, &grid);

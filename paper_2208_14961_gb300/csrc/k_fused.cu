@@ -492,64 +492,147 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
-constexpr int kIncStage = 4;  // 16-byte copies in flight per lane in phase 1
-// shared words of the copy rings of all warps of a block
-constexpr uint32_t kIncStageWords = (kFusedThreads / 32) * 32 * kIncStage * 4;
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 
+// Waits until at most N of this thread's most recent cp.async groups are
+// pending (all older ones complete).
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Copies of one offspring cut at c, in 16-byte groups (16-byte units of a
+// Gram buffer):
+//  [0, nG)              phase 1: the H[:c, :c] tiles of Pt (4 nTL groups,
+//                       the triangle of side J0 = c / 8), then the H[c:, c:]
+//                       tiles of Pb (from tile tBR on);
+//  [nG, nG + n4g)       when 8 does not divide c: Pt's rows i < c of tile
+//                       column J0 (row pairs 2q, 2q + 1), read by phase 2;
+//  [.., total)          and Pb's rows i >= c of tile row I0 = c / 8 (row
+//                       pairs from r0 & ~1 on, g3 per tile), copied to O.
+struct IncCopyPlan {
+    int nTL, J0, nb, tBR, nG, n4g, n3g, g3, r0, total;
+    __host__ __device__ IncCopyPlan(int m, int c)
+    {
+        nb = gram_tiles_nb(m);
+        const int nt = nb * (nb + 1) / 2, I1 = (c + 7) >> 3;
+        J0 = c >> 3;
+        nTL = J0 * (J0 + 1) / 2;
+        tBR = I1 * nb - (I1 * (I1 - 1)) / 2;
+        nG = 4 * (nTL + (nt - tBR));
+        r0 = c & 7;
+        g3 = r0 ? 4 - (r0 >> 1) : 0;
+        n4g = r0 ? (c + 1) >> 1 : 0;
+        n3g = g3 * (nb - J0);
+        total = nG + n4g + n3g;
+    }
+    __device__ __forceinline__ uint32_t tile(int I, int J) const { return (uint32_t)(I * nb - (I * (I - 1)) / 2 + (J - I)); }
+    // unit of extra group x in [0, n4g + n3g) and whether it comes from Pt
+    __device__ __forceinline__ uint32_t extra_unit(int x, bool &from_pt) const
+    {
+        if (x < n4g) {
+            const int i = 2 * x;
+            from_pt = true;
+            return tile(i >> 3, J0) * 4u + (uint32_t)((i & 7) >> 1);
+        }
+        x -= n4g;
+        from_pt = false;
+        const int J = J0 + x / g3, q = (r0 >> 1) + x % g3;
+        return tile(J0, J) * 4u + (uint32_t)q;
+    }
+};
+
+// A lane's phase-1 groups e = e0, e0 + 32, ...: the H[:c, :c] tile (I, J) is
+// stepped through the triangle of side J0 (8 tiles per step), no root taken
+// per group.
+struct IncGroupIter {
+    int e, I, J;
+    __device__ __forceinline__ IncGroupIter(const IncCopyPlan &pl, int e0) : e(e0), I(0), J(0)
+    {
+        if (e0 < 4 * pl.nTL)
+            tile_coords(e0 >> 2, pl.J0, I, J);
+    }
+    __device__ __forceinline__ bool from_pt(const IncCopyPlan &pl) const { return e < 4 * pl.nTL; }
+    __device__ __forceinline__ uint32_t unit(const IncCopyPlan &pl) const
+    {
+        return from_pt(pl) ? pl.tile(I, J) * 4u + (uint32_t)(e & 3) : (uint32_t)(pl.tBR * 4 + (e - 4 * pl.nTL));
+    }
+    __device__ __forceinline__ void next(const IncCopyPlan &pl)
+    {
+        e += 32;
+        if (e < 4 * pl.nTL) {
+            J += 8;
+            while (J >= pl.J0 && I < pl.J0 - 1) {
+                J = J - pl.J0 + I + 1;
+                ++I;
+            }
+        }
+    }
+};
+
+// Issues the cp.async copies of phase-1 groups [base, base + ring) into the
+// warp's ring (slot e - base); each lane copies the groups e = lane mod 32.
+// With base 0 and the whole plan within the ring, the extra groups follow
+// (slots nG ..).
+__device__ __forceinline__ void inc_copy_issue(const IncCopyPlan &pl, const int8_t *gt8, const int8_t *gb8,
+                                               uint4 *ring, int ring_groups, int base, int lane)
+{
+    const int end = min(base + ring_groups, pl.nG);
+    for (IncGroupIter it(pl, base + lane); it.e < end; it.next(pl))
+        cp_async16(ring + (it.e - base), (it.from_pt(pl) ? gt8 : gb8) + (size_t)it.unit(pl) * 16u);
+    if (base == 0 && pl.total <= ring_groups) {
+        for (int x = lane; x < pl.n4g + pl.n3g; x += 32) {
+            bool pt;
+            const uint32_t u = pl.extra_unit(x, pt);
+            cp_async16(ring + pl.nG + x, (pt ? gt8 : gb8) + (size_t)u * 16u);
+        }
+    }
+}
+
+// The caller has issued the first ring-full of phase-1 copies
+// (inc_copy_issue with base 0) before the parent loads, crossover and
+// mutation, whose latency the copies overlap.
 template <int W, int KIND>
 __device__ uint32_t offspring_incremental(const FusedPop &p, const uint32_t *bo, const uint32_t *bt,
                                           const uint32_t *bb, const uint32_t (&mut)[4], int c, uint32_t gt,
-                                          uint32_t gbm, uint32_t go, uint4 *stage, int lane)
+                                          uint32_t gbm, uint32_t go, uint4 *ring, int ring_groups, int lane)
 {
-    const int m = p.m, nb = gram_tiles_nb(m), nt = nb * (nb + 1) / 2, hm = m >> 1;
+    const int m = p.m, nb = gram_tiles_nb(m), hm = m >> 1;
     const int8_t *gt8 = p.gram + (size_t)gt * p.dpad, *gb8 = p.gram + (size_t)gbm * p.dpad;
     const uint2 *Gt = reinterpret_cast<const uint2 *>(gt8), *Gb = reinterpret_cast<const uint2 *>(gb8);
     uint2 *Go = reinterpret_cast<uint2 *>(p.gram + (size_t)go * p.dpad);
     uint32_t acc = 0;
 
     // ---- phase 1: whole tiles of H[:c, :c] (tile columns J < J0) and of
-    // H[c:, c:] (tiles t >= tBR); group e: 16 bytes 16e' of tile t
-    const int J0 = c >> 3, I1 = (c + 7) >> 3;
-    const int nTL = J0 * (J0 + 1) / 2, tBR = I1 * nb - (I1 * (I1 - 1)) / 2;
-    const int nG = 4 * (nTL + (nt - tBR));
-    for (int base = 0; base < nG; base += 32 * kIncStage) {
-        uint32_t unit[kIncStage];
-#pragma unroll
-        for (int u = 0; u < kIncStage; ++u) {
-            const int e = base + 32 * u + lane;
-            unit[u] = 0xFFFFFFFFu;
-            if (e < nG) {
-                const int8_t *src;
-                if (e < 4 * nTL) {
-                    int I, J;
-                    tile_coords(e >> 2, J0, I, J);  // TL tiles form the triangle of side J0
-                    unit[u] = (uint32_t)(((e >> 2) + I * (nb - J0)) * 4 + (e & 3));
-                    src = gt8;
-                } else {
-                    unit[u] = (uint32_t)(tBR * 4 + (e - 4 * nTL));
-                    src = gb8;
-                }
-                cp_async16(stage + u * 32 + lane, src + (size_t)unit[u] * 16u);
-            }
-        }
+    // H[c:, c:] (tiles t >= tBR), one ring-full at a time
+    const IncCopyPlan pl(m, c);
+    const int J0 = pl.J0;
+    for (int base = 0; base < pl.nG; base += ring_groups) {
+        if (base > 0)
+            inc_copy_issue(pl, gt8, gb8, ring, ring_groups, base, lane);
         cp_async_wait_all();
-#pragma unroll
-        for (int u = 0; u < kIncStage; ++u) {
-            if (unit[u] != 0xFFFFFFFFu) {
-                const uint4 v = stage[u * 32 + lane];
-                __stcg(reinterpret_cast<uint4 *>(Go) + unit[u], v);
-                acc += (uint32_t)(word_terms<KIND>(v.x) + word_terms<KIND>(v.y) + word_terms<KIND>(v.z) +
-                                  word_terms<KIND>(v.w));
-            }
+        const int end = min(base + ring_groups, pl.nG);
+        for (IncGroupIter it(pl, base + lane); it.e < end; it.next(pl)) {
+            const uint4 v = ring[it.e - base];
+            __stcg(reinterpret_cast<uint4 *>(Go) + it.unit(pl), v);
+            acc += (uint32_t)(word_terms<KIND>(v.x) + word_terms<KIND>(v.y) + word_terms<KIND>(v.z) +
+                              word_terms<KIND>(v.w));
         }
+        if (base + ring_groups < pl.nG)
+            __syncwarp();  // the ring is refilled by other lanes' copies next round
     }
+    // the extra groups sit in the ring when the whole plan fit (8-byte rows)
+    const bool pre = pl.total <= ring_groups;
+    const uint2 *ring8 = reinterpret_cast<const uint2 *>(ring) + 2 * pl.nG;
     // tile rows i >= c of the tile row I0 = c / 8 cut by c (from Pb)
     if (c & 7) {
         const int I0 = c >> 3, r0 = c & 7, nr = 8 - r0, tot = nr * (nb - I0);
         for (int e = lane; e < tot; e += 32) {
             const int J = I0 + e / nr, i = 8 * I0 + r0 + e % nr;
             const uint32_t un = tile_row_unit(i, J, nb);
-            const uint2 v = __ldcg(Gb + un);
+            const uint2 v = pre ? ring8[2 * (pl.n4g + (J - J0) * pl.g3 + ((i & 7) >> 1) - (r0 >> 1)) + (i & 1)]
+                                : __ldcg(Gb + un);
             __stcg(Go + un, v);
             acc += (uint32_t)(word_terms<KIND>(v.x) + word_terms<KIND>(v.y));
         }
@@ -558,25 +641,27 @@ __device__ uint32_t offspring_incremental(const FusedPop &p, const uint32_t *bo,
     // ---- phase 2: tile rows (i, J), i < c, J >= J0; item e = (J - J0) c + i
     {
         const int total = c * (nb - J0);
+        int i = lane % c, J = J0 + lane / c;
         for (int e = lane; e < total; e += 32) {
-            const int jq = e / c, i = e - jq * c, J = J0 + jq, j0 = 8 * J;
+            const int j0 = 8 * J;
             const uint32_t un = tile_row_unit(i, J, nb);
-            uint2 x = j0 < c ? __ldcg(Gt + un) : make_uint2(0u, 0u);
+            uint2 x = j0 < c ? (pre ? ring8[i] : __ldcg(Gt + un)) : make_uint2(0u, 0u);
             uint32_t ci[W];
             load_col<W>(bo + i * W, ci);
-            // one 4-byte word at a time (keeps the column loads of a word in flight)
-#pragma unroll 1
+            // the eight dot products are computed unconditionally (column
+            // index clamped into the matrix) so their loads issue together;
+            // the bytes j < c or j >= m keep the parent's value
+#pragma unroll
             for (int hw = 0; hw < 2; ++hw) {
                 uint32_t xw = hw ? x.y : x.x;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int j = j0 + 4 * hw + k;
-                    if (j >= c && j < m) {
-                        uint32_t cj[W];
-                        load_col<W>(bo + j * W, cj);
-                        const uint32_t h = (uint32_t)(hm - xor_popc<W>(ci, cj)) & 0xFFu;
-                        xw = (xw & ~(0xFFu << (8 * k))) | (h << (8 * k));
-                    }
+                    uint32_t cj[W];
+                    load_col<W>(bo + min(j, m - 1) * W, cj);
+                    const uint32_t h = (uint32_t)(hm - xor_popc<W>(ci, cj)) & 0xFFu;
+                    const uint32_t keep = (j >= c && j < m) ? ~(0xFFu << (8 * k)) : 0xFFFFFFFFu;
+                    xw = (xw & keep) | (h << (8 * k) & ~keep);
                 }
                 if (hw)
                     x.y = xw;
@@ -585,6 +670,11 @@ __device__ uint32_t offspring_incremental(const FusedPop &p, const uint32_t *bo,
             }
             __stcg(Go + un, x);
             acc += (uint32_t)(word_terms<KIND>(x.x) + word_terms<KIND>(x.y));
+            i += 32;
+            while (i >= c) {
+                i -= c;
+                ++J;
+            }
         }
     }
 
@@ -639,8 +729,8 @@ __device__ uint32_t offspring_incremental(const FusedPop &p, const uint32_t *bo,
 // ---------------------------------------------------------------------------
 template <int W, bool INC>
 __device__ void offspring_warp(const FusedPop &p, PopSel &S, int src, uint32_t gen, uint32_t tch, uint32_t k,
-                               int half, const Surv &sv, uint32_t *err, uint32_t *buf, uint4 *stage,
-                               uint32_t *hist_next, uint32_t *bhist)
+                               int half, const Surv &sv, uint32_t *err, uint32_t *buf, uint4 *ring,
+                               int ring_groups, uint32_t *hist_next, uint32_t *bhist)
 {
     const int lane = threadIdx.x & 31;
     const int m = p.m;
@@ -650,16 +740,34 @@ __device__ void offspring_warp(const FusedPop &p, PopSel &S, int src, uint32_t g
     // lanes 0, 1: slots of the parents (survivors pi(k), pi(k + N)) and
     // their fitness; lane 2 (incremental mode): slot of non-survivor k + oh,
     // whose Gram buffer the offspring takes over
-    uint32_t look = 0, lf = 0;
+    uint32_t look = 0, lf = 0, lg = 0;
     if (lane < (inc ? 3 : 2)) {
-        if (lane < 2) {
+        if (lane < 2)
             look = survivor_of(__ldg(p.perm + (size_t)tch * 2u * N + k + (lane ? N : 0u)), p, S, sv, err);
-            lf = ldcg32(p.fit[src] + look);
-        } else {
+        else
             look = nonsurvivor_of(k + oh, p, S, sv, err);
-        }
+        // fitness and Gram index of the slot in one round trip
+        if (lane < 2)
+            lf = ldcg32(p.fit[src] + look);
+        if (inc)
+            lg = ldcg32(p.gidx[src] + look);
     }
     const uint32_t s1 = __shfl_sync(FULL, look, 0), s2 = __shfl_sync(FULL, look, 1);
+    uint32_t *b1 = buf, *b2 = buf + words, *bo = buf + 2 * words;
+    const uint32_t *sp = p.pop[src];
+    uint32_t *dp = p.pop[src ^ 1];
+    const uint32_t w4 = words >> 2;  // words is a multiple of 4
+    {
+        // both parents as 16-byte cp.async copies (one commit group, waited
+        // for below while the incremental Gram copies stay in flight)
+        const uint4 *pa = reinterpret_cast<const uint4 *>(sp) + (size_t)s1 * w4;
+        const uint4 *pb = reinterpret_cast<const uint4 *>(sp) + (size_t)s2 * w4;
+        for (uint32_t e = lane; e < w4; e += 32) {
+            cp_async16(reinterpret_cast<uint4 *>(b1) + e, pa + e);
+            cp_async16(reinterpret_cast<uint4 *>(b2) + e, pb + e);
+        }
+        cp_async_commit();
+    }
     const uint32_t Fp = __shfl_sync(FULL, lf, half);  // fitness of the parent this half carries over
     const int c = cut_point(p.seed, p.pop_id, gen, k, m);
     // incremental mode: parents keep their Gram buffers, offspring take the
@@ -667,7 +775,7 @@ __device__ void offspring_warp(const FusedPop &p, PopSel &S, int src, uint32_t g
     uint32_t gb1 = 0, gb2 = 0, go = 0;
     if (inc) {
         const uint32_t P = (uint32_t)(4 * p.N);
-        uint32_t g = lane < 3 ? ldcg32(p.gidx[src] + look) : 0u;
+        uint32_t g = lg;
         if (g >= P) {
             atomicOr(err, ERR_INTERNAL);  // never expected: indices stay a permutation of [0, P)
             g = 0u;
@@ -679,27 +787,30 @@ __device__ void offspring_warp(const FusedPop &p, PopSel &S, int src, uint32_t g
         gb1 = __shfl_sync(FULL, g, 0);
         gb2 = __shfl_sync(FULL, g, 1);
         go = __shfl_sync(FULL, g, 2);
-    }
-    uint32_t *b1 = buf, *b2 = buf + words, *bo = buf + 2 * words;
-    const uint32_t *sp = p.pop[src];
-    uint32_t *dp = p.pop[src ^ 1];
-    {
-        // both parents as 16-byte loads (words is a multiple of 4); this
-        // half's parent keeps its place k + oh in the next population
-        const uint32_t w4 = words >> 2;
-        const uint4 *pa = reinterpret_cast<const uint4 *>(sp) + (size_t)s1 * w4;
-        const uint4 *pb = reinterpret_cast<const uint4 *>(sp) + (size_t)s2 * w4;
-        uint4 *d4 = reinterpret_cast<uint4 *>(dp) + (size_t)(k + oh) * w4;
-        for (uint32_t e = lane; e < w4; e += 32) {
-            const uint4 x = __ldcg(pa + e), y = __ldcg(pb + e);
-            reinterpret_cast<uint4 *>(b1)[e] = x;
-            reinterpret_cast<uint4 *>(b2)[e] = y;
-            d4[e] = half ? y : x;
+        // the parents' Gram tiles start moving now, under the parent loads,
+        // crossover and mutation below
+        if constexpr (INC) {
+            const IncCopyPlan pl(m, c);
+            inc_copy_issue(pl, p.gram + (size_t)(half ? gb2 : gb1) * p.dpad,
+                           p.gram + (size_t)(half ? gb1 : gb2) * p.dpad, ring, ring_groups, 0, lane);
+            cp_async_commit();
         }
+    }
+    // the parents have landed once at most the Gram group is pending
+    if (inc)
+        cp_async_wait_group<1>();
+    else
+        cp_async_wait_group<0>();
+    __syncwarp();
+    {
+        // this half's parent keeps its place k + oh in the next population
+        const uint4 *bp = reinterpret_cast<const uint4 *>(half ? b2 : b1);
+        uint4 *d4 = reinterpret_cast<uint4 *>(dp) + (size_t)(k + oh) * w4;
+        for (uint32_t e = lane; e < w4; e += 32)
+            d4[e] = bp[e];
     }
     if (lane == 0)
         p.fit[src ^ 1][k + oh] = Fp;
-    __syncwarp();
     // crossover (Sec. 3.4): O1 = P1[:, :c] | P2[:, c:], O2 = P2[:, :c] | P1[:, c:]
     for (uint32_t e = lane; e < words; e += 32)
         bo[e] = (((int)(e / W) < c) != (half != 0)) ? b1[e] : b2[e];
@@ -740,9 +851,9 @@ __device__ void offspring_warp(const FusedPop &p, PopSel &S, int src, uint32_t g
             const uint32_t gt = half ? gb2 : gb1, gbm = half ? gb1 : gb2;
             const uint32_t *bt = half ? b2 : b1, *bb = half ? b1 : b2;  // parents giving [0, c) and [c, m)
             switch (p.kind) {
-            case FIT_SQ: f = offspring_incremental<W, FIT_SQ>(p, bo, bt, bb, mut, c, gt, gbm, go, stage, lane); break;
-            case FIT_ABS: f = offspring_incremental<W, FIT_ABS>(p, bo, bt, bb, mut, c, gt, gbm, go, stage, lane); break;
-            default: f = offspring_incremental<W, FIT_NNZ>(p, bo, bt, bb, mut, c, gt, gbm, go, stage, lane); break;
+            case FIT_SQ: f = offspring_incremental<W, FIT_SQ>(p, bo, bt, bb, mut, c, gt, gbm, go, ring, ring_groups, lane); break;
+            case FIT_ABS: f = offspring_incremental<W, FIT_ABS>(p, bo, bt, bb, mut, c, gt, gbm, go, ring, ring_groups, lane); break;
+            default: f = offspring_incremental<W, FIT_NNZ>(p, bo, bt, bb, mut, c, gt, gbm, go, ring, ring_groups, lane); break;
             }
         }
     }
@@ -857,11 +968,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
     const uint32_t TT = prm.total_tiles;
     // [tile masks and their prefix (phase B) | incremental copy ring (phase B)
     //  | staged histograms (phase A, overlapping both)] [bhist] [warp buffers]
-    const uint32_t r1 = max(4u * TT + (INC ? kIncStageWords : 0u), 2u * kHistSmem);
+    const uint32_t ring_words = INC ? (uint32_t)(kFusedThreads / 32) * (uint32_t)prm.inc_ring * 4u : 0u;
+    const uint32_t r1 = max(4u * TT + ring_words, 2u * kHistSmem);
     unsigned long long *tm = reinterpret_cast<unsigned long long *>(dyn);
     unsigned long long *ex = tm + TT;
     uint32_t *hcnt = dyn;
-    uint4 *stage = reinterpret_cast<uint4 *>(dyn + 4u * TT) + wib * 32 * kIncStage;
+    uint4 *ring = reinterpret_cast<uint4 *>(dyn + 4u * TT) + wib * prm.inc_ring;
     uint32_t *bhist = dyn + r1;  // block-local histograms of the next generation
     uint32_t *wbuf = bhist + kHistSmem + wib * prm.warp_buf_words;
     const Surv sv{tm, ex};
@@ -1267,9 +1379,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             uint32_t *hn = hist_of(p, par ^ 1);
             const uint32_t gen = S[i].gen0 + 1u + (uint32_t)t;
             switch (p.W) {
-            case 2: offspring_warp<2, INC>(p, S[i], src, gen, (uint32_t)t, k, half, sv, err, wbuf, stage, hn, bhist); break;
-            case 3: offspring_warp<3, INC>(p, S[i], src, gen, (uint32_t)t, k, half, sv, err, wbuf, stage, hn, bhist); break;
-            case 4: offspring_warp<4, INC>(p, S[i], src, gen, (uint32_t)t, k, half, sv, err, wbuf, stage, hn, bhist); break;
+            case 2: offspring_warp<2, INC>(p, S[i], src, gen, (uint32_t)t, k, half, sv, err, wbuf, ring, prm.inc_ring, hn, bhist); break;
+            case 3: offspring_warp<3, INC>(p, S[i], src, gen, (uint32_t)t, k, half, sv, err, wbuf, ring, prm.inc_ring, hn, bhist); break;
+            case 4: offspring_warp<4, INC>(p, S[i], src, gen, (uint32_t)t, k, half, sv, err, wbuf, ring, prm.inc_ring, hn, bhist); break;
             default: break;
             }
         }
@@ -1321,8 +1433,40 @@ size_t fused_smem_bytes(const FusedParams &p)
     bool inc = false;
     for (int i = 0; i < p.npop; ++i)
         inc = inc || p.p[i].gram != nullptr;
-    const size_t r1 = std::max((size_t)4 * p.total_tiles + (inc ? kIncStageWords : 0u), (size_t)2 * kHistSmem);
+    const size_t ring_words = inc ? (size_t)(kFusedThreads / 32) * (size_t)p.inc_ring * 4u : 0u;
+    const size_t r1 = std::max((size_t)4 * p.total_tiles + ring_words, (size_t)2 * kHistSmem);
     return (r1 + kHistSmem + (size_t)(kFusedThreads / 32) * p.warp_buf_words) * 4u;
+}
+
+void fused_plan_ring(FusedParams &p)
+{
+    // every copy of one offspring (the largest IncCopyPlan total over the
+    // cuts) when the shared memory of a block allows it, else the largest
+    // multiple of 32 groups that fits, at least 128
+    int max_groups = 0;
+    bool inc = false;
+    for (int i = 0; i < p.npop; ++i)
+        if (p.p[i].gram != nullptr) {
+            inc = true;
+            for (int c = 1; c < p.p[i].m; ++c)
+                max_groups = std::max(max_groups, IncCopyPlan(p.p[i].m, c).total);
+        }
+    p.inc_ring = 0;
+    if (!inc)
+        return;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, k_fused<true>);
+    const long long budget = (long long)optin - (long long)fa.sharedSizeBytes;
+    int ring = (max_groups + 31) / 32 * 32;
+    for (; ring > 128; ring -= 32) {
+        p.inc_ring = ring;
+        if ((long long)fused_smem_bytes(p) <= budget)
+            return;
+    }
+    p.inc_ring = 128;
 }
 
 cudaError_t fused_grid(size_t smem, int *grid)

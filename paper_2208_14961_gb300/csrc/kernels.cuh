@@ -141,12 +141,16 @@ struct FusedParams {
     int32_t stop_at_zero;    // stop after a generation whose best fitness (population 0) is 0
     int32_t src;             // ping-pong buffer holding the current population
     int32_t warp_buf_words;  // shared words per warp for m > 32 populations
+    int32_t inc_ring;        // 16-byte slots per warp of the incremental copy ring (0: no incremental population)
     uint32_t *bar;           // grid-barrier counter (zeroed before the launch)
     uint32_t *err;           // device error word
     int32_t *done;           // generations completed
 };
 
 size_t fused_smem_bytes(const FusedParams &p);
+// Sets p.inc_ring: the largest copy ring (up to one offspring's phase-1
+// copies) that keeps the block's shared memory within the device limit.
+void fused_plan_ring(FusedParams &p);
 cudaError_t fused_grid(size_t smem, int *grid);
 cudaError_t launch_fused(const FusedParams &p, int grid, size_t smem, cudaStream_t s);
 

@@ -58,7 +58,8 @@ def test_config2_m20_P40000_prefix(mode):
 
 @pytest.mark.parametrize("mode", ["plain", "fused"])
 @pytest.mark.parametrize("m,N,NC,NR,kind", [(4, 1, 1, 1, 0), (8, 3, 2, 2, 2), (16, 40, 4, 2, 1),
-                                            (28, 33, 1, 10, 2), (36, 25, 2, 3, 0), (100, 20, 1, 1, 0)])
+                                            (28, 33, 1, 10, 2), (36, 25, 2, 3, 0), (68, 21, 1, 1, 0),
+                                            (92, 19, 2, 2, 1), (100, 20, 1, 1, 0), (128, 9, 4, 2, 2)])
 def test_small_configs(mode, m, N, NC, NR, kind):
     h = need_gpu()
     _assert_same(_run_gpu(h, m, N, 7, 30, 1, mode, NC, NR, kind, pop_id=3),

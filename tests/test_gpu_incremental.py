@@ -37,7 +37,8 @@ def _gpu(h, m, N, seed, gens, NC=1, NR=1, kind=0, pop_id=0, graph=False):
 
 @pytest.mark.parametrize("m,N,NC,NR,kind", [(36, 25, 1, 1, 0), (36, 40, 2, 3, 1), (64, 30, 1, 1, 0),
                                             (64, 20, 3, 2, 2), (100, 20, 1, 1, 0), (100, 16, 2, 4, 1),
-                                            (128, 12, 1, 1, 0), (44, 33, 1, 10, 2)])
+                                            (128, 12, 1, 1, 0), (44, 33, 1, 10, 2),
+                                            (68, 21, 1, 1, 0), (92, 19, 2, 2, 2)])
 def test_incremental_matches_oracle(m, N, NC, NR, kind):
     h = need_gpu()
     gens = 30
