@@ -53,6 +53,14 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+# DRAM read + write bytes of one k_fused launch of this workload from the
+# ncu capture summarised in profiles/k_fused_m20_P40k.md (the population
+# stays in L2 across the generations of a launch, so the cold read of the
+# starting population is the whole traffic and does not grow with the
+# generations per launch).
+FUSED_M20_DRAM_BYTES_PER_LAUNCH = 3.464192e6
+
+
 def bytes_per_generation(m=M, N=N):
     """Algorithmic HBM bytes of one generation of the fused kernel (bit
     storage): read the 2N surviving parents, write all 4N slots (2N parents
@@ -622,7 +630,7 @@ def main():
         per_launch_bytes = bytes_per_generation() * STEP_GENS
         achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_fused", "peak_source": peak_kind,
+                "traffic": FUSED_M20_DRAM_BYTES_PER_LAUNCH, "kernel": "k_fused", "peak_source": peak_kind,
                 "launch_ms": per_launch_ms, "perm_table_ms_per_launch": perm_ms / max(fused_launches, 1)}
 
     cpu = None

@@ -92,7 +92,7 @@ __device__ __forceinline__ void int8_to_cols(const int8_t *Q, int m, uint32_t *c
                 const uint32_t bal = __ballot_sync(0xFFFFFFFFu, (x >> (8 * k + 7)) & 1u);
                 const int j = 4 * cw + k;
                 if (lane == (j & 31))
-                    store_col_word<W>(cols, j, rg, m, bal);
+                    cols[col_word_index<W>(j, rg, col_set_cols(m))] = bal;
             }
         }
     }
@@ -108,8 +108,13 @@ __global__ void __launch_bounds__(256) k_fit_int8_popc(const int8_t *__restrict_
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int nch = warp_gram_chunks(m);
+    const int mc = col_set_cols(m), ncopy = ((m >> 1) - 1) * W;
     for (int64_t q = first + gw; q < first + count; q += nw) {
         int8_to_cols<W>(pop + (size_t)q * m * m, m, cols, lane);
+        __syncwarp();
+        // copies of columns 0 .. m/2 - 2 after column m - 1
+        for (int e = lane; e < ncopy; e += 32)
+            cols[col_word_index<W>(m + e / W, e % W, mc)] = cols[col_word_index<W>(e / W, e % W, mc)];
         __syncwarp();
         const uint32_t f = warp_fitness_cols<W, KIND>(cols, m, lane, nch);
         if (lane == 0)
