@@ -393,6 +393,60 @@ def table3_workload(args):
             print(json.dumps(line), flush=True)
 
 
+# Sec. 4.4 of the paper: runs that found Hadamard matrices with fitness F2 on
+# an RTX 3080: (m, N, NC, NR, generations, seconds).
+PAPER_SEARCHES = [(20, 1000, 2, 8, 258_875, 517), (24, 1000, 2, 10, 9_576_814, 19_997),
+                  (28, 10_000, 1, 10, 428_082, 3_054)]
+
+
+def search_workload(args):
+    """Time to a Hadamard matrix (Sec. 4.4): for each order of the paper's
+    successful searches, with its population size, mutation parameters and
+    fitness F2, run the fused path in ga_step calls of `--search-chunk`
+    generations with stop_at_zero until the best fitness is 0 or
+    `--search-seconds` pass; several seeds (`--search-seeds`).  A matrix found
+    is read back and checked on the host: Q^T Q = m I.  One JSON line per run
+    with the generations and seconds taken, next to the paper's run (one run
+    of a stochastic search on other hardware: context, not a target)."""
+    import numpy as np
+
+    from paper_2208_14961_gb300.build import build
+    build()
+    from paper_2208_14961_gb300 import hadga as h
+
+    orders = [int(x) for x in args.search_ms.split(",")]
+    for (m, N, NC, NR, p_gens, p_sec) in PAPER_SEARCHES:
+        if m not in orders:
+            continue
+        for seed in range(args.search_seeds):
+            pop = h.Population(m, N, seed=100 + seed, NC=NC, NR=NR, fitness=h.FIT_NNZ, storage=h.STORE_BITS,
+                               traj_cap=args.search_chunk)
+            pop.init_population()
+            pop.fitness()
+            pop.sync()
+            gens, found = 0, False
+            t0 = time.perf_counter()
+            while time.perf_counter() - t0 < args.search_seconds:
+                done = pop.step(args.search_chunk, stop_at_zero=True)
+                gens += done
+                if done < args.search_chunk:
+                    found = True
+                    break
+            pop.sync()
+            sec = time.perf_counter() - t0
+            line = {"workload": "paper Sec. 4.4 search", "m": m, "P": 4 * N, "NC": NC, "NR": NR, "fitness": "F2",
+                    "seed": 100 + seed, "found": found, "generations": gens, "seconds": sec,
+                    "generations_per_s": gens / sec if sec > 0 else None,
+                    "paper_rtx3080": {"generations": p_gens, "seconds": p_sec}}
+            slot, best = pop.best()
+            line["best_fitness"] = int(best)
+            if found:
+                Q = pop.get_slot(slot).astype(np.int64)
+                line["verified_QtQ_eq_mI"] = bool(np.array_equal(Q.T @ Q, m * np.eye(m, dtype=np.int64)))
+            pop.close()
+            print(json.dumps(line), flush=True)
+
+
 def incremental_workload(args):
     """Incremental Gram-delta fitness (a7) on m=100, P=20,000 bit-packed
     balanced matrices (seed 4, F_sq, NC = NR = 1) for `--inc-gens`
@@ -488,6 +542,11 @@ def main():
     ap.add_argument("--table3", action="store_true", help="the paper's fitness-comparison workload (Sec. 4.2)")
     ap.add_argument("--t3-ms", default="20,40,60,80,100")
     ap.add_argument("--t3-gens", type=int, default=1000)
+    ap.add_argument("--search", action="store_true", help="time to a Hadamard matrix (the paper's Sec. 4.4 runs)")
+    ap.add_argument("--search-ms", default="20,24,28")
+    ap.add_argument("--search-seeds", type=int, default=3)
+    ap.add_argument("--search-seconds", type=float, default=60.0)
+    ap.add_argument("--search-chunk", type=int, default=2048)
     args = ap.parse_args()
     if args.gram_sweep:
         gram_sweep(args)
@@ -500,6 +559,9 @@ def main():
         return
     if args.table3:
         table3_workload(args)
+        return
+    if args.search:
+        search_workload(args)
         return
     args.warmup = max(args.warmup, 3)
 

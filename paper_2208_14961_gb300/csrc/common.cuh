@@ -434,6 +434,64 @@ __device__ __forceinline__ void red_release_gpu_add(uint32_t *p, uint32_t v)
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// mbarriers (completion of asynchronous copies and tensor-core work)
+// ---------------------------------------------------------------------------
+constexpr unsigned long long kMbarWaitBudgetNs = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase of `bar` with parity `parity`; false when the
+// budget ran out, or another thread raised an error and the phase is still
+// open (a completed phase always reports true).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t *err)
+{
+    if (mbar_test(bar, parity))
+        return true;
+    const unsigned long long t0 = global_ns();
+    for (uint32_t i = 1;; ++i) {
+        if (mbar_test(bar, parity))
+            return true;
+        if ((i & 255u) == 0u) {
+            if (ld_acquire_gpu(err) != 0u)
+                return mbar_test(bar, parity);
+            if (global_ns() - t0 > kMbarWaitBudgetNs) {
+                atomicOr(err, ERR_TIMEOUT);
+                return mbar_test(bar, parity);
+            }
+        }
+    }
+}
+
+
 // Grid-wide barrier for a cooperative launch with every block resident.
 // `bar` counts arrivals monotonically (zeroed before the launch); `epoch`
 // is the caller's barrier count.  Arrival is a gpu-scope release reduction

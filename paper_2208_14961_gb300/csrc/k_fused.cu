@@ -590,13 +590,65 @@ __device__ __forceinline__ void inc_copy_issue(const IncCopyPlan &pl, const int8
     }
 }
 
+// The whole copy plan as bulk asynchronous copies (cp.async.bulk, the TMA
+// engine's linear form) completing on the warp's mbarrier `bar`: one copy
+// per run of consecutive ring slots -- each H[:c, :c] tile row of Pt, the
+// H[c:, c:] tiles of Pb, and when 8 does not divide c one per tile of the
+// cut tile column (Pt) and of the cut tile row (Pb).  Lane 0 posts the byte
+// count first; the lanes then issue the runs r = lane, lane + 32, ...  Only
+// when the whole plan fits the ring (pl.total <= ring_groups).
+__device__ __forceinline__ void inc_bulk_issue(const IncCopyPlan &pl, const int8_t *gt8, const int8_t *gb8,
+                                               uint4 *ring, uint64_t *bar, int lane)
+{
+    const int nt = pl.nb * (pl.nb + 1) / 2, I0 = pl.J0, nbr = nt > pl.tBR ? 1 : 0;
+    const int n4 = pl.r0 ? I0 + 1 : 0, n3 = pl.r0 ? pl.nb - I0 : 0;
+    const int nruns = pl.J0 + nbr + n4 + n3;
+    // the parents' tiles were written by generic stores before the last grid
+    // barrier, and the ring was last read by generic loads: order both
+    // before this thread's async copies
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (lane == 0)
+        mbar_expect_tx(bar, (uint32_t)pl.total * 16u);
+    __syncwarp();
+    for (int r = lane; r < nruns; r += 32) {
+        const int8_t *src;
+        int slot, bytes;
+        if (r < pl.J0) {  // tile row I = r of the H[:c, :c] triangle
+            const int I = r;
+            src = gt8 + 64u * pl.tile(I, I);
+            slot = 4 * (I * pl.J0 - (I * (I - 1)) / 2);
+            bytes = 64 * (pl.J0 - I);
+        } else if (r < pl.J0 + nbr) {
+            src = gb8 + 64u * (uint32_t)pl.tBR;
+            slot = 4 * pl.nTL;
+            bytes = 64 * (nt - pl.tBR);
+        } else if (r < pl.J0 + nbr + n4) {  // Pt's rows i < c of tile (I, J0)
+            const int I = r - pl.J0 - nbr;
+            src = gt8 + 64u * pl.tile(I, pl.J0);
+            slot = pl.nG + 4 * I;
+            bytes = 16 * (I < I0 ? 4 : (pl.r0 + 1) >> 1);
+        } else {  // Pb's rows i >= c of tile (I0, J)
+            const int J = I0 + (r - pl.J0 - nbr - n4);
+            src = gb8 + 64u * pl.tile(I0, J) + 16u * (uint32_t)(pl.r0 >> 1);
+            slot = pl.nG + pl.n4g + (J - pl.J0) * pl.g3;
+            bytes = 16 * pl.g3;
+        }
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         smem_u32(ring + slot)),
+                     "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                     : "memory");
+    }
+}
+
 // The caller has issued the first ring-full of phase-1 copies
 // (inc_copy_issue with base 0) before the parent loads, crossover and
 // mutation, whose latency the copies overlap.
 template <int W, int KIND>
 __device__ uint32_t offspring_incremental(const FusedPop &p, const uint32_t *bo, const uint32_t *bt,
                                           const uint32_t *bb, const uint32_t (&mut)[4], int c, uint32_t gt,
-                                          uint32_t gbm, uint32_t go, uint4 *ring, int ring_groups, int lane)
+                                          uint32_t gbm, uint32_t go, uint4 *ring, int ring_groups, uint64_t *bar,
+                                          uint32_t &bar_parity, uint32_t *err, int lane)
 {
     const int m = p.m, nb = gram_tiles_nb(m), hm = m >> 1;
     const int8_t *gt8 = p.gram + (size_t)gt * p.dpad, *gb8 = p.gram + (size_t)gbm * p.dpad;
@@ -608,10 +660,18 @@ __device__ uint32_t offspring_incremental(const FusedPop &p, const uint32_t *bo,
     // H[c:, c:] (tiles t >= tBR), one ring-full at a time
     const IncCopyPlan pl(m, c);
     const int J0 = pl.J0;
+    // the extra groups sit in the ring when the whole plan fit (8-byte rows)
+    const bool pre = pl.total <= ring_groups;
+    if (pre) {
+        // one bulk-copy phase of the warp's mbarrier (bounded wait)
+        mbar_wait(bar, bar_parity, err);
+        bar_parity ^= 1u;
+    }
     for (int base = 0; base < pl.nG; base += ring_groups) {
         if (base > 0)
             inc_copy_issue(pl, gt8, gb8, ring, ring_groups, base, lane);
-        cp_async_wait_all();
+        if (!pre)
+            cp_async_wait_all();
         const int end = min(base + ring_groups, pl.nG);
         for (IncGroupIter it(pl, base + lane); it.e < end; it.next(pl)) {
             const uint4 v = ring[it.e - base];
@@ -622,8 +682,6 @@ __device__ uint32_t offspring_incremental(const FusedPop &p, const uint32_t *bo,
         if (base + ring_groups < pl.nG)
             __syncwarp();  // the ring is refilled by other lanes' copies next round
     }
-    // the extra groups sit in the ring when the whole plan fit (8-byte rows)
-    const bool pre = pl.total <= ring_groups;
     const uint2 *ring8 = reinterpret_cast<const uint2 *>(ring) + 2 * pl.nG;
     // tile rows i >= c of the tile row I0 = c / 8 cut by c (from Pb)
     if (c & 7) {
@@ -730,7 +788,8 @@ __device__ uint32_t offspring_incremental(const FusedPop &p, const uint32_t *bo,
 template <int W, bool INC>
 __device__ void offspring_warp(const FusedPop &p, PopSel &S, int src, uint32_t gen, uint32_t tch, uint32_t k,
                                int half, const Surv &sv, uint32_t *err, uint32_t *buf, uint4 *ring,
-                               int ring_groups, uint32_t *hist_next, uint32_t *bhist)
+                               int ring_groups, uint64_t *bar, uint32_t &bar_parity, uint32_t *hist_next,
+                               uint32_t *bhist)
 {
     const int lane = threadIdx.x & 31;
     const int m = p.m;
@@ -773,6 +832,7 @@ __device__ void offspring_warp(const FusedPop &p, PopSel &S, int src, uint32_t g
     // incremental mode: parents keep their Gram buffers, offspring take the
     // buffers of the non-survivors
     uint32_t gb1 = 0, gb2 = 0, go = 0;
+    bool gram_group = false;  // the Gram tiles travel as a cp.async group (plan larger than the ring)
     if (inc) {
         const uint32_t P = (uint32_t)(4 * p.N);
         uint32_t g = lg;
@@ -791,13 +851,19 @@ __device__ void offspring_warp(const FusedPop &p, PopSel &S, int src, uint32_t g
         // crossover and mutation below
         if constexpr (INC) {
             const IncCopyPlan pl(m, c);
-            inc_copy_issue(pl, p.gram + (size_t)(half ? gb2 : gb1) * p.dpad,
-                           p.gram + (size_t)(half ? gb1 : gb2) * p.dpad, ring, ring_groups, 0, lane);
-            cp_async_commit();
+            const int8_t *gt8 = p.gram + (size_t)(half ? gb2 : gb1) * p.dpad;
+            const int8_t *gb8 = p.gram + (size_t)(half ? gb1 : gb2) * p.dpad;
+            if (pl.total <= ring_groups) {
+                inc_bulk_issue(pl, gt8, gb8, ring, bar, lane);
+            } else {
+                inc_copy_issue(pl, gt8, gb8, ring, ring_groups, 0, lane);
+                cp_async_commit();
+                gram_group = true;
+            }
         }
     }
-    // the parents have landed once at most the Gram group is pending
-    if (inc)
+    // the parents have landed once at most the Gram group (if any) is pending
+    if (gram_group)
         cp_async_wait_group<1>();
     else
         cp_async_wait_group<0>();
@@ -851,9 +917,9 @@ __device__ void offspring_warp(const FusedPop &p, PopSel &S, int src, uint32_t g
             const uint32_t gt = half ? gb2 : gb1, gbm = half ? gb1 : gb2;
             const uint32_t *bt = half ? b2 : b1, *bb = half ? b1 : b2;  // parents giving [0, c) and [c, m)
             switch (p.kind) {
-            case FIT_SQ: f = offspring_incremental<W, FIT_SQ>(p, bo, bt, bb, mut, c, gt, gbm, go, ring, ring_groups, lane); break;
-            case FIT_ABS: f = offspring_incremental<W, FIT_ABS>(p, bo, bt, bb, mut, c, gt, gbm, go, ring, ring_groups, lane); break;
-            default: f = offspring_incremental<W, FIT_NNZ>(p, bo, bt, bb, mut, c, gt, gbm, go, ring, ring_groups, lane); break;
+            case FIT_SQ: f = offspring_incremental<W, FIT_SQ>(p, bo, bt, bb, mut, c, gt, gbm, go, ring, ring_groups, bar, bar_parity, err, lane); break;
+            case FIT_ABS: f = offspring_incremental<W, FIT_ABS>(p, bo, bt, bb, mut, c, gt, gbm, go, ring, ring_groups, bar, bar_parity, err, lane); break;
+            default: f = offspring_incremental<W, FIT_NNZ>(p, bo, bt, bb, mut, c, gt, gbm, go, ring, ring_groups, bar, bar_parity, err, lane); break;
             }
         }
     }
@@ -957,6 +1023,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
     __shared__ uint32_t hoff[kMaxPops];
     __shared__ int s_flag;
     __shared__ uint32_t s_next;  // next warp item of the block (phase B)
+    __shared__ __align__(8) uint64_t s_incbar[kFusedThreads / 32];  // per-warp bulk-copy barrier
 
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
     const int npop = prm.npop;
@@ -979,6 +1046,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
     const Surv sv{tm, ex};
     uint32_t *err = prm.err;
     uint32_t epoch = 0;
+    uint32_t inc_parity = 0;  // phase of this warp's bulk-copy barrier
+    if (INC && tid < kFusedThreads / 32)
+        mbar_init(&s_incbar[tid], 1);
+    if (INC && tid == 0)
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     int src = prm.src;
     int done = 0;
     auto tile_base = [&](int i) { return prm.p[i].tile_base; };
@@ -1379,9 +1451,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             uint32_t *hn = hist_of(p, par ^ 1);
             const uint32_t gen = S[i].gen0 + 1u + (uint32_t)t;
             switch (p.W) {
-            case 2: offspring_warp<2, INC>(p, S[i], src, gen, (uint32_t)t, k, half, sv, err, wbuf, ring, prm.inc_ring, hn, bhist); break;
-            case 3: offspring_warp<3, INC>(p, S[i], src, gen, (uint32_t)t, k, half, sv, err, wbuf, ring, prm.inc_ring, hn, bhist); break;
-            case 4: offspring_warp<4, INC>(p, S[i], src, gen, (uint32_t)t, k, half, sv, err, wbuf, ring, prm.inc_ring, hn, bhist); break;
+            case 2: offspring_warp<2, INC>(p, S[i], src, gen, (uint32_t)t, k, half, sv, err, wbuf, ring, prm.inc_ring, &s_incbar[wib], inc_parity, hn, bhist); break;
+            case 3: offspring_warp<3, INC>(p, S[i], src, gen, (uint32_t)t, k, half, sv, err, wbuf, ring, prm.inc_ring, &s_incbar[wib], inc_parity, hn, bhist); break;
+            case 4: offspring_warp<4, INC>(p, S[i], src, gen, (uint32_t)t, k, half, sv, err, wbuf, ring, prm.inc_ring, &s_incbar[wib], inc_parity, hn, bhist); break;
             default: break;
             }
         }

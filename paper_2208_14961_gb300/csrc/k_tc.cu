@@ -39,7 +39,6 @@ namespace {
 constexpr int kTcThreads = 320;  // 10 warps: producer, MMA, two epilogue groups of four
 constexpr int kMaxStages = 32;
 constexpr uint32_t kRingBytes = 160 * 1024;  // shared memory of the stage ring
-constexpr unsigned long long kWaitBudgetNs = 2000000000ull;
 
 // Error word of launches that come without one (the stateless batch call).
 __device__ uint32_t g_tc_err;
@@ -58,58 +57,6 @@ struct TcParams {
     uint32_t *fit;
     uint32_t *err;
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile("{\n\t.reg .pred p;\n\t"
-                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                 "selp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(ok)
-                 : "r"(smem_u32(bar)), "r"(parity)
-                 : "memory");
-    return ok != 0;
-}
-
-// Bounded wait for the phase of `bar` with parity `parity`; false when the
-// budget ran out, or another thread raised an error and the phase is still
-// open (a completed phase always reports true).
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t *err)
-{
-    if (mbar_test(bar, parity))
-        return true;
-    const unsigned long long t0 = global_ns();
-    for (uint32_t i = 1;; ++i) {
-        if (mbar_test(bar, parity))
-            return true;
-        if ((i & 255u) == 0u) {
-            if (ld_acquire_gpu(err) != 0u)
-                return mbar_test(bar, parity);
-            if (global_ns() - t0 > kWaitBudgetNs) {
-                atomicOr(err, ERR_TIMEOUT);
-                return mbar_test(bar, parity);
-            }
-        }
-    }
-}
 
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int32_t x, int32_t y, uint64_t *bar)
 {
