@@ -91,7 +91,9 @@ typedef struct {
     int32_t storage;  /* GA_STORE_INT8 or GA_STORE_BITS */
     int32_t path;     /* ga_gram_path used by ga_fitness */
     int32_t traj_cap; /* generations kept in the best-fitness trajectory (>= 1) */
-    int32_t reserved; /* must be 0 */
+    int32_t mutation; /* 0: each offspring draws its own columns and rows (methods 2 and 3
+                         of Sec. 3.5); 1: method 1 of Sec. 3.5, every offspring of a
+                         generation uses the same draws, those of stream index 2N */
 } ga_config;
 
 typedef struct ga_ctx ga_ctx;
@@ -146,7 +148,8 @@ ga_status ga_crossover(ga_ctx *ctx);
  * generation g.  Offspring o in [0, 2N) (slot 2N+o) draws NC columns in
  * [1, m-1], then NR first rows and NR second rows in [0, m-1], from stream
  * (MUTATE, g, o, 0); for each column in order and each pair in order, the
- * two entries are negated iff their signs differ. */
+ * two entries are negated iff their signs differ.  With cfg.mutation = 1
+ * (method 1) every offspring uses the draws of stream (MUTATE, g, 2N, 0). */
 ga_status ga_mutate(ga_ctx *ctx);
 
 /* a8 -- records the best (least F, lowest slot) of the current population

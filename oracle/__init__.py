@@ -63,13 +63,13 @@ def _load():
             "orc_crossover": (None, [vp, i32, i64, u32, u32, u32]),
             "orc_mutate_explicit": (i32, [vp, i32, i32, i32, vp, vp, vp]),
             "orc_mutation_draws": (None, [i32, i32, i32, u32, u32, u32, u32, vp, vp, vp]),
-            "orc_mutate": (None, [vp, i32, i64, i32, i32, u32, u32, u32]),
+            "orc_mutate": (None, [vp, i32, i64, i32, i32, u32, u32, u32, i32]),
             "orc_select_key": (u32, [u32, u32, u32, u32]),
             "orc_perm": (None, [u32, u32, u32, u32, vp]),
             "orc_survivors": (None, [vp, i64, vp]),
             "orc_select": (None, [vp, vp, i32, i64, u32, u32, u32]),
             "orc_best": (None, [vp, i64, vp, vp]),
-            "orc_run": (i32, [vp, vp, i32, i64, i32, i32, i32, u32, u32, u32, i32, i32, vp, vp]),
+            "orc_run": (i32, [vp, vp, i32, i64, i32, i32, i32, u32, u32, u32, i32, i32, vp, vp, i32]),
             "orc_mixed_N": (i64, [u32, u32]),
             "orc_num_threads": (i32, []),
             "orc_set_num_threads": (None, [i32]),
@@ -186,8 +186,10 @@ def mutation_draws(m, NC, NR, seed, pop_id, gen, o):
     return c, r1, r2
 
 
-def mutate(pop: np.ndarray, N: int, NC: int, NR: int, seed: int, pop_id: int, gen: int) -> None:
-    _load().orc_mutate(_ptr(pop), pop.shape[1], N, NC, NR, seed, pop_id, gen)
+def mutate(pop: np.ndarray, N: int, NC: int, NR: int, seed: int, pop_id: int, gen: int, shared: int = 0) -> None:
+    """Mutation of the 2N offspring; shared = 1 is the paper's method 1 (one
+    draw for the whole generation)."""
+    _load().orc_mutate(_ptr(pop), pop.shape[1], N, NC, NR, seed, pop_id, gen, int(shared))
 
 
 def survivors(F: np.ndarray, N: int) -> np.ndarray:
@@ -211,13 +213,14 @@ def best(F: np.ndarray):
 
 
 def run(pop: np.ndarray, F: np.ndarray, N: int, NC: int, NR: int, kind: int, seed: int,
-        pop_id: int, gen0: int, generations: int, stop_at_zero: bool = False):
-    """Runs `generations` generations in place; returns (n_done, traj_fit, traj_slot)."""
+        pop_id: int, gen0: int, generations: int, stop_at_zero: bool = False, shared_mutation: int = 0):
+    """Runs `generations` generations in place; returns (n_done, traj_fit, traj_slot).
+    shared_mutation = 1 selects the paper's mutation method 1."""
     assert pop.dtype == np.int8 and F.dtype == np.uint64
     tf = np.zeros(max(generations, 1), dtype=np.uint64)
     ts = np.zeros(max(generations, 1), dtype=np.int64)
     n = _load().orc_run(_ptr(pop), _ptr(F), pop.shape[1], N, NC, NR, kind, seed, pop_id, gen0,
-                        generations, int(stop_at_zero), _ptr(tf), _ptr(ts))
+                        generations, int(stop_at_zero), _ptr(tf), _ptr(ts), int(shared_mutation))
     return int(n), tf[:n], ts[:n]
 
 

@@ -298,8 +298,13 @@ void orc_mutation_draws(int32_t m, int32_t NC, int32_t NR, uint32_t seed, uint32
         rows2[ir] = (int32_t)orc_uniform(stream_next(&s), 0u, (uint32_t)(m - 1));
 }
 
+/* Method 3 of Sec. 3.5 (method 2 is NC = NR = 1): offspring o draws from
+ * stream index o.  Method 1 (`shared` set): the same column and row pairs
+ * for every offspring of the generation, drawn once from stream index 2N
+ * (a stream no single offspring uses).  In both, a pair is flipped only
+ * when its two entries differ. */
 void orc_mutate(int8_t *pop, int32_t m, int64_t N, int32_t NC, int32_t NR, uint32_t seed,
-                uint32_t pop_id, uint32_t gen)
+                uint32_t pop_id, uint32_t gen, int32_t shared)
 {
     const size_t S = (size_t)m * m;
     int64_t o;
@@ -310,7 +315,8 @@ void orc_mutate(int8_t *pop, int32_t m, int64_t N, int32_t NC, int32_t NR, uint3
         int32_t *r2 = (int32_t *)malloc(sizeof(int32_t) * (size_t)NR);
 #pragma omp for schedule(static)
         for (o = 0; o < 2 * N; ++o) {
-            orc_mutation_draws(m, NC, NR, seed, pop_id, gen, (uint32_t)o, cols, r1, r2);
+            orc_mutation_draws(m, NC, NR, seed, pop_id, gen, shared ? (uint32_t)(2 * N) : (uint32_t)o, cols, r1,
+                               r2);
             orc_mutate_explicit(pop + (size_t)(2 * N + o) * S, m, NC, NR, cols, r1, r2);
         }
         free(cols);
@@ -460,14 +466,14 @@ void orc_best(const uint64_t *F, int64_t P, int64_t *slot, uint64_t *fit)
 /* ------------------------------------------------------------------------ */
 int32_t orc_run(int8_t *pop, uint64_t *F, int32_t m, int64_t N, int32_t NC, int32_t NR, int32_t kind,
                 uint32_t seed, uint32_t pop_id, uint32_t gen0, int32_t generations, int32_t stop_at_zero,
-                uint64_t *traj_fit, int64_t *traj_slot)
+                uint64_t *traj_fit, int64_t *traj_slot, int32_t shared_mutation)
 {
     int32_t done = 0;
     for (int32_t t = 0; t < generations; ++t) {
         uint32_t gen = gen0 + (uint32_t)t + 1u;
         orc_select(pop, F, m, N, seed, pop_id, gen);
         orc_crossover(pop, m, N, seed, pop_id, gen);
-        orc_mutate(pop, m, N, NC, NR, seed, pop_id, gen);
+        orc_mutate(pop, m, N, NC, NR, seed, pop_id, gen, shared_mutation);
         orc_fitness(pop, m, 2 * N, 2 * N, kind, F);
         int64_t bs;
         uint64_t bf;

@@ -176,8 +176,8 @@ ga_status ga_create(const ga_config *cfg, void *pop_dev, uint32_t *fit_dev, void
         return set_error(nullptr, GA_EINVAL, "unknown fitness %d", cfg->fitness);
     if (cfg->traj_cap < 1)
         return set_error(nullptr, GA_EINVAL, "traj_cap must be >= 1");
-    if (cfg->reserved != 0)
-        return set_error(nullptr, GA_EINVAL, "reserved must be 0");
+    if (cfg->mutation != 0 && cfg->mutation != 1)
+        return set_error(nullptr, GA_EINVAL, "mutation must be 0 (per offspring) or 1 (one draw per generation)");
     int path = cfg->path == GA_PATH_AUTO ? auto_path(cfg->storage, cfg->m, cfg->fitness) : cfg->path;
     if (!fitness_path_supported(cfg->storage, cfg->m, path))
         return set_error(nullptr, GA_EINVAL, "Gram path %d does not read storage %d", cfg->path, cfg->storage);
@@ -368,7 +368,7 @@ ga_status ga_mutate(ga_ctx *ctx)
     ctx->gram_valid = 0;
     return cuda_check(ctx,
                       launch_mutate(ctx->pop, ctx->cfg.storage, ctx->m, ctx->N, ctx->cfg.NC, ctx->cfg.NR,
-                                    ctx->cfg.seed, ctx->cfg.pop_id, ctx->gen, ctx->stream),
+                                    ctx->cfg.seed, ctx->cfg.pop_id, ctx->gen, ctx->cfg.mutation, ctx->stream),
                       "mutate");
 }
 
@@ -427,6 +427,7 @@ static ga_status fused_run(ga_ctx *const *ctxs, int n, int32_t generations, int 
         p.m = c->m;
         p.W = c->W;
         p.nch = warp_gram_chunks(c->m);
+        p.shared_mut = c->cfg.mutation;
         p.NC = c->cfg.NC;
         p.NR = c->cfg.NR;
         p.kind = c->cfg.fitness;

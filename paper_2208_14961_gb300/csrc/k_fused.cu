@@ -263,6 +263,13 @@ __device__ __forceinline__ uint32_t nonsurvivor_of(uint32_t o, const FusedPop &p
     return 32u * lo + (uint32_t)nth_set_bit(mask, (int)r);
 }
 
+// Stream index of the mutation draws of offspring o: o itself, or 2N for
+// every offspring under method 1 of Sec. 3.5 (one draw per generation).
+__device__ __forceinline__ uint32_t mut_stream(const FusedPop &p, uint32_t o)
+{
+    return p.shared_mut ? (uint32_t)(2 * p.N) : o;
+}
+
 // Draws of one build item that do not depend on the selection: survivor
 // number d, cut point c and (for NC = NR = 1) the mutated column and rows.
 struct Pre {
@@ -277,7 +284,7 @@ __device__ __forceinline__ Pre make_pre(const FusedPop &p, uint32_t gen, uint32_
     r.c = (uint32_t)cut_point(p.seed, p.pop_id, gen, k, p.m);
     r.cc = r.ra = r.rb = 0u;
     if (p.NC == 1 && p.NR == 1) {
-        const uint4 w = philox_block(p.seed, p.pop_id, OP_MUTATE, gen, k + (half ? N : 0u), 0u, 0u);
+        const uint4 w = philox_block(p.seed, p.pop_id, OP_MUTATE, gen, mut_stream(p, k + (half ? N : 0u)), 0u, 0u);
         r.cc = uniform_int(w.x, 1u, (uint32_t)(p.m - 1));
         r.ra = uniform_int(w.y, 0u, (uint32_t)(p.m - 1));
         r.rb = uniform_int(w.z, 0u, (uint32_t)(p.m - 1));
@@ -386,7 +393,7 @@ __device__ __forceinline__ void pair_thread(const FusedPop &p, const PopSel &S, 
                 }
             }
         } else {
-            Draws dr(p.seed, p.pop_id, gen, k + (half ? N : 0u));
+            Draws dr(p.seed, p.pop_id, gen, mut_stream(p, k + (half ? N : 0u)));
             uint8_t cols[64], r1[64], r2[64];
             for (int jc = 0; jc < NC; ++jc)
                 cols[jc] = (uint8_t)uniform_int(dr.next(), 1u, (uint32_t)(M - 1));
@@ -885,7 +892,7 @@ __device__ void offspring_warp(const FusedPop &p, PopSel &S, int src, uint32_t g
     // columns where a flip happened
     uint32_t mut[4] = {0u, 0u, 0u, 0u};
     if (lane == 0) {
-        Draws dr(p.seed, p.pop_id, gen, k + oh);
+        Draws dr(p.seed, p.pop_id, gen, mut_stream(p, k + oh));
         uint8_t cols[64], r1[64], r2[64];
         for (int jc = 0; jc < p.NC; ++jc)
             cols[jc] = (uint8_t)uniform_int(dr.next(), 1u, (uint32_t)(m - 1));

@@ -84,7 +84,9 @@ cudaError_t launch_crossover(void *pop, int storage, int m, int64_t N, uint32_t 
 // Offspring o (slot 2N+o): stream (MUTATE, gen, o, 0) gives NC columns in
 // [1, m-1], then NR first rows, then NR second rows in [0, m-1].  For each
 // column in order and each pair in order the two entries are negated iff
-// they differ.  One thread per offspring, reading the stream sequentially.
+// they differ.  With `shared` (method 1 of Sec. 3.5) every offspring uses
+// the draws of stream index 2N.  One thread per offspring, reading the
+// stream sequentially.
 // ---------------------------------------------------------------------------
 struct MutStream {
     uint32_t seed, pop_id, gen, o, block;
@@ -104,7 +106,7 @@ struct MutStream {
 
 template <bool BITS>
 __global__ void __launch_bounds__(128) k_mutate(void *pop, int m, int64_t N, int NC, int NR, uint32_t seed,
-                                                uint32_t pop_id, uint32_t gen)
+                                                uint32_t pop_id, uint32_t gen, int shared)
 {
     const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (o >= 2 * N)
@@ -112,7 +114,7 @@ __global__ void __launch_bounds__(128) k_mutate(void *pop, int m, int64_t N, int
     const int W = words_per_col(m);
     // draws: NC columns, NR first rows, NR second rows (at most 64 each)
     uint8_t col[64], r1[64], r2[64];
-    MutStream st(seed, pop_id, gen, (uint32_t)o);
+    MutStream st(seed, pop_id, gen, shared ? (uint32_t)(2 * N) : (uint32_t)o);
     for (int jc = 0; jc < NC; ++jc)
         col[jc] = (uint8_t)uniform_int(st.next(), 1u, (uint32_t)(m - 1));
     for (int ir = 0; ir < NR; ++ir)
@@ -144,14 +146,14 @@ __global__ void __launch_bounds__(128) k_mutate(void *pop, int m, int64_t N, int
 }
 
 cudaError_t launch_mutate(void *pop, int storage, int m, int64_t N, int NC, int NR, uint32_t seed, uint32_t pop_id,
-                          uint32_t gen, cudaStream_t s)
+                          uint32_t gen, int shared, cudaStream_t s)
 {
     const int bs = 128;
     const unsigned grid = (unsigned)((2 * N + bs - 1) / bs);
     if (storage == ST_BITS)
-        k_mutate<true><<<grid, bs, 0, s>>>(pop, m, N, NC, NR, seed, pop_id, gen);
+        k_mutate<true><<<grid, bs, 0, s>>>(pop, m, N, NC, NR, seed, pop_id, gen, shared);
     else if (storage == ST_INT8)
-        k_mutate<false><<<grid, bs, 0, s>>>(pop, m, N, NC, NR, seed, pop_id, gen);
+        k_mutate<false><<<grid, bs, 0, s>>>(pop, m, N, NC, NR, seed, pop_id, gen, shared);
     else
         return cudaErrorInvalidValue;
     note_launches(1);

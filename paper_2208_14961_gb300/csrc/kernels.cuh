@@ -56,8 +56,9 @@ bool fitness_tc_supported(int storage, int m);
 // ---- operators (k_ops.cu) ---------------------------------------------------
 cudaError_t launch_crossover(void *pop, int storage, int m, int64_t N, uint32_t seed, uint32_t pop_id, uint32_t gen,
                              cudaStream_t s);
+// shared = 1: method 1 of Sec. 3.5 (all offspring use the draws of stream index 2N).
 cudaError_t launch_mutate(void *pop, int storage, int m, int64_t N, int NC, int NR, uint32_t seed, uint32_t pop_id,
-                          uint32_t gen, cudaStream_t s);
+                          uint32_t gen, int shared, cudaStream_t s);
 // Least (F << 32 | slot) of fit[0, P) into *out (which is first set to ~0).
 cudaError_t launch_best(const uint32_t *fit, int64_t P, unsigned long long *out, cudaStream_t s);
 cudaError_t launch_convert(const void *src, int src_storage, void *dst, int dst_storage, int m, int64_t P,
@@ -125,6 +126,7 @@ struct FusedPop {
     int32_t dpad;              // bytes per Gram buffer (64 per tile)
     int32_t m, W, NC, NR, kind, traj_cap;
     int32_t nch;                 // chunks per column of the warp-level Gram (warp_gram_chunks)
+    int32_t shared_mut;          // mutation method 1: every offspring draws from stream index 2N
     int64_t N;
     uint32_t seed, pop_id;
     uint32_t tile_base, ntiles;  // tiles of 32 slots in the joint tile space

@@ -43,7 +43,7 @@ class ga_config(ctypes.Structure):
         ("storage", ctypes.c_int32),
         ("path", ctypes.c_int32),
         ("traj_cap", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("mutation", ctypes.c_int32),
     ]
 
 
@@ -189,7 +189,7 @@ class Population:
 
     def __init__(self, m: int, N: int, seed: int = 0, pop_id: int = 0, NC: int = 1, NR: int = 1,
                  fitness: int = FIT_SQ, storage: int = STORE_BITS, path: int = PATH_AUTO,
-                 traj_cap: int = 1024, device="cuda", stream=None):
+                 traj_cap: int = 1024, device="cuda", stream=None, mutation: int = 0):
         lib = load()
         self.m, self.N, self.P = m, N, 4 * N
         self.storage = storage
@@ -197,7 +197,7 @@ class Population:
         self.pop = empty_population(storage, m, self.P, device)
         self.fit = torch.zeros(self.P, dtype=torch.int32, device=device)
         self.cfg = ga_config(m=m, NC=NC, N=N, seed=seed, pop_id=pop_id, NR=NR, fitness=fitness,
-                             storage=storage, path=path, traj_cap=traj_cap, reserved=0)
+                             storage=storage, path=path, traj_cap=traj_cap, mutation=mutation)
         ctx = ctypes.c_void_p()
         check(lib.ga_create(ctypes.byref(self.cfg), _ptr(self.pop), _ptr(self.fit),
                             ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(ctx)))

@@ -55,12 +55,12 @@ def test_version_and_storage_bytes(lib):
 
 
 @pytest.mark.parametrize("field,value", [("m", 18), ("m", 0), ("m", 260), ("N", 0), ("NC", 0), ("NR", 65),
-                                         ("fitness", 3), ("storage", 2), ("traj_cap", 0), ("reserved", 1),
+                                         ("fitness", 3), ("storage", 2), ("traj_cap", 0), ("mutation", 2), ("mutation", -1),
                                          ("path", 3)])
 def test_create_rejects_bad_config_without_gpu(lib, field, value):
     from paper_2208_14961_gb300 import hadga
     cfg = hadga.ga_config(m=20, NC=1, N=10, seed=0, pop_id=0, NR=1, fitness=0, storage=1, path=0,
-                          traj_cap=8, reserved=0)
+                          traj_cap=8, mutation=0)
     setattr(cfg, field, value)
     ctx = ctypes.c_void_p()
     buf = ctypes.c_void_p(0x1000)  # never dereferenced: validation fails first
@@ -84,7 +84,7 @@ def test_null_arguments(lib):
 def test_misaligned_buffers_rejected(lib):
     from paper_2208_14961_gb300 import hadga
     cfg = hadga.ga_config(m=20, NC=1, N=10, seed=0, pop_id=0, NR=1, fitness=0, storage=1, path=0,
-                          traj_cap=8, reserved=0)
+                          traj_cap=8, mutation=0)
     ctx = ctypes.c_void_p()
     st = lib.ga_create(ctypes.byref(cfg), ctypes.c_void_p(0x1004), ctypes.c_void_p(0x2000), None, ctypes.byref(ctx))
     assert st == hadga.GA_EINVAL and "aligned" in hadga.last_error()

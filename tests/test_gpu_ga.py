@@ -187,3 +187,29 @@ def test_config2_full_1000_generations_fused():
     h = need_gpu()
     gpu = _run_gpu(h, 20, 10000, 1, 1000, 1, "fused")
     _assert_same(gpu, _run_oracle(20, 10000, 1, 1000))
+
+
+@pytest.mark.parametrize("mode", ["plain", "fused"])
+@pytest.mark.parametrize("m,N,NC,NR,kind", [(12, 50, 1, 1, 2), (20, 64, 2, 3, 0), (36, 25, 1, 1, 0),
+                                            (100, 12, 3, 2, 1)])
+def test_mutation_method1_matches_oracle(mode, m, N, NC, NR, kind):
+    """Mutation method 1 of Sec. 3.5 (one draw shared by the generation's
+    offspring): plain and fused paths equal the oracle bit for bit."""
+    h = need_gpu()
+    gens, seed = 12, 8
+    pop = h.Population(m, N, seed=seed, NC=NC, NR=NR, fitness=kind, storage=1, traj_cap=gens, mutation=1)
+    pop.init_population()
+    pop.fitness()
+    if mode == "fused":
+        pop.step(gens)
+    else:
+        pop.step_plain(gens)
+    pop.sync()
+    ref = oracle.init_population(m, 4 * N, seed)
+    F = oracle.fitness(ref, kind)
+    _, tf, ts = oracle.run(ref, F, N, NC, NR, kind, seed, 0, 0, gens, shared_mutation=1)
+    assert np.array_equal(pop.as_int8(), ref)
+    assert np.array_equal(pop.fitness_host(), F)
+    gtf, gts = pop.trajectory()
+    assert np.array_equal(gtf.astype(np.uint64), tf) and np.array_equal(gts, ts)
+    pop.close()

@@ -112,3 +112,23 @@ def test_incremental_rejects_unsupported_contexts():
     with pytest.raises(h.GAError):
         pop.check_incremental()  # mode off
     pop.close()
+
+
+def test_incremental_with_mutation_method1():
+    """The incremental Gram path under mutation method 1 (the same flipped
+    column in every offspring of a generation)."""
+    h = need_gpu()
+    m, N, seed, gens = 64, 30, 9, 25
+    pop = h.Population(m, N, seed=seed, fitness=0, storage=1, traj_cap=gens, mutation=1)
+    pop.init_population()
+    pop.fitness()
+    pop.set_incremental(True)
+    pop.step(gens)
+    pop.sync()
+    ref = oracle.init_population(m, 4 * N, seed)
+    F = oracle.fitness(ref, 0)
+    oracle.run(ref, F, N, 1, 1, 0, seed, 0, 0, gens, shared_mutation=1)
+    assert np.array_equal(pop.as_int8(), ref)
+    assert np.array_equal(pop.fitness_host(), F)
+    assert pop.check_incremental() == (0, 0)
+    pop.close()

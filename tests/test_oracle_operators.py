@@ -142,3 +142,49 @@ def test_init_follows_fisher_yates_on_the_stream():
         v[i1], v[i2] = v[i2], v[i1]
     pop = oracle.init_population(m, 4, seed)
     assert list(pop[slot, :, j]) == v
+
+
+@pytest.mark.parametrize("m,N", [(8, 9), (12, 25), (20, 40)])
+def test_mutation_method1_one_draw_for_the_generation(m, N):
+    """Sec. 3.5, method 1: the same column and the same two rows for every
+    offspring of a generation, a pair switched only where its signs differ.
+    Checked from the definition: the flips of all offspring lie on one
+    column and one row pair, every offspring whose two entries differ there
+    is switched and every other one is unchanged, and the column and rows
+    are the first three words of stream (MUTATE, gen, 2N) mapped to
+    [1, m-1], [0, m-1], [0, m-1]."""
+    seed, pop_id, gen = 6, 1, 3
+    pop = oracle.init_population(m, 4 * N, seed, pop_id)
+    oracle.crossover(pop, N, seed, pop_id, gen)
+    before = pop.copy()
+    oracle.mutate(pop, N, 1, 1, seed, pop_id, gen, shared=1)
+    w = oracle.stream_words(seed, pop_id, oracle.OP_MUTATE, gen, 2 * N, 0, 3)
+    col = 1 + (int(w[0]) * (m - 1) >> 32)
+    r1 = int(w[1]) * m >> 32
+    r2 = int(w[2]) * m >> 32
+    assert np.array_equal(pop[:2 * N], before[:2 * N])
+    switched = 0
+    for o in range(2 * N, 4 * N):
+        a, b = before[o, r1, col], before[o, r2, col]
+        expect = before[o].copy()
+        if a != b:
+            expect[r1, col], expect[r2, col] = -a, -b
+            switched += 1
+        assert np.array_equal(pop[o], expect), o
+    assert switched > 0 or r1 == r2
+
+
+def test_mutation_method1_run_differs_from_method2():
+    """The two methods draw from different streams: same start, different
+    populations after a generation (and both keep every column balanced)."""
+    m, N, seed = 12, 30, 2
+    a = oracle.init_population(m, 4 * N, seed)
+    b = a.copy()
+    Fa = oracle.fitness(a, oracle.FIT_SQ)
+    Fb = Fa.copy()
+    oracle.run(a, Fa, N, 1, 1, oracle.FIT_SQ, seed, 0, 0, 3, shared_mutation=0)
+    oracle.run(b, Fb, N, 1, 1, oracle.FIT_SQ, seed, 0, 0, 3, shared_mutation=1)
+    assert not np.array_equal(a, b)
+    for pop in (a, b):
+        assert np.all(pop[:, :, 0] == 1)
+        assert np.all(pop[:, :, 1:].sum(axis=1) == 0)
