@@ -61,6 +61,20 @@ def _peaks():
 FUSED_M20_DRAM_BYTES_PER_LAUNCH = 3.464192e6
 
 
+def job_rate(local_time, units_per_rank, world, reduce_max=None, device=None):
+    """Whole-job throughput of `world` replica ranks: every rank processed
+    `units_per_rank` units in `local_time` (any time unit); the job takes as
+    long as its slowest rank, so the rate is world * units / max over ranks
+    of the time.  `reduce_max` is a collective MAX over ranks (None on one
+    rank).  Returns (rate per time unit, max time)."""
+    import torch
+    t = torch.tensor([float(local_time)], dtype=torch.float64, device=device)
+    if world > 1 and reduce_max is not None:
+        reduce_max(t)
+    slowest = float(t.item())
+    return world * units_per_rank / slowest, slowest
+
+
 def bytes_per_generation(m=M, N=N):
     """Algorithmic HBM bytes of one generation of the fused kernel (bit
     storage): read the 2N surviving parents, write all 4N slots (2N parents
@@ -626,11 +640,9 @@ def main():
     perm_ms, fused_ms, fused_launches = pop.profile_read()
     pop.profile(False)
     gens = args.steps * STEP_GENS
-    t = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    max_ms = float(t.item())
-    value = world * gens / (max_ms / 1e3)
+    reduce_max = (lambda x: dist.all_reduce(x, op=dist.ReduceOp.MAX)) if world > 1 else None
+    value, max_ms = job_rate(dev_ms / 1e3, gens, world, reduce_max, dev)
+    max_ms *= 1e3
 
     # ---- plain path (one kernel per operator), device-timed ------------------
     pl = h.Population(M, N, seed=SEED, pop_id=rank, NC=NC, NR=NR, fitness=h.FIT_SQ, storage=h.STORE_BITS,
@@ -678,10 +690,7 @@ def main():
         ee.trajectory()          # device -> host read of the step's result
     barrier()
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * args.steps * STEP_GENS / float(te.item())
+    e2e_value, _ = job_rate(e2e_s, args.steps * STEP_GENS, world, reduce_max, dev)
     ee.close()
 
     # ---- roofline of the persistent kernel --------------------------------------
