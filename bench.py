@@ -350,6 +350,17 @@ PAPER_TABLE_SECONDS = {20: (60.50, 59.38), 40: (103.15, 99.84), 60: (176.28, 170
                        80: (275.92, 256.59), 100: (416.68, 381.38)}
 
 
+def _popc_roof(gens_per_s, m, offspring):
+    """The generation rate against the population-count roof of its Gram
+    work: every offspring's m(m-1)/2 column pairs at popc_per_dot(m) counts
+    each, over the measured count rate of the peak microbenchmark."""
+    from paper_2208_14961_gb300 import peaks
+    peak = peaks.rate("popc_chain")
+    achieved = gens_per_s * offspring * (m * (m - 1) // 2) * popc_per_dot(m)
+    return {"bound": "alu", "unit": "popc/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
+            "work": "offspring Gram popcounts per generation", "peak_source": "measured (peaks microbenchmark)"}
+
+
 def table3_workload(args):
     """The paper's fitness-comparison workload (Sec. 4.2): m in {20, 40, 60,
     80, 100}, P = 40,000 balanced +-1 matrices (seed 5), NC = 4 columns and
@@ -403,7 +414,8 @@ def table3_workload(args):
                     "evals_per_s_paper_convention": gps * 4 * N, "fused_equals_plain_50": exact,
                     "best_fitness": int(best[1]),
                     "paper_rtx3080_generations_per_s": paper_gps,
-                    "over_paper": (gps / paper_gps) if paper_gps else None}
+                    "over_paper": (gps / paper_gps) if paper_gps else None,
+                    "roofline": _popc_roof(gps, m, 2 * N)}
             print(json.dumps(line), flush=True)
 
 
@@ -531,6 +543,7 @@ def incremental_workload(args):
             "oracle_prefix_generations": every, "exact_vs_oracle_prefix": exact_prefix,
             "trajectories_equal": bool(np.array_equal(trajs["incremental"], trajs["full"])),
             "best_fitness_at": {str(g): int(t[g - 1]) for g in sorted(set(marks))},
+            "roofline_full": _popc_roof(out["full"]["generations_per_s"], m, 2 * N),
             "gram_bytes": 4 * N * ((m * (m - 1) // 2 + 15) // 16 * 16),
             "l2": "not flushed; population 32 MB + Gram 99 MB resident across calls"}
     print(json.dumps(line), flush=True)
