@@ -406,7 +406,7 @@ static ga_status fused_run(ga_ctx *const *ctxs, int n, int32_t generations, int 
                            bool sync_gen = true, bool tail = true)
 {
     ga_ctx *c0 = ctxs[0];
-    FusedParams prm;
+    FusedParams prm{};
     memset(&prm, 0, sizeof(prm));
     prm.npop = n;
     uint32_t tiles = 0, tslots = 0, wpairs = 0;
