@@ -1054,10 +1054,10 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
     uint32_t *err = prm.err;
     uint32_t epoch = 0;
     uint32_t inc_parity = 0;  // phase of this warp's bulk-copy barrier
-    if (INC && tid < kFusedThreads / 32)
+    if (INC && tid < kFusedThreads / 32) {
         mbar_init(&s_incbar[tid], 1);
-    if (INC && tid == 0)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     int src = prm.src;
     int done = 0;
     auto tile_base = [&](int i) { return prm.p[i].tile_base; };
