@@ -188,6 +188,7 @@ def run_reference(args, rank, world):
 
 GRAM_PATHS = [  # name, storage, path
     ("int32", 0, 1), ("imma", 0, 2), ("popc_int8", 0, 5), ("popc_bits", 1, 5), ("fp8", 2, 3), ("bf16", 3, 4),
+    ("fp8_warp", 2, 6),
 ]
 
 
@@ -197,6 +198,24 @@ def popc_per_dot(m):
     3 at W = 4..7, 4 at W = 8)."""
     W = (m + 31) // 32
     return W if W <= 2 else 2 if W == 3 else 3 if W <= 7 else 4
+
+
+def peaks_report(args):
+    """The microbenchmark rates the roofline fractions use, plus SM count and
+    L2 size (one JSON line)."""
+    import torch
+
+    from paper_2208_14961_gb300 import peaks
+    prop = torch.cuda.get_device_properties(0)
+    r = {k: peaks.rate(k) for k in peaks.KINDS}
+    line = {"gpu": prop.name, "sms": prop.multi_processor_count,
+            "l2_bytes": getattr(prop, "L2_cache_size", None),
+            "popc_per_s": r["popc_chain"], "dp4a_per_s": r["dp4a"], "imad_per_s": r["imad"],
+            "mma_sync_s8_mac_per_s": r["imma_s8"], "mma_sync_e4m3_mac_per_s": r["mma_e4m3"],
+            "l2_read_bytes_per_s": r["l2_read_bytes"],
+            "grid_barrier_us": (1e6 / r["grid_barriers"]) if r["grid_barriers"] > 0 else None,
+            "hbm_gbs": _peaks()[0], "hbm_source": _peaks()[1]}
+    print(json.dumps(line), flush=True)
 
 
 def gram_sweep(args):
@@ -215,9 +234,10 @@ def gram_sweep(args):
     from paper_2208_14961_gb300 import peaks
 
     hbm, hbm_kind = _peaks()
-    rates = {k: peaks.rate(k) for k in ("popc_chain", "dp4a", "imma_s8")}
+    rates = {k: peaks.rate(k) for k in ("popc_chain", "dp4a", "mma_e4m3")}
     print(json.dumps({"peaks": {"hbm_gbs": hbm, "hbm_source": hbm_kind, "popc_per_s": rates["popc_chain"],
-                                "dp4a_per_s": rates["dp4a"], "imma_s8_mac_per_s": rates["imma_s8"]}}), flush=True)
+                                "dp4a_per_s": rates["dp4a"], "mma_sync_e4m3_mac_per_s": rates["mma_e4m3"]}}),
+          flush=True)
     rng = np.random.default_rng(7)
     for m in [int(x) for x in args.gram_ms.split(",")]:
         P = int(args.gram_gb * (1 << 30)) // (m * m)
@@ -264,14 +284,14 @@ def gram_sweep(args):
                 ops, peak, unit = P * D * popc_per_dot(m), rates["popc_chain"], "popc"
             elif name == "int32":
                 ops, peak, unit = P * D * (m // 4), rates["dp4a"], "dp4a"
-            elif name == "imma" and m % 32 == 0:
+            elif name in ("imma", "fp8_warp") and m % 32 == 0:
                 mt, ct, ks = m // 16, m // 8, m // 32
                 tiles = sum(ct - 2 * ri for ri in range(mt))
-                ops, peak, unit = P * tiles * ks * 4096, rates["imma_s8"], "s8 MAC"
+                ops, peak, unit = P * tiles * ks * 4096, rates["mma_e4m3"], "e4m3 MAC"
             else:
                 ops, peak, unit = None, None, None
             t_cmp = ops / peak if ops else 0.0
-            bound = "hbm" if t_mem >= t_cmp else "alu" if name != "imma" else "tensor"
+            bound = "hbm" if t_mem >= t_cmp else "alu" if name not in ("imma", "fp8_warp") else "tensor"
             roof_t = max(t_mem, t_cmp)
             line = {"m": m, "path": name, "P": P, "storage_gib": nbytes / (1 << 30), "ms": sec * 1e3,
                     "matrices_per_s": P / sec, "achieved_gbs": nbytes / sec / 1e9, "bound": bound,
@@ -569,12 +589,16 @@ def main():
     ap.add_argument("--table3", action="store_true", help="the paper's fitness-comparison workload (Sec. 4.2)")
     ap.add_argument("--t3-ms", default="20,40,60,80,100")
     ap.add_argument("--t3-gens", type=int, default=1000)
+    ap.add_argument("--peaks", action="store_true", help="microbenchmark rates used by the roofline fractions")
     ap.add_argument("--search", action="store_true", help="time to a Hadamard matrix (the paper's Sec. 4.4 runs)")
     ap.add_argument("--search-ms", default="20,24,28")
     ap.add_argument("--search-seeds", type=int, default=3)
     ap.add_argument("--search-seconds", type=float, default=60.0)
     ap.add_argument("--search-chunk", type=int, default=2048)
     args = ap.parse_args()
+    if args.peaks:
+        peaks_report(args)
+        return
     if args.gram_sweep:
         gram_sweep(args)
         return

@@ -74,10 +74,12 @@ typedef enum {
 typedef enum {
     GA_PATH_AUTO = 0,   /* fastest measured exact path for storage, m and fitness */
     GA_PATH_INT32 = 1,  /* int8 storage, CUDA-core 8-bit dot products */
-    GA_PATH_IMMA = 2,   /* int8 storage, warp-level int8 tensor-core MMA */
+    GA_PATH_IMMA = 2,   /* int8 storage, warp-level tensor-core MMA (mma.sync with FP8
+                           operands converted from the int8 signs, FP32 accumulate) */
     GA_PATH_FP8 = 3,    /* e4m3 storage, tcgen05 tensor cores, FP32 accumulate */
     GA_PATH_BF16 = 4,   /* bf16 storage, tcgen05 tensor cores, FP32 accumulate */
-    GA_PATH_POPC = 5    /* bits (or int8) storage, XOR + population count */
+    GA_PATH_POPC = 5,   /* bits (or int8) storage, XOR + population count */
+    GA_PATH_FP8_WARP = 6 /* e4m3 storage, warp-level FP8 tensor-core MMA (mma.sync), FP32 accumulate */
 } ga_gram_path;
 
 typedef struct {

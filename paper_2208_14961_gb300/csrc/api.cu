@@ -124,14 +124,16 @@ ga_status check_storage_m(ga_ctx *c, int32_t storage, int32_t m)
 constexpr int kChunk = 64;
 
 // GA_PATH_AUTO by storage, order and fitness, from the measured Gram sweep
-// on GB300 (8 and 32 GiB populations, m = 32..256): bit storage always takes
-// popcount; int8 takes the int8 tensor-core row Gram for F_sq up to m = 128
-// (at m = 256 the legacy int8 MMA rate falls behind popcount) and popcount
-// otherwise; e4m3 / bf16 storage take the tcgen05 paths.
+// on GB300 (8 GiB populations, m = 32..256): bit storage always takes
+// popcount; int8 takes the warp-level tensor-core row Gram (FP8 operands
+// from the int8 signs) for F_sq up to m = 128 and popcount otherwise; e4m3
+// storage takes the tcgen05 path for F_sq at m = 128 and 256 and the
+// warp-level FP8 MMA otherwise (HBM-bound at m <= 64; F1 / F2; orders the
+// tcgen05 kernel does not tile); bf16 storage takes tcgen05.
 int auto_path(int storage, int m, int kind)
 {
     if (storage == GA_STORE_E4M3)
-        return GA_PATH_FP8;
+        return (kind == GA_FIT_SQ && (m == 128 || m == 256)) ? GA_PATH_FP8 : GA_PATH_FP8_WARP;
     if (storage == GA_STORE_BF16)
         return GA_PATH_BF16;
     if (storage == GA_STORE_INT8 && kind == GA_FIT_SQ && m % 32 == 0 && m <= 128)
@@ -1043,7 +1045,7 @@ ga_status ga_fitness_batch(const void *pop_dev, int32_t storage, int32_t m, int6
         return cuda_check(nullptr, launch_fitness_tc(pop_dev, storage, m, 0, P, kind, fit_dev, nullptr, s),
                           "tensor-core fitness");
     }
-    if (path < GA_PATH_AUTO || path > GA_PATH_POPC || !fitness_path_supported(storage, m, path))
+    if (path < GA_PATH_AUTO || path > GA_PATH_FP8_WARP || !fitness_path_supported(storage, m, path))
         return set_error(nullptr, GA_EINVAL, "path %d does not read storage %d", path, storage);
     return cuda_check(nullptr, launch_fitness(pop_dev, storage, m, 0, P, kind, path, fit_dev, s), "fitness");
 }

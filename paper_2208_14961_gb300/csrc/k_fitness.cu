@@ -183,17 +183,41 @@ __global__ void __launch_bounds__(128) k_fit_int8_dp4a(const int8_t *__restrict_
 }
 
 // ---------------------------------------------------------------------------
-// IMMA: mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32
-// A (16x32, row) = rows i0.. of T, B (32x8, col) = rows j0.. of T: both read
-// 4 consecutive k bytes of one T row per register.
+// Warp-level tensor-core MMA on +-1 data:
+// mma.sync.aligned.m16n8k32.row.col.f32.e4m3.e4m3.f32.  +-1 is exact in FP8
+// e4m3 (0x38 / 0xB8) and every Gram entry (|G| <= 256) is exact in the FP32
+// accumulator.  On this GPU the FP8 form of the warp-level MMA issues at
+// about 14x the rate of the int8 (s8) form (peaks microbenchmark: 1.09 P vs
+// 76 T multiply-adds/s), so int8 +-1 storage is fed to it through a sign
+// conversion: byte x in {0x01, 0xFF} -> 0x38 | (x & 0x80).
+// A (16x32, row) and B (32x8, col) registers hold 4 consecutive k elements.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void mma_s8_16832(int (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
+__device__ __forceinline__ void mma_e4m3_16832(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
 {
-    asm volatile("mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 "
+    asm volatile("mma.sync.aligned.m16n8k32.row.col.f32.e4m3.e4m3.f32 "
                  "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-                 : "+r"(d[0]), "+r"(d[1]), "+r"(d[2]), "+r"(d[3])
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
                  : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
+
+// Four int8 +-1 entries -> four e4m3 +-1 entries.
+__device__ __forceinline__ uint32_t i8pm1_to_e4m3(uint32_t x) { return (x & 0x80808080u) | 0x38383838u; }
+
+// The same, keeping zero bytes (padding) zero.
+__device__ __forceinline__ uint32_t i8_to_e4m3_z(uint32_t x)
+{
+    return ((x & 0x80808080u) | 0x38383838u) & __vcmpne4(x, 0u);
+}
+
+// Operand register of the row-Gram kernels: int8 storage converted, e4m3
+// storage as is.
+template <bool E4M3>
+__device__ __forceinline__ uint32_t fp8_operand(uint32_t x)
+{
+    return E4M3 ? x : i8pm1_to_e4m3(x);
+}
+
+__device__ __forceinline__ int gram_value(float d) { return __float2int_rn(d); }
 
 template <int KIND>
 __global__ void __launch_bounds__(128) k_fit_int8_imma(const int8_t *__restrict__ pop, int m, int64_t first,
@@ -212,25 +236,25 @@ __global__ void __launch_bounds__(128) k_fit_int8_imma(const int8_t *__restrict_
         for (int i0 = 0; i0 < mpad; i0 += 16) {
             // only column tiles that reach above the diagonal of this row tile
             for (int j0 = i0 & ~7; j0 < mpad; j0 += 8) {
-                int d[4] = {0, 0, 0, 0};
+                float d[4] = {0.f, 0.f, 0.f, 0.f};
                 for (int k0 = 0; k0 < kpad; k0 += 32) {
                     uint32_t a[4], b[2];
                     const int8_t *ta = T + (i0 + grp) * ts + k0 + tig * 4;
-                    a[0] = *reinterpret_cast<const uint32_t *>(ta);
-                    a[1] = *reinterpret_cast<const uint32_t *>(ta + 8 * ts);
-                    a[2] = *reinterpret_cast<const uint32_t *>(ta + 16);
-                    a[3] = *reinterpret_cast<const uint32_t *>(ta + 8 * ts + 16);
+                    a[0] = i8_to_e4m3_z(*reinterpret_cast<const uint32_t *>(ta));
+                    a[1] = i8_to_e4m3_z(*reinterpret_cast<const uint32_t *>(ta + 8 * ts));
+                    a[2] = i8_to_e4m3_z(*reinterpret_cast<const uint32_t *>(ta + 16));
+                    a[3] = i8_to_e4m3_z(*reinterpret_cast<const uint32_t *>(ta + 8 * ts + 16));
                     const int8_t *tb = T + (j0 + grp) * ts + k0 + tig * 4;
-                    b[0] = *reinterpret_cast<const uint32_t *>(tb);
-                    b[1] = *reinterpret_cast<const uint32_t *>(tb + 16);
-                    mma_s8_16832(d, a, b);
+                    b[0] = i8_to_e4m3_z(*reinterpret_cast<const uint32_t *>(tb));
+                    b[1] = i8_to_e4m3_z(*reinterpret_cast<const uint32_t *>(tb + 16));
+                    mma_e4m3_16832(d, a, b);
                 }
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const int i = i0 + grp + ((e >> 1) << 3);
                     const int j = j0 + tig * 2 + (e & 1);
                     if (i < j && j < m)
-                        acc += fit_term<KIND>(d[e]);
+                        acc += fit_term<KIND>(gram_value(d[e]));
                 }
             }
         }
@@ -254,10 +278,31 @@ __global__ void __launch_bounds__(128) k_fit_int8_imma(const int8_t *__restrict_
 // fully coalesced.
 // ---------------------------------------------------------------------------
 
+// Sum over the upper-triangle entries of one 16 x 8 accumulator tile of the
+// row Gram: d^2 in FP32, exact while a lane's sum stays below 2^24 (at most
+// 4 * tiles_per_lane * m^2 = 4 * 34 * 65536 < 2^24 for m <= 256).  Only the
+// two tiles on the diagonal (cj = 2 ri, 2 ri + 1) need the entry mask.
+__device__ __forceinline__ float tile_sq_sum(const float (&d)[4], int ri, int cj, int grp, int tig, float acc)
+{
+    if (cj >= 2 * ri + 2) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            acc = fmaf(d[e], d[e], acc);
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int r = 16 * ri + grp + ((e >> 1) << 3);
+            const int c = 8 * cj + tig * 2 + (e & 1);
+            acc = fmaf(c > r ? d[e] : 0.f, d[e], acc);
+        }
+    }
+    return acc;
+}
+
 // m in {32, 64}: one warp per matrix, the whole matrix in registers
 // (lane (g, t) holds rows g + 8q, q < m/8, bytes 8t..8t+7 of every 32-byte
 // k step).
-template <int M>
+template <int M, bool E4M3>
 __global__ void __launch_bounds__(256) k_fsq_imma_regs(const int8_t *__restrict__ pop, int64_t first, int64_t count,
                                                       uint32_t *__restrict__ fit)
 {
@@ -281,30 +326,25 @@ __global__ void __launch_bounds__(256) k_fsq_imma_regs(const int8_t *__restrict_
         const int64_t qn = q + nw;
         if (qn < first + count)
             load(qn, nxt);
-        uint32_t acc = 0;
+        float acc = 0.f;  // exact: at most 4 * 20 entries of m^2 = 4096 per lane
 #pragma unroll
         for (int ri = 0; ri < MT; ++ri) {
 #pragma unroll
             for (int cj = 2 * ri; cj < RG; ++cj) {
-                int d[4] = {0, 0, 0, 0};
+                float d[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
                 for (int ks = 0; ks < KS; ++ks) {
-                    const uint32_t a[4] = {cur[2 * ri][ks].x, cur[2 * ri + 1][ks].x, cur[2 * ri][ks].y,
-                                           cur[2 * ri + 1][ks].y};
-                    const uint32_t b[2] = {cur[cj][ks].x, cur[cj][ks].y};
-                    mma_s8_16832(d, a, b);
+                    const uint32_t a[4] = {fp8_operand<E4M3>(cur[2 * ri][ks].x), fp8_operand<E4M3>(cur[2 * ri + 1][ks].x),
+                                           fp8_operand<E4M3>(cur[2 * ri][ks].y), fp8_operand<E4M3>(cur[2 * ri + 1][ks].y)};
+                    const uint32_t b[2] = {fp8_operand<E4M3>(cur[cj][ks].x), fp8_operand<E4M3>(cur[cj][ks].y)};
+                    mma_e4m3_16832(d, a, b);
                 }
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int r = 16 * ri + grp + ((e >> 1) << 3);
-                    const int c = 8 * cj + tig * 2 + (e & 1);
-                    acc += c > r ? (uint32_t)(d[e] * d[e]) : 0u;
-                }
+                acc = tile_sq_sum(d, ri, cj, grp, tig, acc);
             }
         }
-        acc = warp_sum(acc);
+        const uint32_t f = warp_sum((uint32_t)acc);
         if (lane == 0)
-            fit[q] = acc;
+            fit[q] = f;
 #pragma unroll
         for (int r = 0; r < RG; ++r)
 #pragma unroll
@@ -317,52 +357,108 @@ __global__ void __launch_bounds__(256) k_fsq_imma_regs(const int8_t *__restrict_
 // staged in shared memory with rows padded by 32 bytes (a half-warp's 8-byte
 // reads of 4 rows then cover all 32 banks), the upper-triangle 16 x 8 tiles
 // of R dealt round-robin to the warps.
-__global__ void __launch_bounds__(128) k_fsq_imma_smem(const int8_t *__restrict__ pop, int m, int64_t first,
-                                                       int64_t count, uint32_t *__restrict__ fit)
+// One 16-byte asynchronous copy global -> shared (cp.async.cg: through L2).
+__device__ __forceinline__ void cp_async16_g2s(void *smem_dst, const void *gmem_src)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+
+constexpr int kMmaSmemThreads = 256;  // 8 warps per block
+
+// m in {96, 128, ..., 256} (multiple of 32): one matrix per block at a time,
+// staged in shared memory with padded rows (stride m + 32 bytes); two
+// buffers, the next matrix's rows arriving by cp.async while the current
+// one is multiplied.  Each warp takes a contiguous range of the upper tiles
+// (16 rows x 8 rows of the row Gram) in row-block order and keeps the A
+// fragments of a row block in registers across its tiles: one shared-memory
+// operand load per MMA.
+template <int M, bool E4M3>
+__global__ void __launch_bounds__(kMmaSmemThreads) k_fsq_imma_smem(const int8_t *__restrict__ pop, int64_t first,
+                                                                  int64_t count, uint32_t *__restrict__ fit)
 {
     extern __shared__ __align__(16) uint8_t s_q[];
-    __shared__ uint32_t s_part[4];
+    __shared__ uint32_t s_part[kMmaSmemThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, grp = lane >> 2, tig = lane & 3;
-    const int rs = m + 32;  // padded row stride in bytes
-    const int KS = m / 32, MT = m / 16, CT = m / 8;
-    for (int64_t q = first + blockIdx.x; q < first + count; q += gridDim.x) {
-        const uint4 *src = reinterpret_cast<const uint4 *>(pop + (size_t)q * m * m);
-        const int chunks = m * m / 16, per_row = m / 16;
-        for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
-            const int r = c / per_row, w = c % per_row;
-            *reinterpret_cast<uint4 *>(s_q + r * rs + w * 16) = __ldg(src + c);
+    constexpr int NW = kMmaSmemThreads / 32;
+    constexpr int RS = M + 32;  // padded row stride in bytes
+    constexpr int KS = M / 32, MT = M / 16, CT = M / 8;
+    constexpr int T = MT * CT - MT * (MT - 1);  // upper tiles
+    constexpr size_t BSZ = (size_t)M * RS;
+    constexpr int CHUNKS = M * M / 16, PER_ROW = M / 16;
+    auto issue = [&](int64_t q, int b) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(pop + (size_t)q * M * M);
+        uint8_t *dst = s_q + (size_t)b * BSZ;
+        for (int c = threadIdx.x; c < CHUNKS; c += blockDim.x)
+            cp_async16_g2s(dst + (c / PER_ROW) * RS + (c % PER_ROW) * 16, src + c);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    // this warp's tiles [t0, t1) and the (ri, cj) of t0
+    const int t0 = warp * T / NW, t1 = (warp + 1) * T / NW;
+    int ri0 = 0, before = 0;
+    while (before + (CT - 2 * ri0) <= t0) {
+        before += CT - 2 * ri0;
+        ++ri0;
+    }
+    const int cj0 = 2 * ri0 + (t0 - before);
+    const int64_t end = first + count;
+    int64_t q = first + blockIdx.x;
+    int buf = 0;
+    if (q < end)
+        issue(q, buf);
+    for (; q < end; q += gridDim.x) {
+        const int64_t qn = q + gridDim.x;
+        if (qn < end) {
+            issue(qn, buf ^ 1);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
         __syncthreads();
-        uint32_t acc = 0;
-        int tile = 0;
-        for (int ri = 0; ri < MT; ++ri) {
-            for (int cj = 2 * ri; cj < CT; ++cj, ++tile) {
-                if ((tile & 3) != warp)
-                    continue;
-                int d[4] = {0, 0, 0, 0};
-                for (int ks = 0; ks < KS; ++ks) {
-                    const uint2 a0 = *reinterpret_cast<const uint2 *>(s_q + (16 * ri + grp) * rs + ks * 32 + tig * 8);
-                    const uint2 a1 =
-                        *reinterpret_cast<const uint2 *>(s_q + (16 * ri + grp + 8) * rs + ks * 32 + tig * 8);
-                    const uint2 b0 = *reinterpret_cast<const uint2 *>(s_q + (8 * cj + grp) * rs + ks * 32 + tig * 8);
-                    const uint32_t a[4] = {a0.x, a1.x, a0.y, a1.y};
-                    const uint32_t b[2] = {b0.x, b0.y};
-                    mma_s8_16832(d, a, b);
-                }
+        const uint8_t *Q = s_q + (size_t)buf * BSZ + grp * RS + tig * 8;
+        float acc = 0.f;
+        uint32_t a[KS][4];
+        int ri = ri0, cj = cj0, a_ri = -1;
+        for (int t = t0; t < t1; ++t) {
+            if (a_ri != ri) {
+                const uint8_t *qa = Q + 16 * ri * RS;
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int r = 16 * ri + grp + ((e >> 1) << 3);
-                    const int c = 8 * cj + tig * 2 + (e & 1);
-                    acc += c > r ? (uint32_t)(d[e] * d[e]) : 0u;
+                for (int ks = 0; ks < KS; ++ks) {
+                    const uint2 a0 = *reinterpret_cast<const uint2 *>(qa + ks * 32);
+                    const uint2 a1 = *reinterpret_cast<const uint2 *>(qa + 8 * RS + ks * 32);
+                    a[ks][0] = fp8_operand<E4M3>(a0.x);
+                    a[ks][1] = fp8_operand<E4M3>(a1.x);
+                    a[ks][2] = fp8_operand<E4M3>(a0.y);
+                    a[ks][3] = fp8_operand<E4M3>(a1.y);
                 }
+                a_ri = ri;
+            }
+            float d[4] = {0.f, 0.f, 0.f, 0.f};
+            const uint8_t *qb = Q + 8 * cj * RS;
+#pragma unroll
+            for (int ks = 0; ks < KS; ++ks) {
+                const uint2 b0 = *reinterpret_cast<const uint2 *>(qb + ks * 32);
+                const uint32_t b[2] = {fp8_operand<E4M3>(b0.x), fp8_operand<E4M3>(b0.y)};
+                mma_e4m3_16832(d, a[ks], b);
+            }
+            acc = tile_sq_sum(d, ri, cj, grp, tig, acc);
+            if (++cj == CT) {
+                ++ri;
+                cj = 2 * ri;
             }
         }
-        acc = warp_sum(acc);
+        // the lane sum is an exact integer below 2^24; reduce in integers
+        const uint32_t wsum = warp_sum((uint32_t)acc);
         if (lane == 0)
-            s_part[warp] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0)
-            fit[q] = s_part[0] + s_part[1] + s_part[2] + s_part[3];
+            s_part[warp] = wsum;
+        __syncthreads();  // also: every warp is done with `buf` before it is refilled
+        if (threadIdx.x == 0) {
+            uint32_t f = 0;
+            for (int w = 0; w < NW; ++w)
+                f += s_part[w];
+            fit[q] = f;
+        }
+        buf ^= 1;
     }
 }
 
@@ -415,6 +511,8 @@ bool fitness_path_supported(int storage, int m, int path)
         return storage == ST_BITS || storage == ST_INT8;
     if (path == 1 || path == 2)
         return storage == ST_INT8;
+    if (path == 6)
+        return storage == ST_E4M3;
     return false;
 }
 
@@ -426,6 +524,20 @@ static int grid_for_warps(int64_t count, int warps_per_block)
     const int64_t want = (count + warps_per_block - 1) / warps_per_block;
     const int64_t cap = (int64_t)(sms > 0 ? sms : 148) * 64;
     return (int)(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+template <int M, bool E4M3>
+static void launch_fsq_mma_smem(const int8_t *pop, int64_t first, int64_t count, uint32_t *fit, size_t smem, int sms,
+                                cudaStream_t s)
+{
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_fsq_imma_smem<M, E4M3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // as many resident blocks as shared memory allows, each looping over matrices
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fsq_imma_smem<M, E4M3>, kMmaSmemThreads, smem);
+    const int64_t cap = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+    const int64_t want = count < cap ? count : cap;
+    k_fsq_imma_smem<M, E4M3><<<(unsigned)(want > 0 ? want : 1), kMmaSmemThreads, smem, s>>>(pop, first, count, fit);
 }
 
 template <int KIND>
@@ -478,24 +590,39 @@ static cudaError_t fitness_kind(const void *pop, int storage, int m, int64_t fir
         return cudaGetLastError();
     }
     // F_sq on int8: row-Gram kernels (no transpose)
-    if (KIND == FIT_SQ && path == 2 && (m == 32 || m == 64)) {
+    // paths 2 (int8 storage) and 6 (e4m3 storage): warp-level FP8 MMA
+    const bool fp8 = path == 6;
+    if (KIND == FIT_SQ && (path == 2 || path == 6) && (m == 32 || m == 64)) {
         const int grid = grid_for_warps(count, 8);
+        const int8_t *q = (const int8_t *)pop;
         if (m == 32)
-            k_fsq_imma_regs<32><<<grid, 256, 0, s>>>((const int8_t *)pop, first, count, fit);
+            fp8 ? k_fsq_imma_regs<32, true><<<grid, 256, 0, s>>>(q, first, count, fit)
+                : k_fsq_imma_regs<32, false><<<grid, 256, 0, s>>>(q, first, count, fit);
         else
-            k_fsq_imma_regs<64><<<grid, 256, 0, s>>>((const int8_t *)pop, first, count, fit);
+            fp8 ? k_fsq_imma_regs<64, true><<<grid, 256, 0, s>>>(q, first, count, fit)
+                : k_fsq_imma_regs<64, false><<<grid, 256, 0, s>>>(q, first, count, fit);
         note_launches(1);
         return cudaGetLastError();
     }
-    if (KIND == FIT_SQ && path == 2 && m % 32 == 0) {
-        const size_t smem = (size_t)m * (m + 32);
+    if (KIND == FIT_SQ && (path == 2 || path == 6) && m % 32 == 0) {
+        const size_t smem = 2 * (size_t)m * (m + 32);  // two staging buffers
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(k_fsq_imma_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        const int64_t want = count < (int64_t)sms * 16 ? count : (int64_t)sms * 16;
-        k_fsq_imma_smem<<<(unsigned)(want > 0 ? want : 1), 128, smem, s>>>((const int8_t *)pop, m, first, count, fit);
+        const int8_t *q = (const int8_t *)pop;
+        switch (m) {
+#define HADGA_MS(MM)                                                                                         \
+    case MM:                                                                                                 \
+        if (fp8)                                                                                             \
+            launch_fsq_mma_smem<MM, true>(q, first, count, fit, smem, sms, s);                               \
+        else                                                                                                 \
+            launch_fsq_mma_smem<MM, false>(q, first, count, fit, smem, sms, s);                              \
+        break;
+            HADGA_MS(96) HADGA_MS(128) HADGA_MS(160) HADGA_MS(192) HADGA_MS(224) HADGA_MS(256)
+#undef HADGA_MS
+        default:
+            return cudaErrorInvalidValue;
+        }
         note_launches(1);
         return cudaGetLastError();
     }

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libhadga.so")
 GA_OK, GA_EINVAL, GA_ENOMEM, GA_ECUDA, GA_ETIMEOUT, GA_EUNSUPPORTED = range(6)
 FIT_SQ, FIT_ABS, FIT_NNZ = 0, 1, 2
 STORE_INT8, STORE_BITS, STORE_E4M3, STORE_BF16 = 0, 1, 2, 3
-PATH_AUTO, PATH_INT32, PATH_IMMA, PATH_FP8, PATH_BF16, PATH_POPC = range(6)
+PATH_AUTO, PATH_INT32, PATH_IMMA, PATH_FP8, PATH_BF16, PATH_POPC, PATH_FP8_WARP = range(7)
 
 _STATUS_NAMES = {0: "GA_OK", 1: "GA_EINVAL", 2: "GA_ENOMEM", 3: "GA_ECUDA", 4: "GA_ETIMEOUT",
                  5: "GA_EUNSUPPORTED"}

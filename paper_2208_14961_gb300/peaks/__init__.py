@@ -7,7 +7,8 @@ import subprocess
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = os.path.join(os.path.dirname(_HERE), "_build", "libpeaks.so")
 
-KINDS = {"popc": 0, "popc_chain": 1, "dp4a": 2, "imma_s8": 3}
+KINDS = {"popc": 0, "popc_chain": 1, "dp4a": 2, "imma_s8": 3, "imad": 4, "mma_e4m3": 5, "l2_read_bytes": 6,
+         "grid_barriers": 7}
 
 
 def build():
@@ -15,8 +16,8 @@ def build():
     if os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(src):
         return _LIB
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-Xcompiler", "-fPIC", "-shared",
-                    "-o", _LIB, src], check=True)
+    subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
+                    "-shared", "-I", os.path.join(os.path.dirname(_HERE), "csrc"), "-o", _LIB, src], check=True)
     return _LIB
 
 

@@ -31,7 +31,7 @@ def test_init_matches_oracle(m, storage):
 
 
 @pytest.mark.parametrize("m", [4, 8, 12, 16, 20, 24, 28, 32, 36, 64, 100, 128, 256])
-@pytest.mark.parametrize("path,storage", [(5, 1), (5, 0), (1, 0), (2, 0)])
+@pytest.mark.parametrize("path,storage", [(5, 1), (5, 0), (1, 0), (2, 0), (6, 2)])
 def test_fitness_paths_match_oracle(m, path, storage):
     h = need_gpu()
     P = 45 if m <= 64 else 11
@@ -62,7 +62,7 @@ def test_popc_word_counts_match_oracle(m, storage):
         assert np.array_equal(fit_u64(fit), oracle.fitness(host, kind)), (m, storage, kind)
 
 
-@pytest.mark.parametrize("path,storage", [(5, 1), (5, 0), (1, 0), (2, 0)])
+@pytest.mark.parametrize("path,storage", [(5, 1), (5, 0), (1, 0), (2, 0), (6, 2)])
 def test_known_hadamard_matrices_score_zero(path, storage):
     h = need_gpu()
     mats = [sylvester(m) for m in (4, 8, 16, 32, 64, 128, 256)] + [paley1(q) for q in (11, 19, 23, 43)]
