@@ -9,7 +9,7 @@ inc_m100    m=100, P=20,000, bit storage, incremental Gram-delta fitness:
             init, fitness, Gram store, then `generations` generations
 full_m100   the same workload with full fitness recomputation
 gram_m<M>_<path>  Gram + fitness of a population of ~1 GiB (int8 size) at
-            order M with path int32 | imma | popc8 | popc | fp8 | bf16
+            order M with path int32 | imma | popc8 | popc | fp8 | bf16 | fp8w
 """
 import sys
 
@@ -49,7 +49,8 @@ def main(argv):
         m = int(m_s)
         paths = {"int32": (h.STORE_INT8, h.PATH_INT32), "imma": (h.STORE_INT8, h.PATH_IMMA),
                  "popc8": (h.STORE_INT8, h.PATH_POPC), "popc": (h.STORE_BITS, h.PATH_POPC),
-                 "fp8": (h.STORE_E4M3, h.PATH_FP8), "bf16": (h.STORE_BF16, h.PATH_BF16)}
+                 "fp8": (h.STORE_E4M3, h.PATH_FP8), "bf16": (h.STORE_BF16, h.PATH_BF16),
+                 "fp8w": (h.STORE_E4M3, h.PATH_FP8_WARP)}
         storage, path = paths[path_s]
         P = (1 << 30) // (m * m)
         pop = h.empty_population(storage, m, P)
