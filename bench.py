@@ -741,6 +741,19 @@ def main():
                 "traffic": FUSED_M20_DRAM_BYTES_PER_LAUNCH, "kernel": "k_fused", "peak_source": peak_kind,
                 "launch_ms": per_launch_ms, "perm_table_ms_per_launch": perm_ms / max(fused_launches, 1)}
 
+    # what binds instead of HBM: the two grid barriers of every generation
+    sync = None
+    try:
+        from paper_2208_14961_gb300 import peaks
+        bps = peaks.rate("grid_barriers")
+        if bps > 0 and fused_launches > 0:
+            gen_us = fused_ms / fused_launches / STEP_GENS * 1e3
+            sync = {"grid_barrier_us": 1e6 / bps, "barriers_per_generation": 2, "generation_us": gen_us,
+                    "barrier_share": 2e6 / bps / gen_us,
+                    "note": "grid barrier latency from the peaks microbenchmark (same barrier code, 152 blocks)"}
+    except Exception as e:  # the context field must not break the bench line
+        sync = {"error": str(e)[:200]}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         gps, ngen, dt, cores = oracle_sample()
@@ -763,6 +776,7 @@ def main():
             "e2e": {"value": e2e_value, "unit": "generations/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "roofline": roof,
+            "sync_bound": sync,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "gpu_launches": int(launches),
