@@ -157,3 +157,43 @@ def test_set_get_slot_and_best():
     assert np.array_equal(pop.get_slot(17), H)
     pop.fitness()
     assert pop.best() == (17, 0)
+
+
+@pytest.mark.parametrize("m", [32, 64, 128, 256])
+def test_config3_full_size_sampled(m):
+    """The precision sweep's workload at full size: P = 8 GiB / m^2 balanced
+    matrices (seed 2), every Gram path on its own storage, the launch shapes
+    the sweep times; 48 seeded slots checked against the oracle one by one
+    (the same matrices in every storage: the init writes the same content)."""
+    h = need_gpu()
+    P = (8 << 30) // (m * m)
+    rng = np.random.default_rng(m)
+    idx = np.sort(rng.choice(P, size=48, replace=False))
+    sample = np.zeros((len(idx), m, m), dtype=np.int8)
+    pop = h.empty_population(0, m, P)
+    h.ga_init_batch(pop, 0, m, P, 2)
+    torch.cuda.synchronize()
+    sample[:] = pop.index_select(0, torch.as_tensor(idx, device="cuda")).cpu().numpy()
+    del pop
+    torch.cuda.empty_cache()
+    expected = oracle.fitness(sample, oracle.FIT_SQ)
+    for path, storage in ((1, 0), (2, 0), (5, 0), (5, 1), (3, 2), (6, 2), (4, 3)):
+        pop = h.empty_population(storage, m, P)
+        h.ga_init_batch(pop, storage, m, P, 2)
+        fit = torch.zeros(P, dtype=torch.int32, device="cuda")
+        h.ga_fitness_batch(pop, storage, m, P, 0, path, fit)
+        got = fit.index_select(0, torch.as_tensor(idx, device="cuda")).cpu().numpy().view(np.uint32)
+        assert np.array_equal(got.astype(np.uint64), expected), (m, path, storage)
+        del pop, fit
+        torch.cuda.empty_cache()
+
+
+def test_empty_batches_are_no_ops():
+    h = need_gpu()
+    for storage in (0, 1, 2, 3):
+        pop = h.empty_population(storage, 32, 1)
+        fit = torch.full((1,), 7, dtype=torch.int32, device="cuda")
+        h.ga_init_batch(pop, storage, 32, 0, 1)
+        h.ga_fitness_batch(pop, storage, 32, 0, 0, 0, fit)
+        torch.cuda.synchronize()
+        assert int(fit[0]) == 7
