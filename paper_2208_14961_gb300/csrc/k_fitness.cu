@@ -10,9 +10,12 @@
 //             become one column word per __ballot_sync, then as above.
 //  * INT32 -- int8 storage, CUDA-core 4-way byte dot products (__dp4a) on a
 //             transposed copy in shared memory.
-//  * IMMA  -- int8 storage, warp-level mma.sync m16n8k32 s8 x s8 -> s32 on
-//             the same transposed copy (both Gram operands read Q^T with the
-//             row index contiguous).
+//  * IMMA  -- int8 storage, warp-level mma.sync m16n8k32 on the same
+//             transposed copy (both Gram operands read Q^T with the row index
+//             contiguous); the int8 signs are turned into FP8 e4m3 operands
+//             (+-1 exact) and accumulated in FP32, exact for |G| <= 256.
+//  * FP8_WARP -- e4m3 storage, the same warp-level MMA reading the stored
+//             bytes directly (shared-memory tiles, cp.async double buffering).
 // The pairs i < j of a warp's matrix are enumerated without a table: lane
 // a pairs column a with (a + s) mod m for s = 1 .. m/2, the s = m/2 pair only
 // when a < m/2, which visits each unordered pair exactly once.
