@@ -71,6 +71,7 @@ def _load():
             "orc_best": (None, [vp, i64, vp, vp]),
             "orc_run": (i32, [vp, vp, i32, i64, i32, i32, i32, u32, u32, u32, i32, i32, vp, vp, i32]),
             "orc_mixed_N": (i64, [u32, u32]),
+            "orc_gram_real": (None, [vp, i32, i64, vp]),
             "orc_num_threads": (i32, []),
             "orc_set_num_threads": (None, [i32]),
         }
@@ -222,6 +223,19 @@ def run(pop: np.ndarray, F: np.ndarray, N: int, NC: int, NR: int, kind: int, see
     n = _load().orc_run(_ptr(pop), _ptr(F), pop.shape[1], N, NC, NR, kind, seed, pop_id, gen0,
                         generations, int(stop_at_zero), _ptr(tf), _ptr(ts), int(shared_mutation))
     return int(n), tf[:n], ts[:n]
+
+
+def gram_real(Q: np.ndarray) -> np.ndarray:
+    """Batched real Gram Q_b^T Q_b of a [B, m, m] (or [m, m]) array in float64
+    (Sec. 2, Table 1).  float32 input is widened exactly before the loop."""
+    Q = np.asarray(Q)
+    single = Q.ndim == 2
+    Q = np.ascontiguousarray(Q.reshape((1,) + Q.shape) if single else Q, dtype=np.float64)
+    B, m = Q.shape[0], Q.shape[1]
+    assert Q.shape == (B, m, m)
+    G = np.zeros((B, m, m), dtype=np.float64)
+    _load().orc_gram_real(_ptr(Q), m, B, _ptr(G))
+    return G[0] if single else G
 
 
 def num_threads() -> int:

@@ -498,6 +498,32 @@ int64_t orc_mixed_N(uint32_t seed, uint32_t idx)
     return 500 + (int64_t)orc_uniform(stream_next(&s), 0u, 4500u);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Sec. 2, Table 1: batched real Gram F_b = Q_b^T Q_b of B real m x m       */
+/* matrices (the NumPy vs CuPy speed comparison; not a step of the GA).     */
+/* Triple loop in double precision, summing over the rows r in ascending    */
+/* order: G_ij = sum_r Q_ri Q_rj, matrix b at Q[b*m*m + r*m + i].           */
+/* Pinned by: Sylvester H^T H = mI, the diagonal, single-entry and rank-one */
+/* closed forms, the exact rational Gram within the summation error bound,  */
+/* and an orthogonal factor from a QR decomposition.                        */
+/* ------------------------------------------------------------------------ */
+void orc_gram_real(const double *Q, int32_t m, int64_t B, double *G)
+{
+    int64_t b;
+#pragma omp parallel for schedule(static)
+    for (b = 0; b < B; ++b) {
+        const double *q = Q + (size_t)b * m * m;
+        double *g = G + (size_t)b * m * m;
+        for (int32_t i = 0; i < m; ++i)
+            for (int32_t j = 0; j < m; ++j) {
+                double acc = 0.0;
+                for (int32_t r = 0; r < m; ++r)
+                    acc += q[(size_t)r * m + i] * q[(size_t)r * m + j];
+                g[(size_t)i * m + j] = acc;
+            }
+    }
+}
+
 int32_t orc_num_threads(void)
 {
 #ifdef _OPENMP

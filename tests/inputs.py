@@ -23,3 +23,18 @@ def balanced_pm1(P: int, m: int, seed: int) -> np.ndarray:
     cols = base[order]                            # [P, m-1, m]
     pop[:, :, 1:] = np.transpose(cols, (0, 2, 1))
     return pop
+
+
+def uniform_real(B: int, m: int, seed: int, dtype=np.float64) -> np.ndarray:
+    """B real m x m matrices with entries uniform on [0, 1), the input of the
+    batched-Gram speed comparison (Sec. 2, Table 1: N = 10,000, m = 100)."""
+    rng = np.random.default_rng(seed)
+    return rng.random((B, m, m)).astype(dtype)
+
+
+def signed_real(B: int, m: int, seed: int, dtype=np.float64) -> np.ndarray:
+    """Entries uniform on [-1, 1) scaled by random powers of two (2^-8 .. 2^8),
+    so that sums cancel and magnitudes spread."""
+    rng = np.random.default_rng(seed)
+    x = rng.random((B, m, m)) * 2.0 - 1.0
+    return (x * np.exp2(rng.integers(-8, 9, size=(B, m, m)))).astype(dtype)
