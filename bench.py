@@ -212,7 +212,7 @@ def peaks_report(args):
             "l2_bytes": getattr(prop, "L2_cache_size", None),
             "popc_per_s": r["popc_chain"], "dp4a_per_s": r["dp4a"], "imad_per_s": r["imad"],
             "mma_sync_s8_mac_per_s": r["imma_s8"], "mma_sync_e4m3_mac_per_s": r["mma_e4m3"],
-            "l2_read_bytes_per_s": r["l2_read_bytes"],
+            "l2_read_bytes_per_s": r["l2_read_bytes"], "dfma_per_s": r["dfma"], "ffma_per_s": r["ffma"],
             "grid_barrier_us": (1e6 / r["grid_barriers"]) if r["grid_barriers"] > 0 else None,
             "hbm_gbs": _peaks()[0], "hbm_source": _peaks()[1]}
     print(json.dumps(line), flush=True)
@@ -300,6 +300,117 @@ def gram_sweep(args):
             print(json.dumps(line), flush=True)
             del pop, fit, sub, sub8
             torch.cuda.empty_cache()
+
+
+# Sec. 2, Table 1: seconds per additional batched product (N = 10,000, m = 100,
+# float64) on the paper's machines, from the text (CuPy on an RTX 3080: about
+# 0.07 s a loop; NumPy on the host CPU: about 2.12 s a loop).
+PAPER_TABLE1_CUPY_S, PAPER_TABLE1_NUMPY_S = 0.07, 2.12
+
+
+def table1_workload(args):
+    """The batched-Gram speed comparison of Sec. 2 (Table 1): N = 10,000
+    random 100 x 100 matrices (uniform on [0, 1), seeded), each multiplied by
+    its own transpose, in float64 (the paper's type) and float32.  One JSON
+    line per type: seconds per batched product through ga_gram_real_batch
+    with the data resident (800 MB in + 800 MB out in float64, larger than
+    the L2, so no flush), end to end with the input copied in from pinned
+    host memory and G copied back, the library batched product (torch.bmm)
+    timed beside it, the roofline against the measured FMA rate and the HBM
+    copy bandwidth, a sampled check against the oracle, and the oracle's own
+    rate on a bounded sample of host cores."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2208_14961_gb300.build import build
+    build()
+    from paper_2208_14961_gb300 import hadga as h
+    from paper_2208_14961_gb300 import peaks
+
+    Nm, m = args.t1_n, args.t1_m
+    hbm, hbm_kind = _peaks()
+    gen = torch.Generator(device="cuda")
+    for dtype, name, fma_kind in ((torch.float64, "f64", "dfma"), (torch.float32, "f32", "ffma")):
+        fma_rate = peaks.rate(fma_kind)
+        gen.manual_seed(11)
+        q = torch.rand((Nm, m, m), dtype=dtype, device="cuda", generator=gen)
+        g = torch.empty_like(q)
+        reps = args.t1_reps
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        launches0 = h.kernel_launches()
+        for _ in range(3):
+            h.ga_gram_real_batch(q, g)
+        torch.cuda.synchronize()
+        ev[0].record()
+        for _ in range(reps):
+            h.ga_gram_real_batch(q, g)
+        ev[1].record()
+        ev[1].synchronize()
+        sec = ev[0].elapsed_time(ev[1]) / 1e3 / reps
+        launches = h.kernel_launches() - launches0
+        # the library product of the paper's listing: matmul(Q^T, Q), all m^2 entries
+        qt = q.transpose(1, 2)
+        for _ in range(2):
+            torch.bmm(qt, q)
+        torch.cuda.synchronize()
+        ev[0].record()
+        for _ in range(reps):
+            torch.bmm(qt, q)
+        ev[1].record()
+        ev[1].synchronize()
+        sec_lib = ev[0].elapsed_time(ev[1]) / 1e3 / reps
+        # end to end: pinned host input in, G out, every product
+        qh = q.cpu().pin_memory()
+        gh = torch.empty_like(qh).pin_memory()
+        s = torch.cuda.current_stream()
+        t0 = time.perf_counter()
+        e2e_reps = max(1, reps // 4)
+        for _ in range(e2e_reps):
+            q.copy_(qh, non_blocking=True)
+            h.ga_gram_real_batch(q, g, stream=s)
+            gh.copy_(g, non_blocking=True)
+        torch.cuda.synchronize()
+        sec_e2e = (time.perf_counter() - t0) / e2e_reps
+        # sampled check against the oracle (the summation bound of both sides)
+        idx = np.random.default_rng(12).choice(Nm, 32, replace=False)
+        tidx = torch.as_tensor(idx, device="cuda")
+        Qs = q[tidx].cpu().numpy().astype(np.float64)
+        Gs = g[tidx].cpu().numpy().astype(np.float64)
+        u = 2.0 ** -53 if dtype == torch.float64 else 2.0 ** -24
+        gam = lambda n, uu: n * uu / (1 - n * uu)
+        tol = 1.001 * (gam(m, u) + gam(m, 2.0 ** -53)) * oracle.gram_real(np.abs(Qs))
+        ok = bool(np.all(np.abs(Gs - oracle.gram_real(Qs)) <= tol))
+        # oracle on a bounded sample of host cores
+        ns = max(1, min(Nm, args.t1_oracle_matrices))
+        Qc = Qs if ns <= len(Qs) else q[:ns].cpu().numpy().astype(np.float64)
+        Qc = Qc[:ns]
+        t0 = time.perf_counter()
+        oracle.gram_real(Qc)
+        t_orc = (time.perf_counter() - t0) * Nm / ns
+        elem = q.element_size()
+        fma_alg = m * m * (m + 1) // 2          # one FMA per term of each distinct entry
+        bytes_alg = 2 * m * m * elem            # read Q, write G
+        t_fma = Nm * fma_alg / fma_rate
+        t_mem = Nm * bytes_alg / (hbm * 1e9)
+        bound = "fma" if t_fma >= t_mem else "hbm"
+        line = {"metric": "batched Gram seconds per product (Table 1)", "dtype": name, "N": Nm, "m": m,
+                "value": sec, "unit": "s", "higher_is_better": False, "matrices_per_s": Nm / sec,
+                "gpu_launches": launches // (reps + 3),
+                "e2e": {"value": sec_e2e, "unit": "s", "h2d_bytes_per_step": Nm * m * m * elem,
+                        "d2h_bytes_per_step": Nm * m * m * elem},
+                "library_bmm_s": sec_lib,
+                "roofline": {"bound": bound, "fma_per_s_achieved": Nm * fma_alg / sec,
+                             "fma_per_s_peak": fma_rate, "fma_frac": t_fma / sec,
+                             "gbs_achieved": Nm * bytes_alg / sec / 1e9, "gbs_peak": hbm, "hbm_frac": t_mem / sec,
+                             "peak_source": f"FMA rate measured by the peaks microbenchmark; HBM {hbm_kind}"},
+                "paper_s_per_loop": {"cupy_rtx3080": PAPER_TABLE1_CUPY_S, "numpy_cpu": PAPER_TABLE1_NUMPY_S},
+                "cpu_baseline": {"value": t_orc, "unit": "s", "cores": oracle.num_threads(), "kind": "oracle",
+                                 "sample": f"{ns} matrices, scaled to N={Nm}"},
+                "within_bound_32_sampled": ok}
+        print(json.dumps(line), flush=True)
+        del q, g, qh, gh
+        torch.cuda.empty_cache()
 
 
 MIXED_ORDERS = (12, 16, 20, 24, 28, 32, 36)
@@ -589,6 +700,11 @@ def main():
     ap.add_argument("--table3", action="store_true", help="the paper's fitness-comparison workload (Sec. 4.2)")
     ap.add_argument("--t3-ms", default="20,40,60,80,100")
     ap.add_argument("--t3-gens", type=int, default=1000)
+    ap.add_argument("--table1", action="store_true", help="the batched float Gram comparison of Sec. 2 (Table 1)")
+    ap.add_argument("--t1-n", type=int, default=10000)
+    ap.add_argument("--t1-m", type=int, default=100)
+    ap.add_argument("--t1-reps", type=int, default=20)
+    ap.add_argument("--t1-oracle-matrices", type=int, default=2000)
     ap.add_argument("--peaks", action="store_true", help="microbenchmark rates used by the roofline fractions")
     ap.add_argument("--search", action="store_true", help="time to a Hadamard matrix (the paper's Sec. 4.4 runs)")
     ap.add_argument("--search-ms", default="20,24,28")
@@ -613,6 +729,9 @@ def main():
         return
     if args.search:
         search_workload(args)
+        return
+    if args.table1:
+        table1_workload(args)
         return
     args.warmup = max(args.warmup, 3)
 

@@ -301,6 +301,28 @@ ga_status ga_select_static(const void *pop_in, const uint32_t *fit_in, void *par
                            int32_t storage, int32_t m, int64_t N, uint32_t seed, uint32_t pop_id, uint32_t gen,
                            void *stream);
 
+/* Element type of ga_gram_real_batch. */
+typedef enum {
+    GA_REAL_F32 = 0,  /* float  */
+    GA_REAL_F64 = 1   /* double */
+} ga_real_type;
+
+/* The batched matrix product of the speed comparison of Sec. 2 (Table 1:
+ * N = 10,000 random 100 x 100 float64 matrices, each multiplied by its own
+ * transpose).  Not a step of the GA.  Computes G_b = Q_b^T Q_b for b < B:
+ *   q_dev : B real m x m matrices of `type`, row-major, entry (r, i) of
+ *           matrix b at q_dev[(b*m + r)*m + i]; read only.
+ *   g_dev : B matrices of the same type and layout, written in full (both
+ *           triangles of the symmetric G_b).
+ * Entry (i, j) is the sum over r = 0 .. m-1, ascending, of Q_ri Q_rj with one
+ * fused multiply-add per term in the type's precision, so it lies within
+ * m u / (1 - m u) * sum_r |Q_ri Q_rj| of the exact value (u = 2^-53 for
+ * double, 2^-24 for float).  1 <= m <= 256, 0 <= B <= 2^31 (B = 0 does
+ * nothing and accepts NULL buffers).  Both pointers are device memory owned
+ * by the caller, 16-byte aligned, and must not overlap.  GA_EINVAL for a bad type, size, pointer or
+ * overlap (message in ga_last_error(NULL)).  Stream-ordered, asynchronous. */
+ga_status ga_gram_real_batch(const void *q_dev, void *g_dev, int32_t type, int32_t m, int64_t B, void *stream);
+
 /* Converts P matrices between storage formats (any pair). */
 ga_status ga_convert(const void *src, int32_t src_storage, void *dst, int32_t dst_storage, int32_t m,
                      int64_t P, void *stream);

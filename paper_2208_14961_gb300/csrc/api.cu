@@ -1050,6 +1050,24 @@ ga_status ga_fitness_batch(const void *pop_dev, int32_t storage, int32_t m, int6
     return cuda_check(nullptr, launch_fitness(pop_dev, storage, m, 0, P, kind, path, fit_dev, s), "fitness");
 }
 
+ga_status ga_gram_real_batch(const void *q_dev, void *g_dev, int32_t type, int32_t m, int64_t B, void *stream)
+{
+    if (type != GA_REAL_F32 && type != GA_REAL_F64)
+        return set_error(nullptr, GA_EINVAL, "unknown real type %d", type);
+    if (m < 1 || m > 256)
+        return set_error(nullptr, GA_EINVAL, "m=%d outside 1..256", m);
+    if (B == 0)
+        return GA_OK;  // nothing to do; empty buffers may be NULL
+    if (!q_dev || !g_dev || !aligned16(q_dev) || !aligned16(g_dev) || B < 0 || B > kMaxP)
+        return set_error(nullptr, GA_EINVAL, "bad buffers or B");
+    const size_t bytes = (size_t)B * m * m * (type == GA_REAL_F64 ? 8u : 4u);
+    const uintptr_t q0 = (uintptr_t)q_dev, g0 = (uintptr_t)g_dev;
+    if (B > 0 && q0 < g0 + bytes && g0 < q0 + bytes)
+        return set_error(nullptr, GA_EINVAL, "q and g overlap");
+    return cuda_check(nullptr, launch_gram_real(q_dev, g_dev, type == GA_REAL_F64, m, B, (cudaStream_t)stream),
+                      "real Gram");
+}
+
 ga_status ga_convert(const void *src, int32_t src_storage, void *dst, int32_t dst_storage, int32_t m, int64_t P,
                      void *stream)
 {

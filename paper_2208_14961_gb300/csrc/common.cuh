@@ -372,6 +372,39 @@ __device__ __forceinline__ uint32_t warp_fitness_cols(const uint32_t *cols, int 
 }
 
 // ---------------------------------------------------------------------------
+// Asynchronous global -> shared copies (cp.async; 16 bytes through L2 only,
+// 4 or 8 bytes through L1) and their commit / wait groups.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async_small(void *smem_dst, const void *gmem_src)
+{
+    static_assert(BYTES == 4 || BYTES == 8, "cp.async.ca copies 4, 8 or 16 bytes");
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(gmem_src), "n"(BYTES) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+// Waits until at most N of this thread's most recent cp.async groups are
+// pending (all older ones complete).
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// ---------------------------------------------------------------------------
 // Tiled half-Gram storage of the incremental fitness mode: H = G / 2 as int8
 // in 8 x 8 tiles (I <= J) of the upper triangle, tile t = I nb - I(I-1)/2 +
 // (J - I), nb = ceil(m / 8); entry (i, j) at byte 64 t + 8 (i mod 8) +

@@ -360,13 +360,6 @@ __global__ void __launch_bounds__(256) k_fsq_imma_regs(const int8_t *__restrict_
 // staged in shared memory with rows padded by 32 bytes (a half-warp's 8-byte
 // reads of 4 rows then cover all 32 banks), the upper-triangle 16 x 8 tiles
 // of R dealt round-robin to the warps.
-// One 16-byte asynchronous copy global -> shared (cp.async.cg: through L2).
-__device__ __forceinline__ void cp_async16_g2s(void *smem_dst, const void *gmem_src)
-{
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
-}
-
 constexpr int kMmaSmemThreads = 256;  // 8 warps per block
 
 // m in {96, 128, ..., 256} (multiple of 32): one matrix per block at a time,
@@ -393,8 +386,8 @@ __global__ void __launch_bounds__(kMmaSmemThreads) k_fsq_imma_smem(const int8_t 
         const uint4 *src = reinterpret_cast<const uint4 *>(pop + (size_t)q * M * M);
         uint8_t *dst = s_q + (size_t)b * BSZ;
         for (int c = threadIdx.x; c < CHUNKS; c += blockDim.x)
-            cp_async16_g2s(dst + (c / PER_ROW) * RS + (c % PER_ROW) * 16, src + c);
-        asm volatile("cp.async.commit_group;" ::: "memory");
+            cp_async16(dst + (c / PER_ROW) * RS + (c % PER_ROW) * 16, src + c);
+        cp_async_commit();
     };
     // this warp's tiles [t0, t1) and the (ri, cj) of t0
     const int t0 = warp * T / NW, t1 = (warp + 1) * T / NW;
@@ -413,9 +406,9 @@ __global__ void __launch_bounds__(kMmaSmemThreads) k_fsq_imma_smem(const int8_t 
         const int64_t qn = q + gridDim.x;
         if (qn < end) {
             issue(qn, buf ^ 1);
-            asm volatile("cp.async.wait_group 1;" ::: "memory");
+            cp_async_wait_group<1>();
         } else {
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            cp_async_wait_group<0>();
         }
         __syncthreads();
         const uint8_t *Q = s_q + (size_t)buf * BSZ + grp * RS + tig * 8;

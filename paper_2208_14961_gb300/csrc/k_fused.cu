@@ -488,27 +488,6 @@ __device__ __forceinline__ uint32_t tile_row_unit(int i, int J, int nb)
     return (uint32_t)((I * nb - (I * (I - 1)) / 2 + (J - I)) * 8 + (i & 7));
 }
 
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
-{
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_wait_all()
-{
-    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-}
-
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-
-// Waits until at most N of this thread's most recent cp.async groups are
-// pending (all older ones complete).
-template <int N>
-__device__ __forceinline__ void cp_async_wait_group()
-{
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
 // Copies of one offspring cut at c, in 16-byte groups (16-byte units of a
 // Gram buffer):
 //  [0, nG)              phase 1: the H[:c, :c] tiles of Pt (4 nTL groups,

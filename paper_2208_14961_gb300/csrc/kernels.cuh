@@ -63,6 +63,9 @@ cudaError_t launch_mutate(void *pop, int storage, int m, int64_t N, int NC, int 
 cudaError_t launch_best(const uint32_t *fit, int64_t P, unsigned long long *out, cudaStream_t s);
 cudaError_t launch_convert(const void *src, int src_storage, void *dst, int dst_storage, int m, int64_t P,
                            cudaStream_t s);
+// Batched real Gram G_b = Q_b^T Q_b (FP64 when f64 != 0, else FP32).
+cudaError_t launch_gram_real(const void *q, void *g, int f64, int m, int64_t B, cudaStream_t s);
+void gram_real_shape(int m, int elem, int &threads, int &kc, size_t &smem);
 // Tiled half-Gram (common.cuh: 8 x 8 int8 tiles of the upper triangle of
 // G / 2) of P bit-storage matrices into gram[q * dpad]; gidx[q] = q.
 cudaError_t launch_gram_store(const uint32_t *pop, int m, int64_t P, int8_t *gram, int dpad, uint32_t *gidx,

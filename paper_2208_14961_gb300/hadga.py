@@ -20,6 +20,7 @@ GA_OK, GA_EINVAL, GA_ENOMEM, GA_ECUDA, GA_ETIMEOUT, GA_EUNSUPPORTED = range(6)
 FIT_SQ, FIT_ABS, FIT_NNZ = 0, 1, 2
 STORE_INT8, STORE_BITS, STORE_E4M3, STORE_BF16 = 0, 1, 2, 3
 PATH_AUTO, PATH_INT32, PATH_IMMA, PATH_FP8, PATH_BF16, PATH_POPC, PATH_FP8_WARP = range(7)
+GA_REAL_F32, GA_REAL_F64 = 0, 1
 
 _STATUS_NAMES = {0: "GA_OK", 1: "GA_EINVAL", 2: "GA_ENOMEM", 3: "GA_ECUDA", 4: "GA_ETIMEOUT",
                  5: "GA_EUNSUPPORTED"}
@@ -84,6 +85,7 @@ SIGNATURES = {
     "ga_init_batch": (_i32, [_vp, _i32, _i32, _i64, _u32, _u32, _vp]),
     "ga_fitness_batch": (_i32, [_vp, _i32, _i32, _i64, _i32, _i32, _vp, _vp]),
     "ga_convert": (_i32, [_vp, _i32, _vp, _i32, _i32, _i64, _vp]),
+    "ga_gram_real_batch": (_i32, [_vp, _vp, _i32, _i32, _i64, _vp]),
     "ga_select_static": (_i32, [_vp, _vp, _vp, _vp, _i32, _i32, _i64, _u32, _u32, _u32, _vp]),
 }
 
@@ -170,6 +172,17 @@ def ga_fitness_batch(pop: torch.Tensor, storage: int, m: int, P: int, kind: int,
 def ga_convert(src: torch.Tensor, src_storage: int, dst: torch.Tensor, dst_storage: int, m: int, P: int,
                stream=None):
     check(load().ga_convert(_ptr(src), src_storage, _ptr(dst), dst_storage, m, P, _stream(stream)))
+
+
+def ga_gram_real_batch(q: torch.Tensor, g: torch.Tensor, stream=None):
+    """G_b = Q_b^T Q_b for a [B, m, m] float32 or float64 tensor into g (same
+    shape and dtype); the batched product of the speed comparison of Sec. 2."""
+    if q.dtype not in (torch.float32, torch.float64) or g.dtype != q.dtype or g.shape != q.shape:
+        raise ValueError("q and g must be float32 or float64 tensors of one shape [B, m, m]")
+    if q.dim() != 3 or q.shape[1] != q.shape[2]:
+        raise ValueError("q must have shape [B, m, m]")
+    typ = GA_REAL_F64 if q.dtype == torch.float64 else GA_REAL_F32
+    check(load().ga_gram_real_batch(_ptr(q), _ptr(g), typ, q.shape[1], q.shape[0], _stream(stream)))
 
 
 def ga_select_static(pop_in: torch.Tensor, fit_in: torch.Tensor, parents_out: torch.Tensor,

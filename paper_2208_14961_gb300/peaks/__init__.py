@@ -8,7 +8,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = os.path.join(os.path.dirname(_HERE), "_build", "libpeaks.so")
 
 KINDS = {"popc": 0, "popc_chain": 1, "dp4a": 2, "imma_s8": 3, "imad": 4, "mma_e4m3": 5, "l2_read_bytes": 6,
-         "grid_barriers": 7}
+         "grid_barriers": 7, "dfma": 8, "ffma": 9}
 
 
 def build():

@@ -1,8 +1,8 @@
 // peaks.cu -- throughput microbenchmarks of the instruction classes the
 // Gram paths use on this GPU (not part of libhadga): 32-bit population count,
 // 4-way byte dot product (dp4a), 32-bit integer multiply-add, warp-level int8
-// and e4m3 tensor-core MMA, L2 read bandwidth and the latency of the grid
-// barrier of the fused generation kernel.
+// and e4m3 tensor-core MMA, FP64 and FP32 fused multiply-add, L2 read
+// bandwidth and the latency of the grid barrier of the fused generation kernel.
 // Each kernel runs long dependent-free chains per thread and returns a
 // checksum so the compiler keeps the work; the host times it with events.
 #include <cstdint>
@@ -142,6 +142,28 @@ __global__ void k_mma_e4m3(uint32_t *out, int iters)
         out[0] = 1u;
 }
 
+// Fused multiply-adds in T (double or float): 8 independent chains a thread.
+template <typename T>
+__global__ void k_fma(uint32_t *out, int iters)
+{
+    T x[8];
+    const T c = T(0.999755859375), d = T(0.000244140625) * T(threadIdx.x & 7);
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        x[i] = T(threadIdx.x + i) * T(0.0009765625);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            x[i] = fma(x[i], c, d);
+    }
+    T s = T(0);
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        s += x[i];
+    if (s == T(1234.5))
+        out[0] = 1u;
+}
+
 // Reads `n4` 16-byte words of `buf` (small enough to stay in L2) `iters`
 // times through L2 (ld.global.cg), grid-stride.
 __global__ void k_l2_read(const uint4 *__restrict__ buf, size_t n4, int iters, uint32_t *out)
@@ -230,7 +252,8 @@ static double grid_barrier_rate(int sms, int iters)
 } // namespace
 
 // kind: 0 popc (mixed with an integer update), 1 popc chain, 2 dp4a, 3 mma.sync s8,
-// 4 IMAD, 5 mma.sync e4m3 (multiply-adds), 6 L2 read bytes, 7 grid barriers.
+// 4 IMAD, 5 mma.sync e4m3 (multiply-adds), 6 L2 read bytes, 7 grid barriers,
+// 8 FP64 fused multiply-adds, 9 FP32 fused multiply-adds.
 // Returns the operations per second (popc / dp4a instructions per lane, or
 // int8 multiply-adds for the MMA) measured over `iters` loop trips.
 extern "C" double peak_rate(int kind, int iters)
@@ -257,6 +280,8 @@ extern "C" double peak_rate(int kind, int iters)
         case 1: k_popc_only<<<blocks, threads>>>(out, iters); ops_per_thread = 16.0 * iters; break;
         case 2: k_dp4a<<<blocks, threads>>>(out, iters); ops_per_thread = 8.0 * iters; break;
         case 4: k_imad<<<blocks, threads>>>(out, iters); ops_per_thread = 8.0 * iters; break;
+        case 8: k_fma<double><<<blocks, threads>>>(out, iters); ops_per_thread = 8.0 * iters; break;
+        case 9: k_fma<float><<<blocks, threads>>>(out, iters); ops_per_thread = 8.0 * iters; break;
         case 5: k_mma_e4m3<<<blocks, threads>>>(out, iters); ops_per_thread = 4.0 * iters * 4096.0 / 32.0; break;
         default: k_imma<<<blocks, threads>>>(out, iters); ops_per_thread = 4.0 * iters * 4096.0 / 32.0; break;
         }

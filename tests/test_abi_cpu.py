@@ -98,3 +98,19 @@ def test_package_has_no_cpu_fallback():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+@pytest.mark.parametrize("typ,m,B,same", [(2, 8, 1, False), (-1, 8, 1, False), (1, 0, 1, False), (1, 257, 1, False),
+                                          (0, 8, -1, False), (1, 8, 1, True)])
+def test_gram_real_rejects_bad_arguments_without_gpu(lib, typ, m, B, same):
+    from paper_2208_14961_gb300 import hadga
+    q = ctypes.c_void_p(0x10000)
+    g = q if same else ctypes.c_void_p(0x90000000)
+    assert lib.ga_gram_real_batch(q, g, typ, m, B, None) == hadga.GA_EINVAL
+    assert hadga.last_error()
+
+
+def test_gram_real_rejects_misaligned_buffers(lib):
+    from paper_2208_14961_gb300 import hadga
+    st = lib.ga_gram_real_batch(ctypes.c_void_p(0x10008), ctypes.c_void_p(0x90000000), 1, 8, 1, None)
+    assert st == hadga.GA_EINVAL and "bad buffers" in hadga.last_error()
