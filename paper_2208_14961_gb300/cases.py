@@ -10,6 +10,8 @@ inc_m100    m=100, P=20,000, bit storage, incremental Gram-delta fitness:
 full_m100   the same workload with full fitness recomputation
 gram_m<M>_<path>  Gram + fitness of a population of ~1 GiB (int8 size) at
             order M with path int32 | imma | popc8 | popc | fp8 | bf16 | fp8w
+real_<f32|f64>_m<M>  batched real Gram Q^T Q of 10,000 uniform random
+            matrices of order M (two launches)
 """
 import sys
 
@@ -60,6 +62,19 @@ def main(argv):
             h.ga_fitness_batch(pop, storage, m, P, h.FIT_SQ, path, fit)
         torch.cuda.synchronize()
         print(case, "P", P, "fit[0]", int(fit[0]))
+        return
+    if case.startswith("real_"):
+        _, t, m_s = case.split("_")
+        m = int(m_s[1:])
+        dtype = torch.float64 if t == "f64" else torch.float32
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(11)
+        q = torch.rand((10000, m, m), dtype=dtype, device="cuda", generator=gen)
+        g = torch.empty_like(q)
+        for _ in range(2):
+            h.ga_gram_real_batch(q, g)
+        torch.cuda.synchronize()
+        print(case, "g[0,0,0]", float(g[0, 0, 0]))
         return
     raise SystemExit(f"unknown case {case}")
 

@@ -5,34 +5,47 @@
 //
 // G = sum over rows r of q_r^T q_r (q_r the r-th row of Q), so a block streams
 // its matrix through shared memory a chunk of rows at a time (cp.async into
-// two buffers, the next chunk in flight while one is multiplied), and each thread
-// accumulates R x R tiles of the upper triangle of G (tile row ti <= tile
-// column tj) in registers.  The tile is written once as itself and once as
-// its mirror image (G is symmetric), so the block does (m^3 + m^2 R) / 2
-// multiply-adds instead of the m^3 of a general matrix product.  Entry (i, j)
-// is the sum over r = 0 .. m-1 in ascending order, one fused multiply-add per
-// term, in the input's own precision.
+// two buffers, the next chunk in flight while one is multiplied), and each
+// thread accumulates an R x R tile of G in registers.  The column indices are
+// split into nt groups of R; tiles (ti, tj) with ti <= tj cover the upper
+// triangle of the group grid, and each tile is written once as itself and
+// once as its mirror image (G is symmetric), so a block does about
+// (m^3 + m^2 R) / 2 multiply-adds (m rounded up to a multiple of R) instead
+// of the m^3 of a general matrix product.  Entry (i, j) is the sum over
+// r = 0 .. m-1 in ascending order, one fused multiply-add per term, in the
+// input's own precision.
+//
+// Group g holds two runs of R/2 columns (16 bytes each): g R/2 .. g R/2 +
+// R/2 - 1 and H + g R/2 .. H + g R/2 + R/2 - 1, with H = nt R/2.  Threads of a
+// warp hold consecutive groups, so each 16-byte shared-memory load of a warp
+// reads one contiguous span (no bank conflicts), where a run of R contiguous
+// columns per thread would read every other 16 bytes.
 #include "common.cuh"
 #include "kernels.cuh"
 
 namespace hadga {
 namespace {
 
-constexpr int kRealR = 4;               // register tile edge
-constexpr int kRealThreadsMax = 512;
-constexpr int kRealChunkBytes = 24576;  // shared memory of one of the two row buffers
+// Register tile edge: 4 x 4 in FP64 (the FMA pipe is the bound at any
+// tile), 8 x 8 in FP32 (four shared-memory vector loads per 64 FMAs).
+// Threads per block at most, and the register budget those leave.
+template <typename T>
+struct RealTile {
+    static constexpr int R = sizeof(T) == 8 ? 4 : 8;
+    static constexpr int kMaxThreads = sizeof(T) == 8 ? 512 : 256;
+    static constexpr int kMinBlocks = sizeof(T) == 8 ? 1 : 2;  // FP32: <= 128 registers
+    static constexpr int kChunkBytes = sizeof(T) == 8 ? 24576 : 16384;  // one of the two row buffers
+};
 
-__device__ __forceinline__ void ld4(const double *p, double (&v)[4])
+// 16 bytes (R/2 elements) from shared memory.
+__device__ __forceinline__ void ld16(const double *p, double *v)
 {
     const double2 x = *reinterpret_cast<const double2 *>(p);
-    const double2 y = *reinterpret_cast<const double2 *>(p + 2);
     v[0] = x.x;
     v[1] = x.y;
-    v[2] = y.x;
-    v[3] = y.y;
 }
 
-__device__ __forceinline__ void ld4(const float *p, float (&v)[4])
+__device__ __forceinline__ void ld16(const float *p, float *v)
 {
     const float4 x = *reinterpret_cast<const float4 *>(p);
     v[0] = x.x;
@@ -41,15 +54,23 @@ __device__ __forceinline__ void ld4(const float *p, float (&v)[4])
     v[3] = x.w;
 }
 
-__device__ __forceinline__ void st4(double *p, double a, double b, double c, double d)
+// 16 bytes (R/2 elements) to global memory.
+__device__ __forceinline__ void st16(double *p, const double *v)
 {
-    *reinterpret_cast<double2 *>(p) = make_double2(a, b);
-    *reinterpret_cast<double2 *>(p + 2) = make_double2(c, d);
+    *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
 }
 
-__device__ __forceinline__ void st4(float *p, float a, float b, float c, float d)
+__device__ __forceinline__ void st16(float *p, const float *v)
 {
-    *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+// Column (or row) index of element e of group g: e < R/2 in the first run,
+// the rest in the second run H further on.
+template <int R>
+__device__ __forceinline__ int group_index(int g, int e, int H)
+{
+    return (e < R / 2 ? 0 : H) + g * (R / 2) + (e % (R / 2));
 }
 
 // Tile u of the row-major enumeration of the upper triangle of an nt x nt
@@ -118,16 +139,15 @@ __device__ __forceinline__ void real_issue(const T *q, int m, int sp, int kc_max
 // m .. sp-1 are zero so that edge tiles need no bounds checks in the inner
 // loop.
 template <typename T>
-__global__ void __launch_bounds__(kRealThreadsMax)
+__global__ void __launch_bounds__(RealTile<T>::kMaxThreads, RealTile<T>::kMinBlocks)
     k_gram_real(const T *__restrict__ q, T *__restrict__ g, int m, int64_t B, int kc_max)
 {
     extern __shared__ __align__(16) unsigned char real_smem[];
-    constexpr int R = kRealR;
-    const int nt = (m + R - 1) / R, sp = nt * R;
+    constexpr int R = RealTile<T>::R, R2 = R / 2;
+    const int nt = (m + R - 1) / R, sp = nt * R, H = nt * R2;
     const int U = nt * (nt + 1) / 2;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const bool vec_rows = (m * (int)sizeof(T)) % 16 == 0;
-    const bool full_tiles = m % R == 0;
     T *const buf0 = reinterpret_cast<T *>(real_smem);
     const int buf_elems = kc_max * sp;  // second buffer at buf0 + buf_elems
 
@@ -161,12 +181,14 @@ __global__ void __launch_bounds__(kRealThreadsMax)
         __syncthreads();           // ... and every thread's
         const int kc = min(kc_max, m - cur.k0);
         if (active) {
-            const T *pa = buf0 + parity * buf_elems + ti * R, *pb = buf0 + parity * buf_elems + tj * R;
-#pragma unroll 4
+            const T *pa = buf0 + parity * buf_elems + ti * R2, *pb = buf0 + parity * buf_elems + tj * R2;
+#pragma unroll 2
             for (int kk = 0; kk < kc; ++kk) {
                 T a[R], v[R];
-                ld4(pa + kk * sp, a);
-                ld4(pb + kk * sp, v);
+                ld16(pa + kk * sp, a);
+                ld16(pa + kk * sp + H, a + R2);
+                ld16(pb + kk * sp, v);
+                ld16(pb + kk * sp + H, v + R2);
 #pragma unroll
                 for (int r = 0; r < R; ++r)
 #pragma unroll
@@ -177,25 +199,44 @@ __global__ void __launch_bounds__(kRealThreadsMax)
         if (cur.k0 + kc >= m) {  // end of a tile pass: write the tiles
             if (active) {
                 T *gb = g + (size_t)cur.b * m * m;
-                const int i0 = ti * R, j0 = tj * R;
-                if (full_tiles) {
+                if (vec_rows) {  // 16-byte runs, each wholly inside or outside the matrix
 #pragma unroll
-                    for (int r = 0; r < R; ++r)
-                        st4(gb + (size_t)(i0 + r) * m + j0, acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+                    for (int r = 0; r < R; ++r) {
+                        const int i = group_index<R>(ti, r, H);
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int j = h * H + tj * R2;
+                            if (i < m && j < m)
+                                st16(gb + (size_t)i * m + j, &acc[r][h * R2]);
+                        }
+                    }
                     if (ti != tj)
 #pragma unroll
-                        for (int c = 0; c < R; ++c)
-                            st4(gb + (size_t)(j0 + c) * m + i0, acc[0][c], acc[1][c], acc[2][c], acc[3][c]);
+                        for (int c = 0; c < R; ++c) {
+                            const int j = group_index<R>(tj, c, H);
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                const int i = h * H + ti * R2;
+                                T col[R2];
+#pragma unroll
+                                for (int e = 0; e < R2; ++e)
+                                    col[e] = acc[h * R2 + e][c];
+                                if (i < m && j < m)
+                                    st16(gb + (size_t)j * m + i, col);
+                            }
+                        }
                 } else {
 #pragma unroll
                     for (int r = 0; r < R; ++r)
 #pragma unroll
-                        for (int c = 0; c < R; ++c)
-                            if (i0 + r < m && j0 + c < m) {
-                                gb[(size_t)(i0 + r) * m + j0 + c] = acc[r][c];
+                        for (int c = 0; c < R; ++c) {
+                            const int i = group_index<R>(ti, r, H), j = group_index<R>(tj, c, H);
+                            if (i < m && j < m) {
+                                gb[(size_t)i * m + j] = acc[r][c];
                                 if (ti != tj)
-                                    gb[(size_t)(j0 + c) * m + i0 + r] = acc[r][c];
+                                    gb[(size_t)j * m + i] = acc[r][c];
                             }
+                        }
                 }
             }
 #pragma unroll
@@ -219,41 +260,61 @@ __global__ void __launch_bounds__(kRealThreadsMax)
     cp_async_wait_group<0>();
 }
 
-} // namespace
-
-// Threads per block, rows per shared-memory chunk and dynamic shared memory
-// of the batched real Gram at order m for an element of `elem` bytes.
-void gram_real_shape(int m, int elem, int &threads, int &kc, size_t &smem)
+template <typename T>
+void real_shape(int m, int &threads, int &kc, size_t &smem)
 {
-    const int nt = (m + kRealR - 1) / kRealR, sp = nt * kRealR;
+    constexpr int R = RealTile<T>::R, tmax = RealTile<T>::kMaxThreads;
+    const int nt = (m + R - 1) / R, sp = nt * R;
     const int U = nt * (nt + 1) / 2;
-    threads = ((U + 31) / 32) * 32;
-    if (threads > kRealThreadsMax)
-        threads = kRealThreadsMax;
-    kc = kRealChunkBytes / (sp * elem);
+    const int passes = (U + tmax - 1) / tmax;
+    threads = (((U + passes - 1) / passes + 31) / 32) * 32;
+    kc = RealTile<T>::kChunkBytes / (sp * (int)sizeof(T));
     if (kc > m)
         kc = m;
     if (kc < 1)
         kc = 1;
-    smem = 2 * (size_t)kc * sp * elem;
+    smem = 2 * (size_t)kc * sp * sizeof(T);
+}
+
+template <typename T>
+cudaError_t launch_real(const T *q, T *g, int m, int64_t B, cudaStream_t s)
+{
+    static bool carveout_set = false;  // prefer shared memory over L1 (several blocks per SM)
+    if (!carveout_set) {
+        cudaFuncSetAttribute(k_gram_real<T>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+        carveout_set = true;
+    }
+    int threads = 0, kc = 0;
+    size_t smem = 0;
+    real_shape<T>(m, threads, kc, smem);
+    const unsigned grid = (unsigned)(B < (int64_t)0x7fffffff ? B : (int64_t)0x7fffffff);
+    k_gram_real<T><<<grid, threads, smem, s>>>(q, g, m, B, kc);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+} // namespace
+
+// Threads per block, rows per shared-memory chunk and dynamic shared memory
+// of the batched real Gram at order m for an element of `elem` bytes: the
+// upper tiles are dealt evenly to the fewest passes of at most
+// RealTile<T>::kMaxThreads threads.
+void gram_real_shape(int m, int elem, int &threads, int &kc, size_t &smem)
+{
+    if (elem == 8)
+        real_shape<double>(m, threads, kc, smem);
+    else
+        real_shape<float>(m, threads, kc, smem);
 }
 
 cudaError_t launch_gram_real(const void *q, void *g, int f64, int m, int64_t B, cudaStream_t s)
 {
     if (B <= 0)
         return cudaSuccess;
-    int threads = 0, kc = 0;
-    size_t smem = 0;
-    gram_real_shape(m, f64 ? 8 : 4, threads, kc, smem);
-    const unsigned grid = (unsigned)(B < (int64_t)0x7fffffff ? B : (int64_t)0x7fffffff);
     if (f64)
-        k_gram_real<double><<<grid, threads, smem, s>>>(static_cast<const double *>(q), static_cast<double *>(g), m,
-                                                         B, kc);
-    else
-        k_gram_real<float><<<grid, threads, smem, s>>>(static_cast<const float *>(q), static_cast<float *>(g), m, B,
-                                                       kc);
-    note_launches(1);
-    return cudaGetLastError();
+        return launch_real<double>(static_cast<const double *>(q), static_cast<double *>(g), m, B, s);
+    return launch_real<float>(static_cast<const float *>(q), static_cast<float *>(g), m, B, s);
 }
 
 } // namespace hadga
