@@ -58,7 +58,7 @@ def _peaks():
 # stays in L2 across the generations of a launch, so the cold read of the
 # starting population is the whole traffic and does not grow with the
 # generations per launch).
-FUSED_M20_DRAM_BYTES_PER_LAUNCH = 3.465472e6
+FUSED_M20_DRAM_BYTES_PER_LAUNCH = 3.464448e6
 
 
 def job_rate(local_time, units_per_rank, world, reduce_max=None, device=None):

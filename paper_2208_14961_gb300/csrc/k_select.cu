@@ -131,18 +131,45 @@ __global__ void __launch_bounds__(1024) k_sel_scan(const unsigned long long *__r
 // a4 -- survivor order pi of one generation, one block.  Keys
 // ((u_d << 32) | d) are counted into 2^nbits buckets by their top bits,
 // scattered bucket by bucket, and ranked inside their bucket by counting
-// smaller keys; pi[rank] = d.
+// smaller keys; pi[rank] = d.  One Philox block (SELECT, gen, t) gives the
+// keys of d = 4t .. 4t+3.  With G > 0 a thread keeps the blocks of its
+// groups t = tid + i * blockDim (i < G) in registers between the counting
+// and the scattering pass (the caller guarantees ceil(n / 4) <= G * blockDim);
+// with G = 0 they are drawn again.
 // ---------------------------------------------------------------------------
+template <int G>
 __device__ void perm_block(uint32_t n, uint32_t seed, uint32_t pop_id, uint32_t gen, uint32_t *out,
                            unsigned long long *keys, uint32_t *cnt, uint32_t *off, int nbits, uint32_t *tmp)
 {
     const uint32_t B = 1u << nbits;
     const int sh = 32 - nbits;
+    const uint32_t ngroups = (n + 3u) >> 2;
+    constexpr int GR = G > 0 ? G : 1;
+    uint4 kb[GR];
     for (uint32_t b = threadIdx.x; b < B; b += blockDim.x)
         cnt[b] = 0u;
     __syncthreads();
-    for (uint32_t d = threadIdx.x; d < n; d += blockDim.x)
-        atomicAdd(&cnt[select_key(seed, pop_id, gen, d) >> sh], 1u);
+    if (G > 0) {
+#pragma unroll
+        for (int i = 0; i < GR; ++i) {
+            const uint32_t t = threadIdx.x + (uint32_t)i * blockDim.x;
+            if (t < ngroups) {
+                kb[i] = philox_block(seed, pop_id, OP_SELECT, gen, t, 0u, 0u);
+#pragma unroll
+                for (int w = 0; w < 4; ++w)
+                    if (4u * t + w < n)
+                        atomicAdd(&cnt[word_of(kb[i], w) >> sh], 1u);
+            }
+        }
+    } else {
+        for (uint32_t t = threadIdx.x; t < ngroups; t += blockDim.x) {
+            const uint4 b = philox_block(seed, pop_id, OP_SELECT, gen, t, 0u, 0u);
+#pragma unroll
+            for (int w = 0; w < 4; ++w)
+                if (4u * t + w < n)
+                    atomicAdd(&cnt[word_of(b, w) >> sh], 1u);
+        }
+    }
     __syncthreads();
     uint32_t carry = 0, total;
     for (uint32_t base = 0; base < B; base += blockDim.x) {
@@ -156,10 +183,27 @@ __device__ void perm_block(uint32_t n, uint32_t seed, uint32_t pop_id, uint32_t 
         }
     }
     __syncthreads();
-    for (uint32_t d = threadIdx.x; d < n; d += blockDim.x) {
-        const uint32_t u = select_key(seed, pop_id, gen, d);
-        const uint32_t pos = atomicAdd(&cnt[u >> sh], 1u);
-        keys[pos] = ((unsigned long long)u << 32) | d;
+    auto scatter = [&](uint32_t t, const uint4 &b) {
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const uint32_t d = 4u * t + w;
+            if (d < n) {
+                const uint32_t u = word_of(b, w);
+                const uint32_t pos = atomicAdd(&cnt[u >> sh], 1u);
+                keys[pos] = ((unsigned long long)u << 32) | d;
+            }
+        }
+    };
+    if (G > 0) {
+#pragma unroll
+        for (int i = 0; i < GR; ++i) {
+            const uint32_t t = threadIdx.x + (uint32_t)i * blockDim.x;
+            if (t < ngroups)
+                scatter(t, kb[i]);
+        }
+    } else {
+        for (uint32_t t = threadIdx.x; t < ngroups; t += blockDim.x)
+            scatter(t, philox_block(seed, pop_id, OP_SELECT, gen, t, 0u, 0u));
     }
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
@@ -174,14 +218,19 @@ __device__ void perm_block(uint32_t n, uint32_t seed, uint32_t pop_id, uint32_t 
     __syncthreads();
 }
 
+// Philox groups a thread of the 1024-thread shared-memory sort keeps in
+// registers: ceil(kPermSmemMax / 4) <= kPermGroups * 1024.
+constexpr int kPermGroups = 6;
+static_assert(kPermSmemMax <= 4u * kPermGroups * 1024u, "survivor-order groups exceed the register buffer");
+
 __global__ void __launch_bounds__(1024) k_perm_smem(uint32_t n, uint32_t seed, uint32_t pop_id, uint32_t gen0,
                                                     uint32_t *out, const uint32_t *gen_dev)
 {
     extern __shared__ __align__(16) unsigned long long s_keys[];
     __shared__ uint32_t s_cnt[1 << kPermSmemBits], s_off[1 << kPermSmemBits], s_tmp[33];
     const uint32_t g0 = gen_dev ? *gen_dev + 1u : gen0;
-    perm_block(n, seed, pop_id, g0 + blockIdx.x, out + (size_t)blockIdx.x * n, s_keys, s_cnt, s_off,
-               kPermSmemBits, s_tmp);
+    perm_block<kPermGroups>(n, seed, pop_id, g0 + blockIdx.x, out + (size_t)blockIdx.x * n, s_keys, s_cnt, s_off,
+                            kPermSmemBits, s_tmp);
 }
 
 __global__ void k_set_u32(uint32_t *p, uint32_t v) { *p = v; }
@@ -198,7 +247,7 @@ __global__ void __launch_bounds__(1024) k_perm_global(uint32_t n, uint32_t seed,
                                                       int nbits)
 {
     __shared__ uint32_t s_tmp[33];
-    perm_block(n, seed, pop_id, gen, out, keys, cnt, cnt + (1u << nbits), nbits, s_tmp);
+    perm_block<0>(n, seed, pop_id, gen, out, keys, cnt, cnt + (1u << nbits), nbits, s_tmp);
 }
 
 int perm_global_bits(uint32_t n)

@@ -99,9 +99,12 @@ def _fresh(h, m, N, seed, storage, NC=1, NR=1, kind=0, path=0):
     return pop
 
 
-@pytest.mark.parametrize("m,N", [(4, 1), (4, 9), (12, 250), (20, 300), (36, 40), (100, 12), (256, 3)])
+@pytest.mark.parametrize("m,N", [(4, 1), (4, 9), (12, 250), (20, 300), (36, 40), (100, 12), (256, 3),
+                                 (4, 12288), (20, 12287)])
 @pytest.mark.parametrize("storage", [0, 1])
 def test_select_matches_oracle(m, N, storage):
+    """Includes the largest shared-memory survivor sort (2N = 24,576) and a
+    ragged one (2N = 24,574, not a multiple of the four keys per draw)."""
     h = need_gpu()
     seed = 11
     pop = _fresh(h, m, N, seed, storage)
