@@ -270,12 +270,9 @@ def gram_sweep(args):
             ev[1].synchronize()
             sec = ev[0].elapsed_time(ev[1]) / 1e3 / reps
             # exactness on sampled slots
-            idx = torch.as_tensor(np.sort(rng.choice(P, size=min(256, P), replace=False)), device="cuda")
-            sub = pop.index_select(0, idx).contiguous()
-            sub8 = h.empty_population(0, m, len(idx))
-            h.ga_convert(sub, storage, sub8, 0, m, len(idx))
-            torch.cuda.synchronize()
-            ref = oracle.fitness(sub8.cpu().numpy(), oracle.FIT_SQ)
+            idx_np = np.sort(rng.choice(P, size=min(256, P), replace=False))
+            idx = torch.as_tensor(idx_np, device="cuda")
+            ref = oracle.fitness(oracle.init_slots(m, idx_np, 2), oracle.FIT_SQ)
             got = fit.index_select(0, idx).cpu().numpy().view(np.uint32).astype(np.uint64)
             exact = bool(np.array_equal(ref, got))
             nbytes = P * h.storage_bytes(storage, m)
@@ -298,7 +295,7 @@ def gram_sweep(args):
                     "roof_ms": roof_t * 1e3, "frac": roof_t / sec, "hbm_frac": t_mem / sec,
                     "compute_unit": unit, "compute_frac": (t_cmp / sec) if ops else None, "exact_256": exact}
             print(json.dumps(line), flush=True)
-            del pop, fit, sub, sub8
+            del pop, fit
             torch.cuda.empty_cache()
 
 

@@ -56,6 +56,7 @@ def _load():
             "orc_uniform": (u32, [u32, u32, u32]),
             "orc_stream_words": (None, [u32, u32, u32, u32, u32, u32, i32, vp]),
             "orc_init_population": (None, [vp, i32, i64, u32, u32]),
+            "orc_init_slots": (None, [vp, i32, vp, i64, u32, u32]),
             "orc_gram": (None, [vp, i32, vp]),
             "orc_fitness": (None, [vp, i32, i64, i64, i32, vp]),
             "orc_crossover_pair": (None, [vp, vp, vp, vp, i32, i32]),
@@ -131,6 +132,15 @@ def init_population(m: int, P: int, seed: int, pop_id: int = 0) -> np.ndarray:
     pop = np.zeros((P, m, m), dtype=np.int8)
     _load().orc_init_population(_ptr(pop), m, P, seed, pop_id)
     return pop
+
+
+def init_slots(m: int, slots, seed: int, pop_id: int = 0) -> np.ndarray:
+    """The initial matrices of the listed slots of a population (int8
+    [len(slots), m, m]), each as init_population would build it."""
+    sl = np.ascontiguousarray(np.asarray(slots, dtype=np.int64))
+    out = np.zeros((len(sl), m, m), dtype=np.int8)
+    _load().orc_init_slots(_ptr(out), m, _ptr(sl), len(sl), seed, pop_id)
+    return out
 
 
 def gram(Q: np.ndarray) -> np.ndarray:

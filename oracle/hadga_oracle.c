@@ -153,6 +153,16 @@ void orc_init_population(int8_t *pop, int32_t m, int64_t P, uint32_t seed, uint3
         init_one(pop + (size_t)q * m * m, m, seed, pop_id, (uint32_t)q);
 }
 
+/* The initial matrices of the listed slots only (matrix t of `out` is slot
+ * slots[t]), for checking samples of populations too large to build here. */
+void orc_init_slots(int8_t *out, int32_t m, const int64_t *slots, int64_t n, uint32_t seed, uint32_t pop_id)
+{
+    int64_t t;
+#pragma omp parallel for schedule(static)
+    for (t = 0; t < n; ++t)
+        init_one(out + (size_t)t * m * m, m, seed, pop_id, (uint32_t)slots[t]);
+}
+
 /* ------------------------------------------------------------------------ */
 /* a2  Column Gram G = Q^T Q (Sec. 3.2) by the triple loop.                 */
 /* Pinned by: float64 batched matmul, Sylvester/Paley, m = 4 enumeration.   */

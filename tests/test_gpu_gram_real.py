@@ -67,9 +67,8 @@ def test_table1_size_sampled_and_symmetric():
     the oracle within the bound."""
     h = need_gpu()
     N, m = 10000, 100
-    gen = torch.Generator(device="cuda")
-    gen.manual_seed(7)
-    q = torch.rand((N, m, m), dtype=torch.float64, device="cuda", generator=gen)
+    Q = uniform_real(N, m, 7)
+    q = torch.as_tensor(Q).cuda()
     g = torch.empty_like(q)
     h.ga_gram_real_batch(q, g)
     torch.cuda.synchronize()
@@ -77,9 +76,8 @@ def test_table1_size_sampled_and_symmetric():
     assert bool(torch.isfinite(g).all())
     idx = np.random.default_rng(8).choice(N, 48, replace=False)
     idx = np.concatenate([idx, [0, N - 1]])
-    tidx = torch.as_tensor(idx, device="cuda")
-    Qs = q[tidx].cpu().numpy()
-    Gs = g[tidx].cpu().numpy()
+    Gs = g[torch.as_tensor(idx, device="cuda")].cpu().numpy()
+    Qs = Q[idx]
     assert np.all(np.abs(Gs - oracle.gram_real(Qs)) <= bound(Qs, torch.float64))
 
 

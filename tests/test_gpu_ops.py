@@ -167,18 +167,13 @@ def test_config3_full_size_sampled(m):
     """The precision sweep's workload at full size: P = 8 GiB / m^2 balanced
     matrices (seed 2), every Gram path on its own storage, the launch shapes
     the sweep times; 48 seeded slots checked against the oracle one by one
-    (the same matrices in every storage: the init writes the same content)."""
+    (the oracle builds those slots' initial matrices itself; the device init
+    writes the same content in every storage)."""
     h = need_gpu()
     P = (8 << 30) // (m * m)
     rng = np.random.default_rng(m)
     idx = np.sort(rng.choice(P, size=48, replace=False))
-    sample = np.zeros((len(idx), m, m), dtype=np.int8)
-    pop = h.empty_population(0, m, P)
-    h.ga_init_batch(pop, 0, m, P, 2)
-    torch.cuda.synchronize()
-    sample[:] = pop.index_select(0, torch.as_tensor(idx, device="cuda")).cpu().numpy()
-    del pop
-    torch.cuda.empty_cache()
+    sample = oracle.init_slots(m, idx, 2)
     expected = oracle.fitness(sample, oracle.FIT_SQ)
     for path, storage in ((1, 0), (2, 0), (5, 0), (5, 1), (3, 2), (6, 2), (4, 3)):
         pop = h.empty_population(storage, m, P)
@@ -189,6 +184,27 @@ def test_config3_full_size_sampled(m):
         assert np.array_equal(got.astype(np.uint64), expected), (m, path, storage)
         del pop, fit
         torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("m,P", [(36, 100_000), (128, 80_000), (200, 80_000)])
+@pytest.mark.parametrize("storage", [0, 1])
+def test_popc_warps_with_several_matrices(m, P, storage):
+    """Populations larger than the grid's warps (8 x 64 blocks x 152 SMs =
+    77,824), so warps take a second matrix; sampled slots from both rounds."""
+    h = need_gpu()
+    rng = np.random.default_rng(m + 7)
+    split = 77_824
+    idx = np.sort(np.concatenate([rng.choice(split, 16, replace=False),
+                                  rng.choice(np.arange(split, P), 32, replace=False), [P - 1]]))
+    sample = oracle.init_slots(m, idx, 5)
+    pop = h.empty_population(storage, m, P)
+    h.ga_init_batch(pop, storage, m, P, 5)
+    tidx = torch.as_tensor(idx, device="cuda")
+    for kind in KINDS:
+        fit = torch.zeros(P, dtype=torch.int32, device="cuda")
+        h.ga_fitness_batch(pop, storage, m, P, kind, 5, fit)
+        got = fit.index_select(0, tidx).cpu().numpy().view(np.uint32).astype(np.uint64)
+        assert np.array_equal(got, oracle.fitness(sample, kind)), (m, storage, kind)
 
 
 def test_empty_batches_are_no_ops():

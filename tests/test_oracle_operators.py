@@ -121,6 +121,12 @@ def test_init_uniform_over_balanced_columns_m4():
     assert chi2 < 20.5   # 99.9% quantile, 5 dof
 
 
+def test_init_slots_equal_those_of_the_whole_population():
+    pop = oracle.init_population(24, 50, seed=3, pop_id=2)
+    idx = [0, 7, 31, 49]
+    assert np.array_equal(oracle.init_slots(24, idx, 3, 2), pop[idx])
+
+
 def test_init_deterministic_and_thread_independent():
     a = oracle.init_population(20, 100, seed=1)
     n0 = oracle.num_threads()
