@@ -200,9 +200,38 @@ def popc_per_dot(m):
     return W if W <= 2 else 2 if W == 3 else 3 if W <= 7 else 4
 
 
+def _library_gemm_tflops(kind, n=8192, reps=20):
+    """Dense n x n x n GEMM rate of the vendor library (cuBLAS / cuBLASLt via
+    torch) in TFLOP/s: "bf16" (torch.mm) or "fp8" (e4m3 x e4m3 -> bf16,
+    torch._scaled_mm); None where the installed torch lacks the call."""
+    import torch
+    try:
+        a = torch.randn(n, n, device="cuda")
+        b = torch.randn(n, n, device="cuda")
+        if kind == "bf16":
+            a, b = a.to(torch.bfloat16), b.to(torch.bfloat16)
+            run = lambda: torch.mm(a, b)
+        else:
+            a8, b8 = a.to(torch.float8_e4m3fn), b.to(torch.float8_e4m3fn)
+            one = torch.ones((), device="cuda", dtype=torch.float32)
+            bt = b8.t()  # column-major second operand
+            run = lambda: torch._scaled_mm(a8, bt, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)
+        for _ in range(3):
+            run()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record()
+        for _ in range(reps):
+            run()
+        ev[1].record()
+        ev[1].synchronize()
+        return 2.0 * n ** 3 * reps / (ev[0].elapsed_time(ev[1]) / 1e3) / 1e12
+    except Exception:
+        return None
+
+
 def peaks_report(args):
-    """The microbenchmark rates the roofline fractions use, plus SM count and
-    L2 size (one JSON line)."""
+    """The microbenchmark rates the roofline fractions use, plus SM count,
+    L2 size and the library's dense bf16 / fp8 GEMM rates (one JSON line)."""
     import torch
 
     from paper_2208_14961_gb300 import peaks
@@ -214,6 +243,7 @@ def peaks_report(args):
             "mma_sync_s8_mac_per_s": r["imma_s8"], "mma_sync_e4m3_mac_per_s": r["mma_e4m3"],
             "l2_read_bytes_per_s": r["l2_read_bytes"], "dfma_per_s": r["dfma"], "ffma_per_s": r["ffma"],
             "grid_barrier_us": (1e6 / r["grid_barriers"]) if r["grid_barriers"] > 0 else None,
+            "library_gemm_tflops": {"bf16": _library_gemm_tflops("bf16"), "fp8_e4m3": _library_gemm_tflops("fp8")},
             "hbm_gbs": _peaks()[0], "hbm_source": _peaks()[1]}
     print(json.dumps(line), flush=True)
 
