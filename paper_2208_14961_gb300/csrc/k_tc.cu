@@ -163,8 +163,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
     uint8_t *stages = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dyn_raw) + 1023) & ~uintptr_t(1023));
     __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages], acc_full[4], acc_empty[4], drain;
     __shared__ uint32_t tmem_base;
-    __shared__ unsigned long long part_sum[4][2];
-    __shared__ uint32_t part_cnt[4][2];
+    // partial sums of the matrices of a job: [accumulator][matrix of the tile][use parity]
+    __shared__ unsigned long long part_sum[4][2][2];
+    __shared__ uint32_t part_cnt[4][2][2];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m = prm.m, rows = prm.rows, nch = prm.nchunks, kb = prm.kb, S = prm.nstages;
@@ -182,8 +183,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
         for (int b = 0; b < 4; ++b) {
             mbar_init(&acc_full[b], 1);
             mbar_init(&acc_empty[b], 128);
-            part_sum[b][0] = part_sum[b][1] = 0ull;
-            part_cnt[b][0] = part_cnt[b][1] = 0u;
+            for (int g = 0; g < 2; ++g)
+                for (int u = 0; u < 2; ++u) {
+                    part_sum[b][g][u] = 0ull;
+                    part_cnt[b][g][u] = 0u;
+                }
         }
         mbar_init(&drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -307,7 +311,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
                     const uint32_t col0 = lane_addr + (uint32_t)b * 128u + (uint32_t)(g * m);
                     sum_a = m == 32 ? sq_cols<1>(col0) : m == 64 ? sq_cols<2>(col0) : sq_cols<4>(col0);
                 }
+                // the accumulator is read (tcgen05.wait::ld inside sq_cols): hand it
+                // back to the MMA issuer before the reduction
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                mbar_arrive(&acc_empty[b]);
+                const int use = (int)((jt / (uint32_t)nacc) & 1u);
                 unsigned long long tot = (unsigned long long)(uint32_t)sum_a + 2ull * (uint32_t)sum_b;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1)
@@ -322,20 +330,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
                     // m = 64: warps of sub-partitions 2g, 2g+1 hold matrix g; m >= 128: all four
                     const int g = (m == 64) ? (q >> 1) : 0;
                     const uint32_t need = (m == 64) ? 2u : 4u;
-                    atomicAdd(&part_sum[b][g], tot);
+                    atomicAdd(&part_sum[b][g][use], tot);
                     __threadfence_block();
-                    if (atomicAdd(&part_cnt[b][g], 1u) + 1u == need) {
-                        const unsigned long long all = atomicExch(&part_sum[b][g], 0ull);
-                        part_cnt[b][g] = 0u;
+                    if (atomicAdd(&part_cnt[b][g][use], 1u) + 1u == need) {
+                        const unsigned long long all = atomicExch(&part_sum[b][g][use], 0ull);
+                        part_cnt[b][g][use] = 0u;
                         const int64_t mat = (j * rows) / m + g;
                         if (mat < prm.P)
                             prm.fit[mat] = (uint32_t)((all - m3) >> 1);
                     }
                 }
+                // The combining slot of use parity u is taken again by the job two
+                // uses later on this accumulator, whose MMA waits for every thread of
+                // the group to have read the use in between, i.e. to have finished
+                // this job's combination first.
                 __syncwarp();
-                // released only after this job's partial sums are combined, so the
-                // next job on this accumulator cannot reuse its combining slot early
-                mbar_arrive(&acc_empty[b]);
             }
         }
     }
