@@ -16,14 +16,15 @@
 //   warp 0   one thread issues the TMA copies into a ring of stages (up to
 //            32 stages of rows x chunk bytes within 160 KiB)
 //   warp 1   allocates all 512 TMEM columns; one thread issues tcgen05.mma
-//            per stage and commits to the stage's "empty" barrier and, at
-//            the end of a job, to the accumulator's "full" barrier (four
+//            per stage and commits to the stage's "empty" barrier; at the end
+//            of a job it commits to the accumulator's "full" barrier (four
 //            128-column accumulators for m <= 128, one 384-column pair of
-//            blocks for m = 256)
-//   warps 2-9  two epilogue groups of four warps taking alternate jobs: read
-//            the accumulators with tcgen05.ld (warp w reads TMEM lanes
-//            32(w%4)..32(w%4)+31 = tile rows), square and sum, free the
-//            accumulator and write the fitness
+//            blocks for m = 256).  Ring positions and phases are counters
+//            (no division in the issue loop).
+//   warps 2-9  two epilogue groups of four warps taking alternate jobs: wait
+//            for the accumulator, read it with tcgen05.ld (warp w reads TMEM
+//            lanes 32(w%4)..32(w%4)+31 = tile rows), free it, then square,
+//            sum and write the fitness
 // Every mbarrier wait is bounded (about two seconds); on a timeout the block
 // records ERR_TIMEOUT, drains its outstanding copies with bounded waits,
 // frees its TMEM and returns.
@@ -208,11 +209,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
         if (lane == 0) {
             uint32_t it = 0;
             int issued = 0;
+            int st = 0;         // stage of copy `it`
+            uint32_t sph = 0u;  // parity of that stage's current use
             bool ok = true;
             for (int64_t j = blockIdx.x; j < prm.jobs && ok; j += gridDim.x) {
                 for (int c = 0; c < nch; ++c, ++it) {
-                    const int st = (int)(it % (uint32_t)S);
-                    if (!mbar_wait(&empty[st], ((it / (uint32_t)S) & 1u) ^ 1u, err)) {
+                    if (!mbar_wait(&empty[st], sph ^ 1u, err)) {
                         ok = false;
                         break;
                     }
@@ -222,6 +224,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
                         tma_load_2d(stages + (size_t)st * sbytes + (size_t)h * 128 * kb, &map, x,
                                     (int32_t)(j * rows + h * 128), &full[st]);
                     issued = issued < S ? issued + 1 : S;
+                    if (++st == S) {
+                        st = 0;
+                        sph ^= 1u;
+                    }
                 }
             }
             if (!ok) {
@@ -236,19 +242,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
         // ---- MMA issuer ---------------------------------------------------------
         if (lane == 0) {
             const uint32_t sbo = 8u * (uint32_t)kb;
-            uint32_t it = 0, jt = 0;
+            // ring positions kept as counters: no division in the issue loop
+            int st = 0, b = 0;
+            uint32_t sph = 0u, aph = 0u;  // parities of the stage's and accumulator's current use
             bool ok = true;
-            for (int64_t j = blockIdx.x; j < prm.jobs && ok; j += gridDim.x, ++jt) {
-                const int b = (int)(jt % (uint32_t)nacc);
-                if (!mbar_wait(&acc_empty[b], ((jt / (uint32_t)nacc) & 1u) ^ 1u, err)) {
+            for (int64_t j = blockIdx.x; j < prm.jobs && ok; j += gridDim.x) {
+                if (!mbar_wait(&acc_empty[b], aph ^ 1u, err)) {
                     ok = false;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t d0 = tbase + (uint32_t)b * 128u;
-                for (int c = 0; c < nch; ++c, ++it) {
-                    const int st = (int)(it % (uint32_t)S);
-                    if (!mbar_wait(&full[st], (it / (uint32_t)S) & 1u, err)) {
+                for (int c = 0; c < nch; ++c) {
+                    if (!mbar_wait(&full[st], sph, err)) {
                         ok = false;
                         break;
                     }
@@ -269,10 +275,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
                         }
                     }
                     mma_commit(&empty[st]);  // the stage is free once these MMAs have read it
+                    if (++st == S) {
+                        st = 0;
+                        sph ^= 1u;
+                    }
                 }
                 if (!ok)
                     break;
                 mma_commit(&acc_full[b]);  // the accumulator is complete
+                if (++b == nacc) {
+                    b = 0;
+                    aph ^= 1u;
+                }
             }
             if (!ok) {
                 // make sure no MMA is still writing TMEM before it is freed
@@ -289,12 +303,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
         const int q = warp & 3;               // TMEM sub-partition this warp may read
         const int t = q * 32 + lane;          // tile row (and TMEM lane)
         if (grp < ngroups) {
-            uint32_t jt = 0;
-            for (int64_t j = blockIdx.x; j < prm.jobs; j += gridDim.x, ++jt) {
-                if ((int)(jt % (uint32_t)ngroups) != grp)
+            // the block's jobs in order: group gsel takes the job, on accumulator
+            // bn whose use has parity aph (counters, no division)
+            int gsel = 0, bn = 0;
+            uint32_t aph = 0u;
+            for (int64_t j = blockIdx.x; j < prm.jobs; j += gridDim.x) {
+                const bool mine = gsel == grp;
+                const int b = bn;
+                const uint32_t ph = aph;
+                if (++gsel == ngroups)
+                    gsel = 0;
+                if (++bn == nacc) {
+                    bn = 0;
+                    aph ^= 1u;
+                }
+                if (!mine)
                     continue;
-                const int b = (int)(jt % (uint32_t)nacc);
-                if (!mbar_wait(&acc_full[b], (jt / (uint32_t)nacc) & 1u, err))
+                if (!mbar_wait(&acc_full[b], ph, err))
                     break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t lane_addr = tbase + ((uint32_t)(q * 32) << 16);
@@ -315,7 +340,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
                 // back to the MMA issuer before the reduction
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 mbar_arrive(&acc_empty[b]);
-                const int use = (int)((jt / (uint32_t)nacc) & 1u);
+                const int use = (int)ph;
                 unsigned long long tot = (unsigned long long)(uint32_t)sum_a + 2ull * (uint32_t)sum_b;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1)
