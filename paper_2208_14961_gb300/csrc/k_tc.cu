@@ -21,6 +21,8 @@
 //            128-column accumulators for m <= 128, one 384-column pair of
 //            blocks for m = 256).  Ring positions and phases are counters
 //            (no division in the issue loop).
+//   warp 10  with four accumulators (m <= 128), a second MMA issuer: warp 1
+//            takes the block's even jobs, warp 10 the odd ones
 //   warps 2-9  two epilogue groups of four warps taking alternate jobs: wait
 //            for the accumulator, read it with tcgen05.ld (warp w reads TMEM
 //            lanes 32(w%4)..32(w%4)+31 = tile rows), free it, then square,
@@ -30,6 +32,8 @@
 // frees its TMEM and returns.
 #include <cuda.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -37,7 +41,8 @@ namespace hadga {
 
 namespace {
 
-constexpr int kTcThreads = 320;  // 10 warps: producer, MMA, two epilogue groups of four
+constexpr int kTcThreads = 352;  // 11 warps: producer, MMA, two epilogue groups of four, second MMA
+constexpr int kTcMma2Warp = 10;  // the second MMA issuer
 constexpr int kMaxStages = 32;
 constexpr uint32_t kRingBytes = 160 * 1024;  // shared memory of the stage ring
 
@@ -162,7 +167,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
     extern __shared__ __align__(1024) uint8_t dyn_raw[];
     // 1024-byte alignment keeps every stage on the swizzle pattern's base
     uint8_t *stages = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dyn_raw) + 1023) & ~uintptr_t(1023));
-    __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages], acc_full[4], acc_empty[4], drain;
+    __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages], acc_full[4], acc_empty[4], drain[2];
     __shared__ uint32_t tmem_base;
     // partial sums of the matrices of a job: [accumulator][matrix of the tile][use parity]
     __shared__ unsigned long long part_sum[4][2][2];
@@ -190,7 +195,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
                     part_cnt[b][g][u] = 0u;
                 }
         }
-        mbar_init(&drain, 1);
+        mbar_init(&drain[0], 1);
+        mbar_init(&drain[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -238,15 +244,39 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
                 }
             }
         }
-    } else if (warp == 1) {
-        // ---- MMA issuer ---------------------------------------------------------
-        if (lane == 0) {
+    } else if (warp == 1 || warp == kTcMma2Warp) {
+        // ---- MMA issuers ----------------------------------------------------------
+        // With several accumulators (m <= 128) warp 1 issues the block's even jobs
+        // and warp kTcMma2Warp the odd ones, each on its own accumulators and
+        // stages (the issue of a 128 x 128 job's MMAs and commits, not the tensor
+        // pipe, paces one thread); m = 256 has one accumulator and one issuer.
+        const int nis = nacc > 1 ? 2 : 1;
+        const int me = warp == 1 ? 0 : 1;
+        // TWO: compiled with the job split (the single-issuer loop keeps none of it)
+        auto issue = [&](auto two) {
+            constexpr bool TWO = decltype(two)::value;
             const uint32_t sbo = 8u * (uint32_t)kb;
             // ring positions kept as counters: no division in the issue loop
-            int st = 0, b = 0;
+            int st = 0, b = 0, who = 0;
             uint32_t sph = 0u, aph = 0u;  // parities of the stage's and accumulator's current use
             bool ok = true;
             for (int64_t j = blockIdx.x; j < prm.jobs && ok; j += gridDim.x) {
+                const bool mine = !TWO || who == me;
+                if (TWO && ++who == 2)
+                    who = 0;
+                if (!mine) {
+                    // the other issuer's job: step over its stages and accumulator use
+                    for (int c = 0; c < nch; ++c)
+                        if (++st == S) {
+                            st = 0;
+                            sph ^= 1u;
+                        }
+                    if (++b == nacc) {
+                        b = 0;
+                        aph ^= 1u;
+                    }
+                    continue;
+                }
                 if (!mbar_wait(&acc_empty[b], aph ^ 1u, err)) {
                     ok = false;
                     break;
@@ -289,10 +319,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
                 }
             }
             if (!ok) {
-                // make sure no MMA is still writing TMEM before it is freed
-                mma_commit(&drain);
-                mbar_wait(&drain, 0u, err);
+                // make sure none of this thread's MMAs is still writing TMEM before it is freed
+                mma_commit(&drain[me]);
+                mbar_wait(&drain[me], 0u, err);
             }
+        };
+        if (lane == 0 && me < nis) {
+            if (nis == 2)
+                issue(std::true_type{});
+            else
+                issue(std::false_type{});
         }
     } else {
         // ---- epilogue: warps 2..5 (group 0) and 6..9 (group 1) --------------------
@@ -487,7 +523,9 @@ cudaError_t launch_fitness_tc(const void *pop, int storage, int m, int64_t first
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t grid = prm.jobs < sms ? prm.jobs : sms;
-    kern<<<(unsigned)grid, kTcThreads, smem, s>>>(map, prm);
+    // m = 256 has a single issuer: no second MMA warp
+    const int threads = m == 256 ? kTcThreads - 32 : kTcThreads;
+    kern<<<(unsigned)grid, threads, smem, s>>>(map, prm);
     note_launches(1);
     return cudaGetLastError();
 }
