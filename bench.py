@@ -41,7 +41,9 @@ if ROOT not in sys.path:
 M, N, SEED, NC, NR = 20, 10_000, 1, 1, 1
 P = 4 * N
 STEP_GENS = 50
-WORKLOAD = "m=20, P=40,000, F_sq, NC=NR=1, seed 1, bit storage, 50 generations per step"
+# the same metric and workload on both arms (the reference arm's steps are shorter)
+METRIC = "GA generations/s at m=20, P=40k"
+WORKLOAD = "m=20, P=40,000, F_sq, NC=NR=1, seed 1"
 
 
 def _peaks():
@@ -174,11 +176,11 @@ def run_reference(args, rank, world):
     gps = args.steps * sample / dt
     line = {
         "impl": "reference",
-        "metric": "GA generations/s at m=20, P=40k (CPU oracle)",
+        "metric": METRIC, "arm": "CPU oracle (int8 matrices)",
         "value": gps, "unit": "generations/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": WORKLOAD.replace("50 generations", f"{sample} generations")},
+        "config": {"workload": WORKLOAD, "generations_per_step": sample, "global_batch": P},
         "cpu_baseline": {"value": gps, "unit": "generations/s", "cores": oracle.num_threads(), "kind": "oracle",
                          "sample": f"{sample} generations per step, {args.steps} steps"},
         "e2e": {"value": gps, "unit": "generations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -908,11 +910,12 @@ def main():
 
     if rank == 0:
         line = {
-            "metric": "GA generations/s at m=20, P=40k (fused persistent generation kernel)",
+            "metric": METRIC, "arm": "fused persistent generation kernel",
             "value": value, "unit": "generations/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "global_batch": P * world, "parallelism": f"replicas{world}",
+            "config": {"workload": WORKLOAD, "generations_per_step": STEP_GENS, "storage": "bits",
+                       "global_batch": P * world, "parallelism": f"replicas{world}",
                        "l2": "flushed before every step (256 MiB write), outside the timed events",
                        "fused": bool(pop.is_fused())},
             "evals_per_s": value * (P // 2),
