@@ -114,3 +114,9 @@ def test_gram_real_rejects_misaligned_buffers(lib):
     from paper_2208_14961_gb300 import hadga
     st = lib.ga_gram_real_batch(ctypes.c_void_p(0x10008), ctypes.c_void_p(0x90000000), 1, 8, 1, None)
     assert st == hadga.GA_EINVAL and "bad buffers" in hadga.last_error()
+
+
+def test_gram_real_empty_batch_accepts_null_buffers(lib):
+    from paper_2208_14961_gb300 import hadga
+    assert lib.ga_gram_real_batch(None, None, 1, 8, 0, None) == hadga.GA_OK
+    assert lib.ga_gram_real_batch(None, None, 0, 256, 0, None) == hadga.GA_OK
