@@ -414,11 +414,11 @@ __host__ __device__ __forceinline__ int gram_tiles_nb(int m) { return (m + 7) >>
 __host__ __device__ __forceinline__ int gram_tiles(int m) { return gram_tiles_nb(m) * (gram_tiles_nb(m) + 1) / 2; }
 
 // Tile-row I and tile-column J of tile t (tile-row I holds nb - I tiles).
-__device__ __forceinline__ void tile_coords(int t, int nb, int &I, int &J)
+__host__ __device__ __forceinline__ void tile_coords(int t, int nb, int &I, int &J)
 {
     const float b = (float)(2 * nb + 1);
     int i = (int)((b - sqrtf(b * b - 8.0f * (float)t)) * 0.5f);
-    i = max(0, min(i, nb - 1));
+    i = i < 0 ? 0 : (i > nb - 1 ? nb - 1 : i);
     while (i > 0 && i * nb - (i * (i - 1)) / 2 > t)
         --i;
     while (i + 1 < nb && (i + 1) * nb - ((i + 1) * i) / 2 <= t)
