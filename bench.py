@@ -139,10 +139,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_sample(seconds=12.0, min_gens=3):
+def oracle_sample(seconds=12.0, min_gens=3, threads=None):
     """Times the CPU oracle on the same workload for a bounded number of
-    generations (about `seconds` of host CPU time)."""
+    generations (about `seconds` of host CPU time), on all host cores or on
+    `threads` of them."""
     import oracle
+    if threads:
+        prev = oracle.num_threads()
+        oracle.set_num_threads(threads)
+        try:
+            return oracle_sample(seconds, min_gens)
+        finally:
+            oracle.set_num_threads(prev)
     pop = oracle.init_population(M, P, SEED)
     F = oracle.fitness(pop, oracle.FIT_SQ)
     t0 = time.perf_counter()
@@ -907,6 +915,11 @@ def main():
         gps, ngen, dt, cores = oracle_sample()
         cpu = {"value": gps, "unit": "generations/s", "cores": cores, "kind": "oracle",
                "sample": f"{ngen} generations of the same workload in {dt:.1f} s"}
+        try:  # the single-core figure is context: it must not break the bench line
+            gps1, ngen1, dt1, _ = oracle_sample(seconds=4.0, min_gens=2, threads=1)
+            cpu["one_core"] = {"value": gps1, "sample": f"{ngen1} generations in {dt1:.1f} s on 1 thread"}
+        except Exception as e:
+            cpu["one_core"] = {"error": str(e)[:200]}
 
     if rank == 0:
         line = {
