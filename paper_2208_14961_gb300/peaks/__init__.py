@@ -1,5 +1,6 @@
-"""Throughput microbenchmarks (popcount, dp4a, int8 mma.sync) used as the
-compute roof of the Gram paths; built into _build/libpeaks.so."""
+"""Throughput microbenchmarks used as the compute roofs of the kernels
+(popcount, dp4a, IMAD, warp-level s8 and e4m3 MMA, FP64 and FP32 FMA), the
+L2 read rate and the grid-barrier latency; built into _build/libpeaks.so."""
 import ctypes
 import os
 import subprocess
