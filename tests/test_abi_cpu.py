@@ -120,3 +120,15 @@ def test_gram_real_empty_batch_accepts_null_buffers(lib):
     from paper_2208_14961_gb300 import hadga
     assert lib.ga_gram_real_batch(None, None, 1, 8, 0, None) == hadga.GA_OK
     assert lib.ga_gram_real_batch(None, None, 0, 256, 0, None) == hadga.GA_OK
+
+
+def test_binding_constants_match_the_header():
+    """Every enum value include/hadga.h declares has the same value in the
+    binding (GA_FIT_SQ -> FIT_SQ, GA_PATH_POPC -> PATH_POPC, ...)."""
+    from paper_2208_14961_gb300 import hadga
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    consts = dict((n, int(v)) for n, v in re.findall(r"\b(GA_[A-Z0-9_]+)\s*=\s*([0-9]+)", src))
+    assert len(consts) >= 22
+    for name, value in consts.items():
+        short = name if hasattr(hadga, name) else name[3:]
+        assert getattr(hadga, short) == value, name
