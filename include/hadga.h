@@ -287,11 +287,17 @@ ga_status ga_fitness_batch(const void *pop_dev, int32_t storage, int32_t m, int6
  *   pop_in, fit_in   : the population (4N matrices in `storage`, INT8 or
  *                      BITS) and its fitness, read only.
  *   parents_out,     : the 2N parents in placement order (2N matrices and
- *   parent_fit_out     2N fitness words); must not overlap pop_in.
+ *   parent_fit_out     2N fitness words).  Neither output may overlap
+ *                      pop_in, fit_in or the other output (GA_EINVAL).
  * N is limited to 1..8192 (P <= 32768); larger N is rejected with
  * GA_EINVAL.  No cudaMalloc, cudaFree or allocating routine is called.  The
  * first call on a device looks up the array's device address (with that
- * device current) and should therefore come before any stream capture.
+ * device current); under lazy module loading (CUDA's default) it is also
+ * the call that loads the library's device code on that device, which can
+ * take device memory.  So make one warm-up call per device before any
+ * region that forbids allocation or stream capture.  The address is kept
+ * per device ordinal and is invalid once that device's context is
+ * destroyed (cudaDeviceReset): do not call this entry point afterwards.
  * Every call shares the one array and leaves its contents behind (the parts
  * that must start at zero are cleared by each call), so calls that overlap
  * on the GPU -- on different streams, or from different threads -- race.

@@ -7,9 +7,18 @@
 // allocators that forbid out-of-pool allocations), or code on a hot path
 // where an allocation would implicitly synchronise the device.  For them the
 // scratch of the selection lives in one file-scope device array of fixed
-// size, reserved when the library is loaded and held by every GPU that loads
-// it until the process exits.
+// size, held by every GPU that loads the library's device code until the
+// process exits.  Under CUDA's default lazy module loading that code (and
+// the array with it) is loaded on a device at its first use -- the first
+// call of this entry point or of any other kernel of this file -- and that
+// load can itself take device memory, so one warm-up call per device must
+// come before any region that forbids allocation or stream capture.  The
+// device address found by that first call is kept per device ordinal; it
+// belongs to the device's current (primary) context and must not be used
+// after that context is destroyed (cudaDeviceReset), which this library
+// cannot detect.
 #include <mutex>
+#include <string>
 
 #include "common.cuh"
 #include "hadga.h"
@@ -60,10 +69,27 @@ extern "C" ga_status ga_select_static(const void *pop_in, const uint32_t *fit_in
     if ((((uintptr_t)pop_in) | ((uintptr_t)fit_in) | ((uintptr_t)parents_out) | ((uintptr_t)parent_fit_out)) & 15u)
         return fail(GA_EINVAL, "ga_select_static: buffers must be 16-byte aligned");
     const size_t mat = matrix_bytes(storage, m);
-    const uintptr_t in0 = (uintptr_t)pop_in, in1 = in0 + (size_t)(4 * N) * mat;
-    const uintptr_t o0 = (uintptr_t)parents_out, o1 = o0 + (size_t)(2 * N) * mat;
-    if (o0 < in1 && in0 < o1)
-        return fail(GA_EINVAL, "ga_select_static: parents_out must not overlap pop_in");
+    // every output is written while the inputs are still read (the gather
+    // reads fit_in[src] for any src while parent_fit_out[p] is written), so
+    // no output may share bytes with an input or with the other output
+    struct Span {
+        uintptr_t lo, hi;
+        const char *name;
+    };
+    const Span in[2] = {{(uintptr_t)pop_in, (uintptr_t)pop_in + (size_t)(4 * N) * mat, "pop_in"},
+                        {(uintptr_t)fit_in, (uintptr_t)fit_in + (size_t)(4 * N) * 4u, "fit_in"}};
+    const Span out[2] = {{(uintptr_t)parents_out, (uintptr_t)parents_out + (size_t)(2 * N) * mat, "parents_out"},
+                         {(uintptr_t)parent_fit_out, (uintptr_t)parent_fit_out + (size_t)(2 * N) * 4u,
+                          "parent_fit_out"}};
+    auto overlap = [](const Span &a, const Span &b) { return a.lo < b.hi && b.lo < a.hi; };
+    for (const Span &o : out)
+        for (const Span &i : in)
+            if (overlap(o, i)) {
+                set_thread_error((std::string("ga_select_static: ") + o.name + " must not overlap " + i.name).c_str());
+                return GA_EINVAL;
+            }
+    if (overlap(out[0], out[1]))
+        return fail(GA_EINVAL, "ga_select_static: parents_out must not overlap parent_fit_out");
 
     // set-up, once per device, with that device current: the device address
     // of the scratch array (its host-side name is only a stand-in)

@@ -132,3 +132,27 @@ def test_binding_constants_match_the_header():
     for name, value in consts.items():
         short = name if hasattr(hadga, name) else name[3:]
         assert getattr(hadga, short) == value, name
+
+
+# ga_select_static: every output must stay clear of every input and of the
+# other output (the gather writes parent_fit_out[p] while fit_in[src] is still
+# read).  Buffers are fake addresses: validation answers before any device call.
+_N_SS, _M_SS = 8, 20          # BITS storage: 80 bytes per matrix
+_POP, _FIT = 0x100000, 0x200000
+_PAR, _PFIT = 0x300000, 0x400000
+
+
+@pytest.mark.parametrize("par,pfit,what", [
+    (_POP + 16, _PFIT, "parents_out must not overlap pop_in"),
+    (_PAR, _FIT, "parent_fit_out must not overlap fit_in"),
+    (_FIT - 16, _PFIT, "parents_out must not overlap fit_in"),
+    (_PAR, _POP + 4 * _N_SS * 80 - 16, "parent_fit_out must not overlap pop_in"),
+    (_PAR, _PAR + 2 * _N_SS * 80 - 16, "parents_out must not overlap parent_fit_out"),
+])
+def test_select_static_rejects_every_overlap(lib, par, pfit, what):
+    from paper_2208_14961_gb300 import hadga
+    st = lib.ga_select_static(ctypes.c_void_p(_POP), ctypes.c_void_p(_FIT), ctypes.c_void_p(par),
+                              ctypes.c_void_p(pfit), hadga.STORE_BITS, _M_SS, _N_SS, 0, 0, 1, None)
+    assert st == hadga.GA_EINVAL
+    assert what in hadga.last_error()
+

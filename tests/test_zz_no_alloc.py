@@ -1,14 +1,24 @@
 """ga_select_static: the selection step for callers that cannot allocate
 device memory while it runs (its scratch is a fixed array inside the
-library).  Checked against the context-based ga_select, bit for bit, on two
-calls in a row.  Named to be collected last."""
+library).  Checked against the context-based ga_select and the oracle's
+selection, bit for bit, on two calls in a row.  Named to be collected last."""
 import numpy as np
 import pytest
 import torch
 
+import oracle
 from gpu_util import need_gpu
 
 pytestmark = pytest.mark.gpu
+
+
+def _as_int8(h, t, storage, m, P):
+    if storage == h.STORE_INT8:
+        return t.cpu().numpy().copy()
+    out = h.empty_population(h.STORE_INT8, m, P)
+    h.ga_convert(t, storage, out, h.STORE_INT8, m, P)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
 
 
 @pytest.mark.parametrize("storage,m,N", [(1, 20, 2500), (0, 12, 8192)])
@@ -33,6 +43,12 @@ def test_select_static_matches_ga_select(storage, m, N):
         assert ref.generation() == gen
         assert torch.equal(parents, ref.pop[:2 * N])
         assert torch.equal(pfit, ref.fit[:2 * N])
+        # and the oracle's selection of the same generation (Sec. 3.3)
+        host_in = _as_int8(h, pop_in, storage, m, 4 * N)
+        F = fit_in.cpu().numpy().view(np.uint32).astype(np.uint64)
+        oracle.select(host_in, F, N, seed, pop_id, gen)
+        assert np.array_equal(_as_int8(h, parents, storage, m, 2 * N), host_in[:2 * N])
+        assert np.array_equal(pfit.cpu().numpy().view(np.uint32).astype(np.uint64), F[:2 * N])
         # next call: the population after this selection
         pop_in = ref.pop.clone()
         fit_in = ref.fit.clone()
