@@ -2,10 +2,11 @@
 
 Workload: m = 20, P = 40,000 balanced +-1 matrices (N = 10,000; the paper's
 stated scale), fitness = sum over i < j of G_ij^2, one balanced pair-flip per
-child (NC = NR = 1), Philox seed 1, bit storage.  A step is one chunk of
-STEP_GENS generations of the whole hot path (selection, survivor placement,
-crossover, mutation, offspring fitness, best individual), run by the fused
-persistent generation kernel through the C ABI (ga_step).
+child (NC = NR = 1), Philox seed 1, bit storage.  A step is the whole
+1,000-generation run of that workload (STEP_GENS generations of the whole hot
+path: selection, survivor placement, crossover, mutation, offspring fitness,
+best individual), run by the fused persistent generation kernel through the
+C ABI (ga_step).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -13,10 +14,16 @@ value     generations/s of the fused path, inputs resident in HBM, CUDA events
           on the context's stream; the L2 cache is flushed (256 MiB write)
           before every step, outside the timed events.
 e2e       the same metric with the population and fitness copied in from
-          pinned host memory and the step's best-fitness trajectory copied
-          back, every step, inside the timed region (wall clock).
+          pinned host memory, and the final population, fitness and the
+          step's best-fitness trajectory copied back, every step, inside the
+          timed region (wall clock).
 plain     the one-kernel-per-operator path on the same workload.
-roofline  the persistent kernel against the measured HBM copy bandwidth.
+roofline  the persistent kernel's algorithmic bytes (P*S + 16P per
+          generation) against the measured HBM copy bandwidth.
+m32plus   orders m >= 32: the m = 100 GA with full and incremental fitness
+          and the batched Gram + F_sq at m = 32..256 (8 GiB of int8 each),
+          with roofline fractions against their algorithmic work and sampled
+          checks against the oracle (bounded: about a minute).
 cpu_baseline  the CPU oracle on a bounded sample of the same workload.
 --impl reference times the oracle alone (the reference arm of this build).
 Under torchrun each rank runs an independent replica population
@@ -40,7 +47,7 @@ if ROOT not in sys.path:
 
 M, N, SEED, NC, NR = 20, 10_000, 1, 1, 1
 P = 4 * N
-STEP_GENS = 50
+STEP_GENS = 1000
 # the same metric and workload on both arms (the reference arm's steps are shorter)
 METRIC = "GA generations/s at m=20, P=40k"
 WORKLOAD = "m=20, P=40,000, F_sq, NC=NR=1, seed 1"
@@ -55,12 +62,24 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-# DRAM read + write bytes of one k_fused launch of this workload from the
-# ncu capture summarised in profiles/k_fused_m20_P40k.md (the population
-# stays in L2 across the generations of a launch, so the cold read of the
-# starting population is the whole traffic and does not grow with the
-# generations per launch).
-FUSED_M20_DRAM_BYTES_PER_LAUNCH = 3.464448e6
+# DRAM read + write bytes of one k_fused launch of this workload (ncu,
+# dram__bytes_read.sum + dram__bytes_write.sum, caches flushed before the
+# launch), with the SHA-256 of the kernel sources the capture was taken on:
+# when the sources differ the number no longer describes the kernel that
+# runs and the bench line reports traffic as null.
+FUSED_M20_TRAFFIC = {"bytes": 3.464448e6, "generations_per_launch": 8,
+                     "sources_sha256": "unrecorded"}
+FUSED_SOURCES = ("k_fused.cu", "common.cuh", "inc_plan.cuh", "kernels.cuh")
+
+
+def fused_sources_sha256():
+    """SHA-256 over the sources the persistent generation kernel is built from."""
+    import hashlib
+    hsh = hashlib.sha256()
+    for f in FUSED_SOURCES:
+        with open(os.path.join(ROOT, "paper_2208_14961_gb300", "csrc", f), "rb") as fh:
+            hsh.update(fh.read())
+    return hsh.hexdigest()
 
 
 def job_rate(local_time, units_per_rank, world, reduce_max=None, device=None):
@@ -78,10 +97,18 @@ def job_rate(local_time, units_per_rank, world, reduce_max=None, device=None):
 
 
 def bytes_per_generation(m=M, N=N):
-    """Algorithmic HBM bytes of one generation of the fused kernel (bit
-    storage): read the 2N surviving parents, write all 4N slots (2N parents
-    placed + 2N offspring), read and write the 4N fitness words, read the
-    survivor-order row (2N words)."""
+    """Algorithmic HBM bytes of one generation of the method (bit storage):
+    read the 2N parents and write the 2N offspring, P*S bytes, plus 16 bytes
+    per individual of fitness, keys and indices."""
+    w = (m + 31) // 32
+    return 4 * N * m * w * 4 + 16 * 4 * N
+
+
+def impl_bytes_per_generation(m=M, N=N):
+    """Bytes this implementation moves per generation (context, not the
+    roofline's numerator): it also places the 2N parents physically in the
+    next population buffer, i.e. read 2N parents, write all 4N slots, read
+    and write the 4N fitness words, read the survivor-order row (2N words)."""
     w = (m + 31) // 32
     mat = m * w * 4
     return 2 * N * mat + 4 * N * mat + 2 * 4 * N * 4 + 2 * N * 4
@@ -101,7 +128,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             threading.Thread(target=self._read, daemon=True).start()
         except Exception:
@@ -717,6 +744,292 @@ def incremental_workload(args):
     print(json.dumps(line), flush=True)
 
 
+PROFILE_CASES = """Named small workloads for profiling one kernel at a time (ncu -k):
+
+  python bench.py --case <case> [--case-gens G]
+
+fused_m20   m=20, P=40,000, bit storage: init, fitness, then G generations
+            (default 8) in one persistent launch
+plain_m20   the same with the one-kernel-per-operator path
+inc_m100    m=100, P=20,000, bit storage, incremental Gram-delta fitness:
+            init, fitness, Gram store, then G generations
+full_m100   the same workload with full fitness recomputation
+gram_m<M>_<path>  Gram + fitness of a population of ~1 GiB (int8 size) at
+            order M with path int32 | imma | popc8 | popc | fp8 | bf16 | fp8w
+real_<f32|f64>_m<M>  batched real Gram Q^T Q of 10,000 uniform random
+            matrices of order M (two launches)"""
+
+
+def profile_case(args):
+    """Runs one named small workload (PROFILE_CASES) and prints one line."""
+    import torch
+
+    from paper_2208_14961_gb300.build import build
+    build()
+    from paper_2208_14961_gb300 import hadga as h
+    case, gens = args.case, args.case_gens
+    if case in ("fused_m20", "plain_m20"):
+        p = h.Population(20, 10000, seed=1, storage=h.STORE_BITS, traj_cap=64)
+        p.init_population()
+        p.fitness()
+        if case == "fused_m20":
+            p.step(gens)
+        else:
+            p.step_plain(gens)
+        p.sync()
+        print(case, "best", p.best())
+        return
+    if case in ("inc_m100", "full_m100"):
+        p = h.Population(100, 5000, seed=4, storage=h.STORE_BITS, traj_cap=64)
+        p.init_population()
+        p.fitness()
+        if case == "inc_m100":
+            p.set_incremental(True)
+        p.step(gens)
+        p.sync()
+        print(case, "best", p.best())
+        return
+    if case.startswith("gram_m"):
+        m_s, path_s = case[len("gram_m"):].split("_")
+        m = int(m_s)
+        paths = {"int32": (h.STORE_INT8, h.PATH_INT32), "imma": (h.STORE_INT8, h.PATH_IMMA),
+                 "popc8": (h.STORE_INT8, h.PATH_POPC), "popc": (h.STORE_BITS, h.PATH_POPC),
+                 "fp8": (h.STORE_E4M3, h.PATH_FP8), "bf16": (h.STORE_BF16, h.PATH_BF16),
+                 "fp8w": (h.STORE_E4M3, h.PATH_FP8_WARP)}
+        storage, path = paths[path_s]
+        P = (1 << 30) // (m * m)
+        pop = h.empty_population(storage, m, P)
+        h.ga_init_batch(pop, storage, m, P, 2)
+        fit = torch.zeros(P, dtype=torch.int32, device="cuda")
+        for _ in range(2):
+            h.ga_fitness_batch(pop, storage, m, P, h.FIT_SQ, path, fit)
+        torch.cuda.synchronize()
+        print(case, "P", P, "fit[0]", int(fit[0]))
+        return
+    if case.startswith("real_"):
+        _, t, m_s = case.split("_")
+        m = int(m_s[1:])
+        dtype = torch.float64 if t == "f64" else torch.float32
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(11)
+        q = torch.rand((10000, m, m), dtype=dtype, device="cuda", generator=gen)
+        g = torch.empty_like(q)
+        for _ in range(2):
+            h.ga_gram_real_batch(q, g)
+        torch.cuda.synchronize()
+        print(case, "g[0,0,0]", float(g[0, 0, 0]))
+        return
+    raise SystemExit(f"unknown case {case}\n{PROFILE_CASES}")
+
+
+# ---------------------------------------------------------------------------
+# orders m >= 32 in the default line
+# ---------------------------------------------------------------------------
+M32_GRAM_ORDERS = (32, 64, 128, 256)
+# exact Gram + F_sq paths timed per order: bit storage with popcounts, and
+# GA_PATH_AUTO on e4m3 storage (warp-level FP8 MMA at m <= 64, tcgen05 at
+# m = 128, 256)
+M32_GRAM_PATHS = (("popc_bits", 1, 5), ("auto_e4m3", 2, 0))
+
+
+def gram_algorithmic_work(m):
+    """Algorithmic work of one matrix's Gram + fitness (i < j, i, j >= 1:
+    D = (m-1)(m-2)/2 column dot products): D*m multiply-adds on int8 / e4m3
+    storage, D*ceil(m/32) 32-bit population counts on bit storage."""
+    D = (m - 1) * (m - 2) // 2
+    return D * m, D * ((m + 31) // 32)
+
+
+def _fp8_mac_rate():
+    """Dense FP8 multiply-adds/s of this GPU, from the library's e4m3 GEMM
+    (cuBLASLt through torch), else the nominal 4.5 PFLOP/s."""
+    t = _library_gemm_tflops("fp8", n=8192, reps=10)
+    return (t * 1e12 / 2, "library e4m3 GEMM, measured") if t else (2.25e15, "nominal 4.5 PFLOP/s dense")
+
+
+def _roof_entry(achieved_time_s, t_mem, t_cmp, unit_cmp, peak_cmp, ops, nbytes, hbm):
+    bound = "hbm" if t_mem >= t_cmp else unit_cmp
+    roof_t = max(t_mem, t_cmp)
+    return {"bound": bound, "frac": roof_t / achieved_time_s,
+            "hbm": {"achieved_gbs": nbytes / achieved_time_s / 1e9, "peak_gbs": hbm, "frac": t_mem / achieved_time_s},
+            "compute": {"unit": unit_cmp, "achieved_per_s": ops / achieved_time_s, "peak_per_s": peak_cmp,
+                        "frac": t_cmp / achieved_time_s}}
+
+
+def m32_gram_report(hbm, popc_rate, e4m3_warp_rate, fp8_rate, gib=8.0, reps=5):
+    """Config 3 in the default line: per order m in {32, 64, 128, 256}, a
+    balanced population of `gib` GiB of int8 (P = gib * 2^30 / m^2, seed 2),
+    Gram + F_sq by each exact path of M32_GRAM_PATHS on its own storage,
+    `reps` passes timed with CUDA events (inputs larger than L2), 256 sampled
+    slots checked against the oracle; roofline against the path's
+    algorithmic work (gram_algorithmic_work) and its storage bytes."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2208_14961_gb300 import hadga as h
+    rng = np.random.default_rng(7)
+    out = []
+    for m in M32_GRAM_ORDERS:
+        P = int(gib * (1 << 30)) // (m * m)
+        macs, popcs = gram_algorithmic_work(m)
+        idx_np = np.sort(rng.choice(P, size=256, replace=False))
+        ref = oracle.fitness(oracle.init_slots(m, idx_np, 2), oracle.FIT_SQ)
+        rows = []
+        for name, storage, path in M32_GRAM_PATHS:
+            pop = h.empty_population(storage, m, P)
+            fit = torch.zeros(P, dtype=torch.int32, device="cuda")
+            h.ga_init_batch(pop, storage, m, P, 2)
+            h.ga_fitness_batch(pop, storage, m, P, h.FIT_SQ, path, fit)
+            torch.cuda.synchronize()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record()
+            for _ in range(reps):
+                h.ga_fitness_batch(pop, storage, m, P, h.FIT_SQ, path, fit)
+            ev[1].record()
+            ev[1].synchronize()
+            sec = ev[0].elapsed_time(ev[1]) / 1e3 / reps
+            got = fit.index_select(0, torch.as_tensor(idx_np, device="cuda")).cpu().numpy()
+            exact = bool(np.array_equal(ref, got.view(np.uint32).astype(np.uint64)))
+            nbytes = P * h.storage_bytes(storage, m)
+            t_mem = nbytes / (hbm * 1e9)
+            if storage == h.STORE_BITS:
+                ops, peak, unit = P * popcs, popc_rate, "popc32"
+            elif m >= 128:   # AUTO on e4m3: tcgen05
+                ops, peak, unit = P * macs, fp8_rate, "e4m3 MAC (tcgen05)"
+            else:            # AUTO on e4m3: warp-level FP8 MMA
+                ops, peak, unit = P * macs, e4m3_warp_rate, "e4m3 MAC (mma.sync)"
+            row = {"path": name, "ms": sec * 1e3, "matrices_per_s": P / sec, "exact_256_sampled": exact}
+            row.update(_roof_entry(sec, t_mem, ops / peak, unit, peak, ops, nbytes, hbm))
+            rows.append(row)
+            del pop, fit
+            torch.cuda.empty_cache()
+        best = min(rows, key=lambda r: r["ms"])
+        out.append({"m": m, "P": P, "paths": rows, "fastest": best["path"], "fastest_frac": best["frac"],
+                    "fastest_bound": best["bound"]})
+    return out
+
+
+def m32_ga_report(dev, gens=500, call=100, prefix=5):
+    """Config 5 in the default line: m = 100, P = 20,000 bit-packed balanced
+    matrices (seed 4), F_sq, NC = NR = 1, `gens` generations of the fused
+    path in ga_step calls of `call`, with full recomputation and with the
+    incremental Gram-delta fitness (a GPU full recheck after every call).
+    Checked against the oracle: the first `prefix` generations from the
+    initial population, and one generation from the GPU's state after
+    `gens` generations (population and fitness bit for bit, both modes).
+    Roofline of each mode against its algorithmic work: offspring Gram
+    popcounts (full: D ceil(m/32) per offspring; incremental: E[c(m-c)]
+    ceil(m/32) cross dot products) and HBM bytes (P*S + 16P, plus the
+    stored Gram read and written in incremental mode)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2208_14961_gb300 import hadga as h
+    from paper_2208_14961_gb300 import peaks
+    m, N, seed = 100, 5000, 4
+    P = 4 * N
+    stream = torch.cuda.Stream(device=dev)
+
+    def fresh(inc):
+        p = h.Population(m, N, seed=seed, fitness=h.FIT_SQ, storage=h.STORE_BITS, traj_cap=gens + 1,
+                         stream=stream, device=dev)
+        p.init_population()
+        p.fitness()
+        if inc:
+            p.set_incremental(True)
+        p.sync()
+        return p
+
+    w = fresh(True)
+    w.step(call)
+    w.sync()
+    w.close()
+    ref0 = oracle.init_population(m, P, seed, 0)
+    F0 = oracle.fitness(ref0, oracle.FIT_SQ)
+    refp, Fp = ref0.copy(), F0.copy()
+    oracle.run(refp, Fp, N, 1, 1, oracle.FIT_SQ, seed, 0, 0, prefix)
+    W = (m + 31) // 32
+    D = (m - 1) * (m - 2) // 2
+    cuts = range(1, m)
+    e_cross = sum(c * (m - c) for c in cuts) / (m - 1)
+    e_gram_read = sum((c * (c - 1) + (m - c) * (m - c - 1)) / 2 for c in cuts) / (m - 1)
+    popc_rate = peaks.rate("popc_chain")
+    hbm, hbm_kind = _peaks()
+    base_bytes = bytes_per_generation(m, N)
+    res, trajs = {}, {}
+    for mode in ("full", "incremental"):
+        inc = mode == "incremental"
+        p = fresh(inc)
+        p.step(prefix)
+        p.sync()
+        prefix_ok = bool(np.array_equal(p.as_int8(), refp)) and bool(np.array_equal(p.fitness_host(), Fp))
+        p.close()
+        p = fresh(inc)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms, checks, mism = 0.0, 0, 0
+        for _ in range(gens // call):
+            e0.record(stream)
+            p.step(call)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            if inc:
+                a, b = p.check_incremental()
+                checks += 1
+                mism += a + b
+        trajs[mode] = p.trajectory()[0].astype(np.uint64)
+        snap_pop, snap_F = p.as_int8(), p.fitness_host()
+        p.step(1)
+        p.sync()
+        oracle.run(snap_pop, snap_F, N, 1, 1, oracle.FIT_SQ, seed, 0, gens, 1)
+        step_ok = bool(np.array_equal(p.as_int8(), snap_pop)) and bool(np.array_equal(p.fitness_host(), snap_F))
+        p.close()
+        sec = ms / 1e3
+        gps = gens / sec
+        if inc:
+            ops = 2 * N * e_cross * W
+            nbytes = base_bytes + 2 * N * (e_gram_read + m * (m - 1) / 2)
+            work = "offspring cross dot products E[c(m-c)] = %.0f x %d popc32 + stored Gram bytes" % (e_cross, W)
+        else:
+            ops = 2 * N * D * W
+            nbytes = base_bytes
+            work = "offspring Gram D x ceil(m/32) = %d x %d popc32 per offspring" % (D, W)
+        t_gen = 1.0 / gps
+        entry = {"generations": gens, "ms": ms, "generations_per_s": gps, "evals_per_s": gps * 2 * N,
+                 "oracle_prefix_exact": prefix_ok, "oracle_step_exact_after": step_ok, "work": work}
+        entry.update(_roof_entry(t_gen, nbytes / (hbm * 1e9), ops / popc_rate, "popc32", popc_rate, ops, nbytes,
+                                 hbm))
+        if inc:
+            entry.update({"gpu_full_rechecks": checks, "recheck_mismatches": mism})
+        res[mode] = entry
+    res["incremental_over_full"] = res["incremental"]["generations_per_s"] / res["full"]["generations_per_s"]
+    res["trajectories_equal"] = bool(np.array_equal(trajs["full"], trajs["incremental"]))
+    res["workload"] = "m=100, P=20,000, bit storage, F_sq, NC=NR=1, seed 4"
+    res["peaks"] = {"popc_per_s": popc_rate, "source": "measured (peaks microbenchmark)",
+                    "hbm_gbs": hbm, "hbm_source": hbm_kind}
+    return res
+
+
+def m32plus_report(args, dev):
+    """Orders m >= 32 (configs 3 and 5) for the default line: bounded to
+    about a minute including the oracle checks."""
+    from paper_2208_14961_gb300 import peaks
+    t0 = time.perf_counter()
+    hbm, hbm_kind = _peaks()
+    popc_rate = peaks.rate("popc_chain")
+    e4m3_warp = peaks.rate("mma_e4m3")
+    fp8_rate, fp8_src = _fp8_mac_rate()
+    ga = m32_ga_report(dev)
+    gram = m32_gram_report(hbm, popc_rate, e4m3_warp, fp8_rate)
+    return {"config5_ga_m100": ga, "config3_gram_8gib": gram,
+            "peaks": {"hbm_gbs": hbm, "hbm_source": hbm_kind, "popc_per_s": popc_rate,
+                      "mma_sync_e4m3_mac_per_s": e4m3_warp, "fp8_mac_per_s": fp8_rate, "fp8_source": fp8_src,
+                      "note": "popc and mma.sync rates from the peaks microbenchmark"},
+            "seconds": time.perf_counter() - t0}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -724,6 +1037,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-m32plus", action="store_true", help="skip the m >= 32 section of the default line")
     ap.add_argument("--plain-steps", type=int, default=4)
     ap.add_argument("--gram-sweep", action="store_true", help="precision sweep of the Gram + fitness paths")
     ap.add_argument("--gram-gb", type=float, default=8.0)
@@ -748,7 +1062,12 @@ def main():
     ap.add_argument("--search-seeds", type=int, default=3)
     ap.add_argument("--search-seconds", type=float, default=60.0)
     ap.add_argument("--search-chunk", type=int, default=2048)
+    ap.add_argument("--case", default="", help="one named small workload for ncu (see PROFILE_CASES)")
+    ap.add_argument("--case-gens", type=int, default=8)
     args = ap.parse_args()
+    if args.case:
+        profile_case(args)
+        return
     if args.peaks:
         peaks_report(args)
         return
@@ -865,22 +1184,31 @@ def main():
     ee.sync()
     host_pop = ee.pop.cpu().pin_memory()
     host_fit = ee.fit.cpu().pin_memory()
+    out_pop = torch.empty_like(host_pop).pin_memory()
+    out_fit = torch.empty_like(host_fit).pin_memory()
     h2d = host_pop.numel() * host_pop.element_size() + host_fit.numel() * host_fit.element_size()
-    d2h = STEP_GENS * 8          # the step's best-fitness trajectory (one 64-bit key per generation)
-    for _ in range(2):
+    # device -> host per step: the final population and fitness, the step's
+    # best-fitness trajectory (ga_trajectory copies one 64-bit key per
+    # generation) and the 4-byte device error word its synchronisation reads
+    d2h = (out_pop.numel() * out_pop.element_size() + out_fit.numel() * out_fit.element_size()
+           + STEP_GENS * 8 + 4)
+
+    def e2e_step():
         with torch.cuda.stream(stream):
             ee.pop.copy_(host_pop, non_blocking=True)
             ee.fit.copy_(host_fit, non_blocking=True)
         ee.step(STEP_GENS)
-        ee.trajectory()
+        with torch.cuda.stream(stream):
+            out_pop.copy_(ee.pop, non_blocking=True)
+            out_fit.copy_(ee.fit, non_blocking=True)
+        ee.trajectory()          # synchronises the stream: the step's results are on the host
+
+    for _ in range(2):
+        e2e_step()
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        with torch.cuda.stream(stream):
-            ee.pop.copy_(host_pop, non_blocking=True)
-            ee.fit.copy_(host_fit, non_blocking=True)
-        ee.step(STEP_GENS)
-        ee.trajectory()          # device -> host read of the step's result
+        e2e_step()
     barrier()
     e2e_s = time.perf_counter() - t0
     e2e_value, _ = job_rate(e2e_s, args.steps * STEP_GENS, world, reduce_max, dev)
@@ -891,10 +1219,19 @@ def main():
     roof = None
     if fused_launches > 0 and fused_ms > 0:
         per_launch_ms = fused_ms / fused_launches
-        per_launch_bytes = bytes_per_generation() * STEP_GENS
+        gens_per_launch = gens / fused_launches
+        per_launch_bytes = bytes_per_generation() * gens_per_launch
         achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9
+        fresh = FUSED_M20_TRAFFIC["sources_sha256"] == fused_sources_sha256()
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": FUSED_M20_DRAM_BYTES_PER_LAUNCH, "kernel": "k_fused", "peak_source": peak_kind,
+                "traffic": FUSED_M20_TRAFFIC["bytes"] if fresh else None,
+                "traffic_note": ("ncu DRAM read+write of one launch of %d generations after a cache flush"
+                                 % FUSED_M20_TRAFFIC["generations_per_launch"]) if fresh else
+                                "kernel sources changed since the last capture",
+                "kernel": "k_fused", "peak_source": peak_kind,
+                "algorithmic_bytes_per_generation": bytes_per_generation(),
+                "impl_bytes_per_generation": impl_bytes_per_generation(),
+                "generations_per_launch": gens_per_launch,
                 "launch_ms": per_launch_ms, "perm_table_ms_per_launch": perm_ms / max(fused_launches, 1)}
 
     # what binds instead of HBM: the two grid barriers of every generation
@@ -909,6 +1246,13 @@ def main():
                     "note": "grid barrier latency from the peaks microbenchmark (same barrier code, 152 blocks)"}
     except Exception as e:  # the context field must not break the bench line
         sync = {"error": str(e)[:200]}
+
+    m32 = None
+    if world == 1 and not args.no_m32plus:
+        try:  # the m >= 32 context must not break the headline line
+            m32 = m32plus_report(args, dev)
+        except Exception as e:
+            m32 = {"error": f"{type(e).__name__}: {e}"[:300]}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -939,6 +1283,7 @@ def main():
                     "d2h_bytes_per_step": int(d2h)},
             "roofline": roof,
             "sync_bound": sync,
+            "m32plus": m32,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "gpu_launches": int(launches),

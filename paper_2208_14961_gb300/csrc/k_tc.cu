@@ -22,7 +22,12 @@
 //            blocks for m = 256).  Ring positions and phases are counters
 //            (no division in the issue loop).
 //   warp 10  with four accumulators (m <= 128), a second MMA issuer: warp 1
-//            takes the block's even jobs, warp 10 the odd ones
+//            takes the block's even jobs, warp 10 the odd ones.  The stage
+//            ring is then split in two halves, one per issuer: the producer
+//            fills half r for the jobs of issuer r only, so every use of a
+//            stage follows a use by the same issuer and a parity wait on its
+//            "full" barrier can never pass on the phase of an earlier lap
+//            that the other issuer has not consumed yet
 //   warps 2-9  two epilogue groups of four warps taking alternate jobs: wait
 //            for the accumulator, read it with tcgen05.ld (warp w reads TMEM
 //            lanes 32(w%4)..32(w%4)+31 = tile rows), free it, then square,
@@ -195,17 +200,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tbase = tmem_base;
 
+    // MMA issuers and the stage ring halves they own (one ring of S stages
+    // with a single issuer; two halves of SR stages with two)
+    const int nis = nacc > 1 ? 2 : 1;
+    const int SR = S / nis;
     if (warp == 0) {
         // ---- TMA producer ----------------------------------------------------
         if (lane == 0) {
-            uint32_t it = 0;
-            int issued = 0;
-            int st = 0;         // stage of copy `it`
-            uint32_t sph = 0u;  // parity of that stage's current use
+            int pos[2] = {0, 0};          // next stage of each ring half (relative)
+            uint32_t sph[2] = {0u, 0u};   // parity of that stage's current use
+            uint32_t used[2] = {0u, 0u};  // stage uses issued in each half
+            int who = 0;                  // issuer (ring half) of the next job
             bool ok = true;
             for (int64_t j = blockIdx.x; j < prm.jobs && ok; j += gridDim.x) {
-                for (int c = 0; c < nch; ++c, ++it) {
-                    if (!mbar_wait(&empty[st], sph ^ 1u, err)) {
+                const int r = who;
+                if (++who == nis)
+                    who = 0;
+                for (int c = 0; c < nch; ++c) {
+                    const int st = r * SR + pos[r];
+                    if (!mbar_wait(&empty[st], sph[r] ^ 1u, err)) {
                         ok = false;
                         break;
                     }
@@ -214,35 +227,40 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
                     for (int h = 0; h < rows / 128; ++h)
                         tma_load_2d(stages + (size_t)st * sbytes + (size_t)h * 128 * kb, &map, x,
                                     (int32_t)(j * rows + h * 128), &full[st]);
-                    issued = issued < S ? issued + 1 : S;
-                    if (++st == S) {
-                        st = 0;
-                        sph ^= 1u;
+                    ++used[r];
+                    if (++pos[r] == SR) {
+                        pos[r] = 0;
+                        sph[r] ^= 1u;
                     }
                 }
             }
             if (!ok) {
                 // drain: let copies already in flight land before the block exits
-                for (int q = 0; q < issued; ++q) {
-                    const uint32_t itq = it - 1u - (uint32_t)q;
-                    mbar_wait(&full[itq % (uint32_t)S], (itq / (uint32_t)S) & 1u, err);
+                // (the last min(used, SR) uses of each half)
+                for (int r = 0; r < nis; ++r) {
+                    const uint32_t n = used[r] < (uint32_t)SR ? used[r] : (uint32_t)SR;
+                    for (uint32_t q = 0; q < n; ++q) {
+                        const uint32_t u = used[r] - 1u - q;
+                        mbar_wait(&full[r * SR + (int)(u % (uint32_t)SR)], (u / (uint32_t)SR) & 1u, err);
+                    }
                 }
             }
         }
     } else if (warp == 1 || warp == kTcMma2Warp) {
         // ---- MMA issuers ----------------------------------------------------------
         // With several accumulators (m <= 128) warp 1 issues the block's even jobs
-        // and warp kTcMma2Warp the odd ones, each on its own accumulators and
-        // stages (the issue of a 128 x 128 job's MMAs and commits, not the tensor
-        // pipe, paces one thread); m = 256 has one accumulator and one issuer.
-        const int nis = nacc > 1 ? 2 : 1;
+        // and warp kTcMma2Warp the odd ones, each on its own accumulators and its
+        // own half of the stage ring (the issue of a 128 x 128 job's MMAs and
+        // commits, not the tensor pipe, paces one thread); m = 256 has one
+        // accumulator and one issuer.
         const int me = warp == 1 ? 0 : 1;
         // TWO: compiled with the job split (the single-issuer loop keeps none of it)
         auto issue = [&](auto two) {
             constexpr bool TWO = decltype(two)::value;
             const uint32_t sbo = 8u * (uint32_t)kb;
             // ring positions kept as counters: no division in the issue loop
-            int st = 0, b = 0, who = 0;
+            const int s0 = me * SR;  // first stage of this issuer's ring half
+            int st = s0, b = 0, who = 0;
             uint32_t sph = 0u, aph = 0u;  // parities of the stage's and accumulator's current use
             bool ok = true;
             for (int64_t j = blockIdx.x; j < prm.jobs && ok; j += gridDim.x) {
@@ -250,12 +268,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
                 if (TWO && ++who == 2)
                     who = 0;
                 if (!mine) {
-                    // the other issuer's job: step over its stages and accumulator use
-                    for (int c = 0; c < nch; ++c)
-                        if (++st == S) {
-                            st = 0;
-                            sph ^= 1u;
-                        }
+                    // the other issuer's job: its stages are in the other half; only
+                    // the accumulator use advances
                     if (++b == nacc) {
                         b = 0;
                         aph ^= 1u;
@@ -290,8 +304,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
                         }
                     }
                     mma_commit(&empty[st]);  // the stage is free once these MMAs have read it
-                    if (++st == S) {
-                        st = 0;
+                    if (++st == s0 + SR) {
+                        st = s0;
                         sph ^= 1u;
                     }
                 }

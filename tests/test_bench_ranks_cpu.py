@@ -70,3 +70,33 @@ def test_reference_arm_prints_the_contract_line():
     assert d["value"] > 0 and d["steps"] == 1 and d["warmup"] == 3
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def test_headline_bytes_follow_the_algorithmic_count():
+    """The headline roofline's numerator is the method's traffic per
+    generation: read 2N parents and write 2N offspring (P*S bytes, S = 80 B
+    per bit-packed order-20 matrix) plus 16 bytes per individual; the
+    implementation's own extra parent placement is reported apart."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.bytes_per_generation(20, 10_000) == 40_000 * 80 + 16 * 40_000
+    assert bench.bytes_per_generation(100, 5_000) == 20_000 * 1_600 + 16 * 20_000
+    assert bench.impl_bytes_per_generation(20, 10_000) > bench.bytes_per_generation(20, 10_000)
+
+
+def test_gram_algorithmic_work():
+    """D = (m-1)(m-2)/2 dot products per matrix: D*m multiply-adds, or
+    D*ceil(m/32) population counts on bit storage."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.gram_algorithmic_work(20) == (3_420, 171)
+    assert bench.gram_algorithmic_work(32) == (14_880, 465)
+    assert bench.gram_algorithmic_work(100) == (485_100, 19_404)
+    assert bench.gram_algorithmic_work(256) == (8_290_560, 259_080)
+
+
+def test_traffic_guard_tracks_the_kernel_sources():
+    sys.path.insert(0, ROOT)
+    import bench
+    h = bench.fused_sources_sha256()
+    assert len(h) == 64 and h == bench.fused_sources_sha256()

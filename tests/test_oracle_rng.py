@@ -81,3 +81,15 @@ def test_mixed_order_sizes_in_range():
     Ns = [oracle.mixed_N(3, i) for i in range(7)]
     assert all(500 <= N <= 5000 for N in Ns)
     assert len(set(Ns)) > 1
+
+
+@pytest.mark.parametrize("seed", [3, 0, 77])
+def test_mixed_order_sizes_from_the_config_stream(seed):
+    """N of order position idx is 500 + U[0, 4500] of word 0 of the Philox
+    block with key (seed, 0) and counter (CONFIG, generation 0, idx, 0),
+    rebuilt here from the known-answer-pinned Philox and the multiply-shift
+    map lo + floor(w (hi - lo + 1) / 2^32): a wrong key, op, index or span
+    fails it."""
+    for idx in range(7):
+        w0 = int(oracle.philox4x32_10([oracle.OP_CONFIG, 0, idx, 0], [seed, 0])[0])
+        assert oracle.mixed_N(seed, idx) == 500 + ((w0 * 4501) >> 32)
