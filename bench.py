@@ -910,7 +910,7 @@ def m32_gram_report(hbm, popc_rate, e4m3_warp_rate, fp8_rate, gib=8.0, reps=5):
     return out
 
 
-def m32_ga_report(dev, gens=500, call=100, prefix=5):
+def m32_ga_report(dev, gens=500, call=100, prefix=50):
     """Config 5 in the default line: m = 100, P = 20,000 bit-packed balanced
     matrices (seed 4), F_sq, NC = NR = 1, `gens` generations of the fused
     path in ga_step calls of `call`, with full recomputation and with the
@@ -1240,7 +1240,7 @@ def main():
         from paper_2208_14961_gb300 import peaks
         bps = peaks.rate("grid_barriers")
         if bps > 0 and fused_launches > 0:
-            gen_us = fused_ms / fused_launches / STEP_GENS * 1e3
+            gen_us = fused_ms / gens * 1e3
             sync = {"grid_barrier_us": 1e6 / bps, "barriers_per_generation": 2, "generation_us": gen_us,
                     "barrier_share": 2e6 / bps / gen_us,
                     "note": "grid barrier latency from the peaks microbenchmark (same barrier code, 152 blocks)"}

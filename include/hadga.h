@@ -168,9 +168,11 @@ ga_status ga_step_plain(ga_ctx *ctx, int32_t generations);
  * are bit-identical to ga_step_plain.  When stop_at_zero is set, stops after
  * the first generation whose best fitness is 0.  *done (may be NULL)
  * receives the number of generations run; it synchronises only when
- * stop_at_zero is set or done is not NULL.  Falls back to the plain
- * sequence when the population does not fit the fused kernel (see
- * ga_step_is_fused). */
+ * stop_at_zero is set or done is not NULL.  The fused kernel takes orders
+ * m <= 128 and P <= 262,144 whose shared-memory plan fits a block; for any
+ * other population ga_step runs the plain sequence instead (see
+ * ga_step_is_fused), or returns GA_EUNSUPPORTED with the reason in
+ * ga_last_error when the context is strict (ga_set_strict). */
 ga_status ga_step(ga_ctx *ctx, int32_t generations, int32_t stop_at_zero, int32_t *done);
 
 /* Like ga_step for n contexts at once (orders m may differ): every
@@ -224,6 +226,13 @@ ga_status ga_set_fused_grid(ga_ctx *ctx, int32_t blocks);
 /* 1 if ga_step runs the fused kernel for this context, 0 if it falls back. */
 int32_t ga_step_is_fused(const ga_ctx *ctx);
 
+/* strict != 0: ga_step and ga_step_multi never fall back to the one-kernel-
+ * per-operator path; a population the persistent kernel cannot run makes
+ * them return GA_EUNSUPPORTED (reason in ga_last_error).  Returns
+ * GA_EUNSUPPORTED at once when setting strict mode on such a context (the
+ * mode is still set), GA_OK otherwise.  Host only. */
+ga_status ga_set_strict(ga_ctx *ctx, int32_t strict);
+
 /* Best individual of the current population: least F, lowest slot on ties
  * (Sec. 6, the minimum of F).  Synchronises. */
 ga_status ga_best(ga_ctx *ctx, int64_t *slot, uint32_t *fitness);
@@ -250,6 +259,29 @@ ga_status ga_get_slot(ga_ctx *ctx, int64_t slot, int8_t *host_matrix);
 /* Message of the last failure of ctx (or of the calling thread when ctx is
  * NULL); never NULL. */
 const char *ga_last_error(const ga_ctx *ctx);
+
+/* ---- Test-only exports: failure detection without a fault ---------------- */
+
+/* Drives one of the library's bounded device waits to its limit, on purpose
+ * and without any fault (not a step of the paper; it checks the failure
+ * handling of every kernel that waits).  which = 0: the grid-wide barrier of
+ * the persistent generation kernel, launched cooperatively on two blocks
+ * that expect one more arrival than there are blocks; which = 1: the
+ * mbarrier wait of the tensor-core and bulk-copy pipelines, on a barrier
+ * nobody arrives on.  The wait gives up after budget_us microseconds
+ * (1 .. 1,000,000), records ERR_TIMEOUT (bit 0) in a fresh device error
+ * word and the kernel returns normally.  Synchronises the stream, stores
+ * the error word in *err_out and returns GA_ETIMEOUT when the timeout bit is
+ * set (GA_OK if the wait completed, which it cannot).  The CUDA context stays
+ * usable afterwards.  Allocates and frees 8 bytes of device memory. */
+ga_status ga_debug_wait_timeout(int32_t which, uint32_t budget_us, uint32_t *err_out, void *stream);
+
+/* Makes the next n device allocations of this library (context workspaces
+ * of ga_create, the Gram storage of ga_set_incremental) fail as if the
+ * device were out of memory, without calling the allocator: the failing call
+ * returns GA_ENOMEM and leaves nothing behind (no context, no allocation).
+ * n = 0 clears the hook; n < 0 is GA_EINVAL.  Process-wide. */
+ga_status ga_debug_fail_allocations(int32_t n);
 
 /* ---- Instrumentation ------------------------------------------------------ */
 

@@ -18,6 +18,19 @@ namespace {
 
 thread_local std::string g_thread_error;
 std::atomic<unsigned long long> g_launches{0};
+// test hook: allocations still to fail (ga_debug_fail_allocations)
+std::atomic<int> g_fail_allocs{0};
+
+// cudaMalloc, or a simulated out-of-memory while the test hook is armed
+cudaError_t dev_alloc(void **p, size_t bytes)
+{
+    int n = g_fail_allocs.load();
+    while (n > 0) {
+        if (g_fail_allocs.compare_exchange_weak(n, n - 1))
+            return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
 
 constexpr int32_t kVersion = 1 * 10000 + 0 * 100 + 0;
 constexpr int64_t kMaxP = int64_t(1) << 31;
@@ -54,7 +67,10 @@ struct ga_ctx {
     int fused_blocks = 0;                     // persistent blocks (0: one per SM)
     unsigned long long *ftmask = nullptr;
     uint32_t *fperm = nullptr;                // [chunk][2N] survivor orders
+    unsigned long long *fperm_keys = nullptr; // [chunk][2N] sort keys when 2N > kPermSmemMax
     int fused_ok = 0;
+    std::string fused_why;                    // why the persistent kernel cannot run this context
+    int strict = 0;                           // ga_step: GA_EUNSUPPORTED instead of the plain path
     // incremental Gram-delta mode (BITS, 32 < m <= 128)
     int incremental = 0;
     int gram_valid = 0;
@@ -147,6 +163,14 @@ extern "C" {
 
 int32_t ga_version(void) { return kVersion; }
 
+ga_status ga_debug_fail_allocations(int32_t n)
+{
+    if (n < 0)
+        return set_error(nullptr, GA_EINVAL, "n=%d must be >= 0", n);
+    g_fail_allocs.store(n);
+    return GA_OK;
+}
+
 uint64_t ga_kernel_launches(void) { return (uint64_t)g_launches.load(); }
 
 size_t ga_storage_bytes(int32_t storage, int32_t m)
@@ -203,7 +227,27 @@ ga_status ga_create(const ga_config *cfg, void *pop_dev, uint32_t *fit_dev, void
 
     const int64_t P = c->P, n_keep = 2 * c->N, tiles = (P + 31) / 32;
     const size_t bits_bytes = (size_t)P * c->m * c->W * 4u;
-    const bool fused_fit = (uint64_t)n_keep <= kPermSmemMax;
+    // can the persistent kernel run this population alone?  (orders up to
+    // kFusedMaxM, tiles up to kFusedMaxTiles, and its shared memory: the
+    // tile masks and their prefix, the staged histograms, the warp buffers)
+    bool fused_fit = c->m <= kFusedMaxM && (uint64_t)tiles <= kFusedMaxTiles;
+    if (!fused_fit) {
+        c->fused_why = c->m > kFusedMaxM ? "the persistent kernel builds orders m <= 128"
+                                         : "the persistent kernel takes P <= 262144 (8192 tiles of 32 slots)";
+    } else {
+        FusedParams fp{};
+        fp.npop = 1;
+        fp.total_tiles = (uint32_t)tiles;
+        fp.warp_buf_words = c->m > 32 ? ((2 * c->m * c->W + col_set_words(c->m, c->W) + 3) & ~3) : 0;
+        const size_t need = fused_smem_bytes(fp), have = fused_smem_limit();
+        if (need > have) {
+            fused_fit = false;
+            char why[160];
+            snprintf(why, sizeof(why), "the persistent kernel would need %zu bytes of shared memory per block (%zu "
+                     "available) at m=%d, P=%lld", need, have, c->m, (long long)P);
+            c->fused_why = why;
+        }
+    }
     // sub-allocation plan
     struct Part {
         void **dst;
@@ -238,13 +282,15 @@ ga_status ga_create(const ga_config *cfg, void *pop_dev, uint32_t *fit_dev, void
         parts.push_back({(void **)&c->fmisc, 64u * 4u});
         parts.push_back({(void **)&c->ftmask, (size_t)tiles * 8u});
         parts.push_back({(void **)&c->fperm, (size_t)kChunk * n_keep * 4u});
+        if ((uint64_t)n_keep > kPermSmemMax)
+            parts.push_back({(void **)&c->fperm_keys, (size_t)kChunk * n_keep * 8u});
     }
     (void)tmp_ptrs;
     size_t total = 0;
     for (auto &p : parts)
         total = align_up(total, 256) + align_up(p.bytes, 256);
     void *ws = nullptr;
-    cudaError_t e = cudaMalloc(&ws, total);
+    cudaError_t e = dev_alloc(&ws, total);
     if (e != cudaSuccess) {
         delete c;
         cudaGetLastError();
@@ -268,7 +314,7 @@ ga_status ga_create(const ga_config *cfg, void *pop_dev, uint32_t *fit_dev, void
         delete c;
         return set_error(nullptr, GA_ECUDA, "workspace initialisation failed: %s", cudaGetErrorString(e));
     }
-    c->fused_ok = (fused_fit && c->m <= kFusedMaxM && (uint64_t)tiles <= kFusedMaxTiles) ? 1 : 0;
+    c->fused_ok = fused_fit ? 1 : 0;
     *out = c;
     return GA_OK;
 }
@@ -402,6 +448,16 @@ ga_status ga_step_plain(ga_ctx *ctx, int32_t generations)
 
 int32_t ga_step_is_fused(const ga_ctx *ctx) { return ctx ? ctx->fused_ok : 0; }
 
+ga_status ga_set_strict(ga_ctx *ctx, int32_t strict)
+{
+    if (!ctx)
+        return set_error(nullptr, GA_EINVAL, "ctx is NULL");
+    ctx->strict = strict ? 1 : 0;
+    if (strict && !ctx->fused_ok)
+        return set_error(ctx, GA_EUNSUPPORTED, "%s", ctx->fused_why.c_str());
+    return GA_OK;
+}
+
 // Runs `generations` generations of ctxs[0..n) with the persistent kernel,
 // in chunks of kChunk generations (survivor orders of a chunk first).
 static ga_status fused_run(ga_ctx *const *ctxs, int n, int32_t generations, int stop_at_zero, int32_t *done_out,
@@ -486,6 +542,10 @@ static ga_status fused_run(ga_ctx *const *ctxs, int n, int32_t generations, int 
     prm.err = c0->err;
     fused_plan_ring(prm);
     const size_t smem = fused_smem_bytes(prm);
+    if (smem > fused_smem_limit())
+        return set_error(c0, GA_EUNSUPPORTED,
+                         "the persistent kernel would need %zu bytes of shared memory per block for these "
+                         "populations (%zu available)", smem, fused_smem_limit());
     int grid = 0;
     cudaError_t e = fused_grid(smem, &grid);
     if (e != cudaSuccess)
@@ -506,7 +566,7 @@ static ga_status fused_run(ga_ctx *const *ctxs, int n, int32_t generations, int 
                 cudaEventRecord(ev[0], c0->stream);
             }
             e = launch_perm_table((uint32_t)(2 * c->N), c->cfg.seed, c->cfg.pop_id, c->gen + 1u, chunk, c->fperm,
-                                  c0->stream, c->fmisc + 2);
+                                  c0->stream, c->fmisc + 2, c->fperm_keys);
             if (c->profiling) {
                 cudaEventRecord(ev[1], c0->stream);
                 c->prof_perm.push_back(ev[0]);
@@ -584,6 +644,8 @@ ga_status ga_step(ga_ctx *ctx, int32_t generations, int32_t stop_at_zero, int32_
         return st;
     if (generations < 0)
         return set_error(ctx, GA_EINVAL, "generations must be >= 0");
+    if (!ctx->fused_ok && ctx->strict)
+        return set_error(ctx, GA_EUNSUPPORTED, "strict mode: %s", ctx->fused_why.c_str());
     if (ctx->fused_ok) {
         int32_t d = 0;
         st = fused_run(&ctx, 1, generations, stop_at_zero, &d);
@@ -619,14 +681,18 @@ ga_status ga_step_multi(ga_ctx *const *ctxs, int32_t n, int32_t generations)
         return set_error(nullptr, GA_EINVAL, "ctxs must hold n >= 1 contexts");
     if (generations < 0)
         return set_error(nullptr, GA_EINVAL, "generations must be >= 0");
-    bool fused = n <= kMaxPops;
+    bool fused = n <= kMaxPops, strict = false;
     for (int32_t i = 0; i < n; ++i) {
         if (!ctxs[i])
             return set_error(nullptr, GA_EINVAL, "context %d is NULL", i);
         if (ctxs[i]->stream != ctxs[0]->stream || ctxs[i]->device != ctxs[0]->device)
             return set_error(nullptr, GA_EINVAL, "contexts must share stream and device");
         fused = fused && ctxs[i]->fused_ok;
+        strict = strict || ctxs[i]->strict;
     }
+    if (!fused && strict)
+        return set_error(nullptr, GA_EUNSUPPORTED, "strict mode: the populations cannot run in one persistent launch "
+                         "(more than %d, or one of them cannot run the persistent kernel)", kMaxPops);
     ga_status st = begin(ctxs[0]);
     if (st != GA_OK)
         return st;
@@ -782,7 +848,7 @@ ga_status ga_set_incremental(ga_ctx *ctx, int32_t enable)
         const int dpad = gram_tiles(ctx->m) * 64;  // 8 x 8 int8 tiles of the upper triangle
         const size_t gbytes = align_up((size_t)ctx->P * dpad, 256), ibytes = align_up((size_t)ctx->P * 4u, 256);
         void *mem = nullptr;
-        cudaError_t e = cudaMalloc(&mem, gbytes + 2 * ibytes + 256);
+        cudaError_t e = dev_alloc(&mem, gbytes + 2 * ibytes + 256);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return set_error(ctx, e == cudaErrorMemoryAllocation ? GA_ENOMEM : GA_ECUDA,

@@ -503,9 +503,11 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
 }
 
 // Bounded wait for the phase of `bar` with parity `parity`; false when the
-// budget ran out, or another thread raised an error and the phase is still
-// open (a completed phase always reports true).
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t *err)
+// budget (`budget_ns`, about two seconds unless a test asks for less) ran
+// out, or another thread raised an error and the phase is still open (a
+// completed phase always reports true).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t *err,
+                                          unsigned long long budget_ns = kMbarWaitBudgetNs)
 {
     if (mbar_test(bar, parity))
         return true;
@@ -516,7 +518,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32
         if ((i & 255u) == 0u) {
             if (ld_acquire_gpu(err) != 0u)
                 return mbar_test(bar, parity);
-            if (global_ns() - t0 > kMbarWaitBudgetNs) {
+            if (global_ns() - t0 > budget_ns) {
                 atomicOr(err, ERR_TIMEOUT);
                 return mbar_test(bar, parity);
             }
@@ -536,7 +538,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32
 // data written by other blocks through L2 (ld.global.cg or atomics).
 constexpr unsigned long long kBarrierBudgetNs = 2000000000ull;
 
-__device__ __forceinline__ bool grid_barrier(uint32_t *bar, uint32_t nblocks, uint32_t &epoch, uint32_t *err)
+__device__ __forceinline__ bool grid_barrier(uint32_t *bar, uint32_t nblocks, uint32_t &epoch, uint32_t *err,
+                                             unsigned long long budget_ns = kBarrierBudgetNs)
 {
     __shared__ int s_ok;
     __syncthreads();
@@ -557,7 +560,7 @@ __device__ __forceinline__ bool grid_barrier(uint32_t *bar, uint32_t nblocks, ui
                     ok = 0;
                     break;
                 }
-                if (global_ns() - t0 > kBarrierBudgetNs) {
+                if (global_ns() - t0 > budget_ns) {
                     atomicOr(err, ERR_TIMEOUT);
                     ok = 0;
                     break;

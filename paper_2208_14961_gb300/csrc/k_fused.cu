@@ -1428,6 +1428,18 @@ size_t fused_smem_bytes(const FusedParams &p)
     return (r1 + kHistSmem + (size_t)(kFusedThreads / 32) * p.warp_buf_words) * 4u;
 }
 
+size_t fused_smem_limit()
+{
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes f0{}, f1{};
+    cudaFuncGetAttributes(&f0, k_fused<false>);
+    cudaFuncGetAttributes(&f1, k_fused<true>);
+    const size_t stat = std::max(f0.sharedSizeBytes, f1.sharedSizeBytes);
+    return (size_t)optin > stat ? (size_t)optin - stat : 0u;
+}
+
 void fused_plan_ring(FusedParams &p)
 {
     // every copy of one offspring (the largest IncCopyPlan total over the

@@ -250,6 +250,36 @@ __global__ void __launch_bounds__(1024) k_perm_global(uint32_t n, uint32_t seed,
     perm_block<0>(n, seed, pop_id, gen, out, keys, cnt, cnt + (1u << nbits), nbits, s_tmp);
 }
 
+// Survivor orders of `gridDim.x` consecutive generations for n > kPermSmemMax
+// (one block per generation): bucket counters and offsets in shared memory
+// (2^nbits buckets each), the keys of generation b in keys[b * n .. ),
+// Philox blocks drawn twice.  The result is the full sort of the keys, the
+// same as the shared-memory sort's.
+__global__ void __launch_bounds__(1024) k_perm_big(uint32_t n, uint32_t seed, uint32_t pop_id, uint32_t gen0,
+                                                   uint32_t *out, unsigned long long *keys, int nbits,
+                                                   const uint32_t *gen_dev)
+{
+    extern __shared__ __align__(16) uint32_t s_cnt_off[];
+    __shared__ uint32_t s_tmp[33];
+    const uint32_t g0 = gen_dev ? *gen_dev + 1u : gen0;
+    const uint32_t B = 1u << nbits;
+    perm_block<0>(n, seed, pop_id, g0 + blockIdx.x, out + (size_t)blockIdx.x * n, keys + (size_t)blockIdx.x * n,
+                  s_cnt_off, s_cnt_off + B, nbits, s_tmp);
+}
+
+// Buckets of k_perm_big: about eight keys per bucket, at most 2^kPermBigMaxBits
+// (the counters and offsets then take 2 * 4 * 2^14 = 128 KiB of shared memory).
+constexpr int kPermBigMaxBits = 14;
+
+int perm_big_bits(uint32_t n)
+{
+    int b = 0;
+    while ((1u << b) < n)
+        ++b;
+    b -= 3;
+    return b < kPermSmemBits ? kPermSmemBits : (b > kPermBigMaxBits ? kPermBigMaxBits : b);
+}
+
 int perm_global_bits(uint32_t n)
 {
     int b = 0;
@@ -260,10 +290,22 @@ int perm_global_bits(uint32_t n)
 }
 
 cudaError_t launch_perm_table(uint32_t n, uint32_t seed, uint32_t pop_id, uint32_t gen0, int ngen, uint32_t *out,
-                              cudaStream_t s, const uint32_t *gen_dev)
+                              cudaStream_t s, const uint32_t *gen_dev, unsigned long long *keys)
 {
-    if (n > kPermSmemMax || ngen <= 0)
+    if (ngen <= 0)
         return cudaErrorInvalidValue;
+    if (n > kPermSmemMax) {
+        if (!keys)
+            return cudaErrorInvalidValue;
+        const int nb = perm_big_bits(n);
+        const size_t smem = (size_t)2u * (1u << nb) * sizeof(uint32_t);
+        cudaError_t e = cudaFuncSetAttribute(k_perm_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        k_perm_big<<<ngen, 1024, smem, s>>>(n, seed, pop_id, gen0, out, keys, nb, gen_dev);
+        note_launches(1);
+        return cudaGetLastError();
+    }
     const size_t smem = (size_t)n * sizeof(unsigned long long);
     cudaError_t e = cudaFuncSetAttribute(k_perm_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(kPermSmemMax * sizeof(unsigned long long)));

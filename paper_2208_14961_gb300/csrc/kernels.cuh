@@ -93,12 +93,14 @@ struct SelWork {
 cudaError_t launch_select(const void *pop, const uint32_t *fit, int64_t N, size_t mat_bytes, uint32_t seed,
                           uint32_t pop_id, uint32_t gen, const SelWork &w, void *scratch_pop, uint32_t *scratch_fit,
                           cudaStream_t s);
-// Survivor orders pi of `ngen` consecutive generations into out[ngen][n]
-// (n <= kPermSmemMax), one block per generation.  The first generation is
-// gen0, or *gen_dev + 1 when gen_dev is not null (a device-side counter, so
-// that a captured launch sequence can be replayed).
+// Survivor orders pi of `ngen` consecutive generations into out[ngen][n],
+// one block per generation.  The first generation is gen0, or *gen_dev + 1
+// when gen_dev is not null (a device-side counter, so that a captured launch
+// sequence can be replayed).  n <= kPermSmemMax sorts in shared memory; a
+// larger n needs `keys`, ngen * n 64-bit words of device memory.
 cudaError_t launch_perm_table(uint32_t n, uint32_t seed, uint32_t pop_id, uint32_t gen0, int ngen, uint32_t *out,
-                              cudaStream_t s, const uint32_t *gen_dev = nullptr);
+                              cudaStream_t s, const uint32_t *gen_dev = nullptr,
+                              unsigned long long *keys = nullptr);
 // *p = v, as a one-thread kernel (stream-ordered, capturable).
 cudaError_t launch_set_u32(uint32_t *p, uint32_t v, cudaStream_t s);
 int perm_global_bits(uint32_t n);
@@ -153,6 +155,9 @@ struct FusedParams {
 };
 
 size_t fused_smem_bytes(const FusedParams &p);
+// Dynamic shared memory a block of the persistent kernel may take on the
+// current device (opt-in maximum less the kernel's static shared memory).
+size_t fused_smem_limit();
 // Sets p.inc_ring: the largest copy ring (up to one offspring's phase-1
 // copies) that keeps the block's shared memory within the device limit.
 void fused_plan_ring(FusedParams &p);

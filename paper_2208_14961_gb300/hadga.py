@@ -65,6 +65,7 @@ SIGNATURES = {
     "ga_step": (_i32, [_vp, _i32, _i32, ctypes.POINTER(_i32)]),
     "ga_step_multi": (_i32, [ctypes.POINTER(_vp), _i32, _i32]),
     "ga_step_is_fused": (_i32, [_vp]),
+    "ga_set_strict": (_i32, [_vp, _i32]),
     "ga_step_multi_graph": (_i32, [ctypes.POINTER(_vp), _i32, _i32, _i32]),
     "ga_set_fused_grid": (_i32, [_vp, _i32]),
     "ga_set_incremental": (_i32, [_vp, _i32]),
@@ -87,6 +88,8 @@ SIGNATURES = {
     "ga_convert": (_i32, [_vp, _i32, _vp, _i32, _i32, _i64, _vp]),
     "ga_gram_real_batch": (_i32, [_vp, _vp, _i32, _i32, _i64, _vp]),
     "ga_select_static": (_i32, [_vp, _vp, _vp, _vp, _i32, _i32, _i64, _u32, _u32, _u32, _vp]),
+    "ga_debug_wait_timeout": (_i32, [_i32, _u32, ctypes.POINTER(_u32), _vp]),
+    "ga_debug_fail_allocations": (_i32, [_i32]),
 }
 
 _lib = None
@@ -194,6 +197,19 @@ def ga_select_static(pop_in: torch.Tensor, fit_in: torch.Tensor, parents_out: to
                                   N, seed, pop_id, gen, _stream(stream)))
 
 
+def debug_wait_timeout(which: int, budget_us: int, stream=None):
+    """Test hook: drives a bounded device wait (0 grid barrier, 1 mbarrier)
+    to its limit; returns (status, device error word) without raising."""
+    w = ctypes.c_uint32(0)
+    st = load().ga_debug_wait_timeout(which, budget_us, ctypes.byref(w), _stream(stream))
+    return int(st), int(w.value)
+
+
+def debug_fail_allocations(n: int):
+    """Test hook: the next n device allocations of the library fail (GA_ENOMEM)."""
+    check(load().ga_debug_fail_allocations(n))
+
+
 # ---------------------------------------------------------------------------
 # Context
 # ---------------------------------------------------------------------------
@@ -261,6 +277,10 @@ class Population:
 
     def is_fused(self) -> bool:
         return bool(load().ga_step_is_fused(self.ctx))
+
+    def set_strict(self, strict: bool = True):
+        """ga_step raises GA_EUNSUPPORTED instead of falling back to the plain path."""
+        self._chk(load().ga_set_strict(self.ctx, int(strict)))
 
     def profile(self, enable: bool):
         self._chk(load().ga_profile(self.ctx, int(enable)))

@@ -156,3 +156,23 @@ def test_select_static_rejects_every_overlap(lib, par, pfit, what):
     assert st == hadga.GA_EINVAL
     assert what in hadga.last_error()
 
+
+
+def test_out_of_memory_hook_in_create_without_gpu(lib):
+    """The allocation-failure hook makes ga_create fail with GA_ENOMEM before
+    the allocator is called, and return no context (host side only: the
+    buffers are fake and never touched)."""
+    from paper_2208_14961_gb300 import hadga
+    cfg = hadga.ga_config(m=20, NC=1, N=10, seed=0, pop_id=0, NR=1, fitness=0, storage=1, path=0,
+                          traj_cap=8, mutation=0)
+    ctx = ctypes.c_void_p()
+    assert lib.ga_debug_fail_allocations(-1) == hadga.GA_EINVAL
+    assert lib.ga_debug_fail_allocations(1) == hadga.GA_OK
+    try:
+        st = lib.ga_create(ctypes.byref(cfg), ctypes.c_void_p(0x100000), ctypes.c_void_p(0x200000), None,
+                           ctypes.byref(ctx))
+    finally:
+        lib.ga_debug_fail_allocations(0)
+    assert st == hadga.GA_ENOMEM
+    assert not ctx.value
+    assert "allocation" in hadga.last_error()

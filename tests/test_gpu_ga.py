@@ -213,3 +213,59 @@ def test_mutation_method1_matches_oracle(mode, m, N, NC, NR, kind):
     gtf, gts = pop.trajectory()
     assert np.array_equal(gtf.astype(np.uint64), tf) and np.array_equal(gts, ts)
     pop.close()
+
+
+def test_fused_m32_P80000_paper_search_parameters():
+    """The paper's m = 32 search parameters (Sec. 4.4: P = 80,000, NC = 1,
+    NR = 12, F2) in the fused kernel (strict: no fallback), 20 generations,
+    bit-exact with the oracle.  2N = 40,000 survivors take the survivor-order
+    sort with keys in global memory."""
+    h = need_gpu()
+    m, N, gens, NC, NR, kind, seed = 32, 20000, 20, 1, 12, 2, 9
+    pop = h.Population(m, N, seed=seed, NC=NC, NR=NR, fitness=kind, storage=h.STORE_BITS, traj_cap=gens)
+    pop.set_strict(True)
+    assert pop.is_fused()
+    pop.init_population()
+    pop.fitness()
+    pop.step(gens)
+    pop.sync()
+    gpu = pop.as_int8(), pop.fitness_host(), pop.trajectory()
+    pop.close()
+    _assert_same(gpu, _run_oracle(m, N, seed, gens, NC, NR, kind))
+
+
+@pytest.mark.parametrize("m,N,gens", [(20, 30000, 12), (64, 16384, 6), (8, 65536, 4)])
+def test_fused_large_populations_match_oracle(m, N, gens):
+    """Populations whose 2N survivors exceed the shared-memory survivor sort
+    (2N > 24,576), up to P = 262,144 at m = 8, fused and strict."""
+    h = need_gpu()
+    pop = h.Population(m, N, seed=4, storage=h.STORE_BITS, traj_cap=gens)
+    pop.set_strict(True)
+    pop.init_population()
+    pop.fitness()
+    pop.step(gens)
+    pop.sync()
+    gpu = pop.as_int8(), pop.fitness_host(), pop.trajectory()
+    pop.close()
+    _assert_same(gpu, _run_oracle(m, N, 4, gens))
+
+
+def test_strict_mode_reports_instead_of_falling_back():
+    """m = 256 is beyond the persistent kernel: a strict context reports
+    GA_EUNSUPPORTED with the reason; a non-strict one runs the plain path."""
+    h = need_gpu()
+    pop = h.Population(256, 2, seed=1, storage=h.STORE_BITS, traj_cap=4)
+    assert not pop.is_fused()
+    with pytest.raises(h.GAError) as ei:
+        pop.set_strict(True)
+    assert ei.value.status == h.GA_EUNSUPPORTED and "m <= 128" in str(ei.value)
+    pop.init_population()
+    pop.fitness()
+    with pytest.raises(h.GAError) as ei:
+        pop.step(2)
+    assert ei.value.status == h.GA_EUNSUPPORTED
+    pop.set_strict(False)
+    pop.step(2)
+    pop.sync()
+    assert pop.generation() == 2
+    pop.close()
