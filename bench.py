@@ -617,7 +617,7 @@ def table3_workload(args):
 # Sec. 4.4 of the paper: runs that found Hadamard matrices with fitness F2 on
 # an RTX 3080: (m, N, NC, NR, generations, seconds).
 PAPER_SEARCHES = [(20, 1000, 2, 8, 258_875, 517), (24, 1000, 2, 10, 9_576_814, 19_997),
-                  (28, 10_000, 1, 10, 428_082, 3_054)]
+                  (28, 10_000, 1, 10, 428_082, 3_054), (32, 20_000, 1, 12, 7_472_853, 94_923)]
 
 
 def search_workload(args):
@@ -642,6 +642,7 @@ def search_workload(args):
         for seed in range(args.search_seeds):
             pop = h.Population(m, N, seed=100 + seed, NC=NC, NR=NR, fitness=h.FIT_NNZ, storage=h.STORE_BITS,
                                traj_cap=args.search_chunk)
+            pop.set_strict(True)   # the persistent kernel, never the plain fallback
             pop.init_population()
             pop.fitness()
             pop.sync()
