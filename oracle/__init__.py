@@ -27,7 +27,8 @@ _lock = threading.Lock()
 _lib = None
 
 FIT_SQ, FIT_ABS, FIT_NNZ = 0, 1, 2
-OP_INIT, OP_SELECT, OP_CROSS, OP_MUTATE, OP_CONFIG = 0, 1, 2, 3, 4
+OP_INIT, OP_SELECT, OP_CROSS, OP_MUTATE, OP_CONFIG, OP_PSELECT = 0, 1, 2, 3, 4, 5
+SEL_TRUNCATION, SEL_PROBABILISTIC = 0, 1
 
 
 def build(force: bool = False) -> str:
@@ -70,7 +71,10 @@ def _load():
             "orc_survivors": (None, [vp, i64, vp]),
             "orc_select": (None, [vp, vp, i32, i64, u32, u32, u32]),
             "orc_best": (None, [vp, i64, vp, vp]),
-            "orc_run": (i32, [vp, vp, i32, i64, i32, i32, i32, u32, u32, u32, i32, i32, vp, vp, i32]),
+            "orc_psel_weight": (u64, [u64]),
+            "orc_psel_pick": (i64, [vp, i64, u32, u32, u32, u32]),
+            "orc_select_prob": (None, [vp, vp, i32, i64, u32, u32, u32]),
+            "orc_run": (i32, [vp, vp, i32, i64, i32, i32, i32, u32, u32, u32, i32, i32, vp, vp, i32, i32]),
             "orc_mixed_N": (i64, [u32, u32]),
             "orc_gram_real": (None, [vp, i32, i64, vp]),
             "orc_num_threads": (i32, []),
@@ -215,6 +219,25 @@ def select(pop: np.ndarray, F: np.ndarray, N: int, seed: int, pop_id: int, gen: 
     _load().orc_select(_ptr(pop), _ptr(F), pop.shape[1], N, seed, pop_id, gen)
 
 
+def psel_weight(f: int) -> int:
+    """Weight of fitness f in the probabilistic selection: floor(2^32 / (f + 1))."""
+    return int(_load().orc_psel_weight(f))
+
+
+def psel_pick(F: np.ndarray, seed: int, pop_id: int, gen: int, p: int) -> int:
+    """The individual the probabilistic selection of generation `gen` draws
+    for parent slot p, given the fitness F of the whole population."""
+    F = np.ascontiguousarray(F, dtype=np.uint64)
+    C = np.cumsum(np.array([psel_weight(int(f)) for f in F], dtype=np.uint64)).astype(np.uint64)
+    return int(_load().orc_psel_pick(_ptr(C), len(F), seed, pop_id, gen, p))
+
+
+def select_prob(pop: np.ndarray, F: np.ndarray, N: int, seed: int, pop_id: int, gen: int) -> None:
+    """Probabilistic selection of generation `gen` (weights inverse to F), in place."""
+    assert F.dtype == np.uint64
+    _load().orc_select_prob(_ptr(pop), _ptr(F), pop.shape[1], N, seed, pop_id, gen)
+
+
 def best(F: np.ndarray):
     F = np.ascontiguousarray(F, dtype=np.uint64)
     s = ctypes.c_int64()
@@ -224,14 +247,16 @@ def best(F: np.ndarray):
 
 
 def run(pop: np.ndarray, F: np.ndarray, N: int, NC: int, NR: int, kind: int, seed: int,
-        pop_id: int, gen0: int, generations: int, stop_at_zero: bool = False, shared_mutation: int = 0):
+        pop_id: int, gen0: int, generations: int, stop_at_zero: bool = False, shared_mutation: int = 0,
+        selection: int = SEL_TRUNCATION):
     """Runs `generations` generations in place; returns (n_done, traj_fit, traj_slot).
-    shared_mutation = 1 selects the paper's mutation method 1."""
+    shared_mutation = 1 selects the paper's mutation method 1; selection = 1
+    the probabilistic selection."""
     assert pop.dtype == np.int8 and F.dtype == np.uint64
     tf = np.zeros(max(generations, 1), dtype=np.uint64)
     ts = np.zeros(max(generations, 1), dtype=np.int64)
     n = _load().orc_run(_ptr(pop), _ptr(F), pop.shape[1], N, NC, NR, kind, seed, pop_id, gen0,
-                        generations, int(stop_at_zero), _ptr(tf), _ptr(ts), int(shared_mutation))
+                        generations, int(stop_at_zero), _ptr(tf), _ptr(ts), int(shared_mutation), int(selection))
     return int(n), tf[:n], ts[:n]
 
 

@@ -35,7 +35,8 @@
 #include <omp.h>
 #endif
 
-enum { ORC_OP_INIT = 0, ORC_OP_SELECT = 1, ORC_OP_CROSS = 2, ORC_OP_MUTATE = 3, ORC_OP_CONFIG = 4 };
+enum { ORC_OP_INIT = 0, ORC_OP_SELECT = 1, ORC_OP_CROSS = 2, ORC_OP_MUTATE = 3, ORC_OP_CONFIG = 4,
+       ORC_OP_PSELECT = 5 };
 enum { ORC_FIT_SQ = 0, ORC_FIT_ABS = 1, ORC_FIT_NNZ = 2 };
 
 /* ------------------------------------------------------------------------ */
@@ -453,6 +454,76 @@ void orc_select(int8_t *pop, uint64_t *F, int32_t m, int64_t N, uint32_t seed, u
 }
 
 /* ------------------------------------------------------------------------ */
+/* Probabilistic selection (Sec. 3.3: selection with probabilities inverse  */
+/* proportional to the fitness values, which the paper names and reports    */
+/* as no better than truncation; Sec. 4.1 on stalling).  The paper gives no */
+/* formula; the reading implemented here:                                   */
+/*   weight      w_q = floor(2^32 / (F_q + 1))   (integer; F = 0 allowed)   */
+/*   cumulative  C_q = w_0 + ... + w_q,  W = C_{P-1}  (< 2^63)             */
+/*   parent slot p in [0, 2N), independently, with replacement:            */
+/*     u = (word 0 << 32) | word 1 of Philox, key (seed, pop_id), counter   */
+/*         (PSELECT, g, p, 0);  t = floor(u W / 2^64)  (in [0, W))          */
+/*     receives the individual q with C_{q-1} <= t < C_q                   */
+/* and its fitness moves with it; the right-hand side is read from a copy.  */
+/* Pinned by: chi-square of the selection frequencies against w_q / W on    */
+/* tiny populations, the degenerate cases (equal F: uniform; one F = 0 and  */
+/* the rest huge: always that one), monotone frequency in F, and every      */
+/* parent being a copy of an individual of the previous population.         */
+/* ------------------------------------------------------------------------ */
+uint64_t orc_psel_weight(uint64_t f)
+{
+    return ((uint64_t)1 << 32) / (f + 1u);
+}
+
+/* The individual drawn for parent slot p (weights from F[0, P)). */
+int64_t orc_psel_pick(const uint64_t *C, int64_t P, uint32_t seed, uint32_t pop_id, uint32_t gen, uint32_t p)
+{
+    uint32_t ctr[4] = {ORC_OP_PSELECT, gen, p, 0u};
+    uint32_t key[2] = {seed, pop_id};
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, key, w);
+    const uint64_t u = ((uint64_t)w[0] << 32) | (uint64_t)w[1];
+    const uint64_t W = C[P - 1];
+    const uint64_t t = (uint64_t)(((unsigned __int128)u * (unsigned __int128)W) >> 64);
+    /* smallest q with C_q > t (binary search over the increasing C) */
+    int64_t lo = 0, hi = P - 1;
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (C[mid] > t)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo;
+}
+
+void orc_select_prob(int8_t *pop, uint64_t *F, int32_t m, int64_t N, uint32_t seed, uint32_t pop_id, uint32_t gen)
+{
+    const size_t S = (size_t)m * m;
+    const int64_t P = 4 * N;
+    int8_t *old_pop = (int8_t *)malloc(S * (size_t)P);
+    uint64_t *old_F = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)P);
+    uint64_t *C = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)P);
+    memcpy(old_pop, pop, S * (size_t)P);
+    memcpy(old_F, F, sizeof(uint64_t) * (size_t)P);
+    uint64_t run = 0;
+    for (int64_t q = 0; q < P; ++q) {
+        run += orc_psel_weight(old_F[q]);
+        C[q] = run;
+    }
+    int64_t p;
+#pragma omp parallel for schedule(static)
+    for (p = 0; p < 2 * N; ++p) {
+        const int64_t src = orc_psel_pick(C, P, seed, pop_id, gen, (uint32_t)p);
+        memcpy(pop + (size_t)p * S, old_pop + (size_t)src * S, S);
+        F[p] = old_F[src];
+    }
+    free(C);
+    free(old_pop);
+    free(old_F);
+}
+
+/* ------------------------------------------------------------------------ */
 /* a8  Best individual: least F, lowest slot on ties (Sec. 6 listing, the   */
 /* minimum of F and the loop test).                                         */
 /* ------------------------------------------------------------------------ */
@@ -468,7 +539,8 @@ void orc_best(const uint64_t *F, int64_t P, int64_t *slot, uint64_t *fit)
 
 /* ------------------------------------------------------------------------ */
 /* a1..a8  The generation loop (Sec. 3 enumerated steps; Sec. 6 listing):   */
-/* selection, crossover, mutation, then fitness of the 2N offspring; the    */
+/* selection (truncation, or the probabilistic variant when selection = 1), */
+/* crossover, mutation, then fitness of the 2N offspring; the               */
 /* parents keep the fitness carried by the selection.  Generation numbers   */
 /* run from gen0 + 1; traj receives the best after each generation.        */
 /* When stop_at_zero is set the loop ends after the first generation whose  */
@@ -476,12 +548,15 @@ void orc_best(const uint64_t *F, int64_t P, int64_t *slot, uint64_t *fit)
 /* ------------------------------------------------------------------------ */
 int32_t orc_run(int8_t *pop, uint64_t *F, int32_t m, int64_t N, int32_t NC, int32_t NR, int32_t kind,
                 uint32_t seed, uint32_t pop_id, uint32_t gen0, int32_t generations, int32_t stop_at_zero,
-                uint64_t *traj_fit, int64_t *traj_slot, int32_t shared_mutation)
+                uint64_t *traj_fit, int64_t *traj_slot, int32_t shared_mutation, int32_t selection)
 {
     int32_t done = 0;
     for (int32_t t = 0; t < generations; ++t) {
         uint32_t gen = gen0 + (uint32_t)t + 1u;
-        orc_select(pop, F, m, N, seed, pop_id, gen);
+        if (selection == 1)
+            orc_select_prob(pop, F, m, N, seed, pop_id, gen);
+        else
+            orc_select(pop, F, m, N, seed, pop_id, gen);
         orc_crossover(pop, m, N, seed, pop_id, gen);
         orc_mutate(pop, m, N, NC, NR, seed, pop_id, gen, shared_mutation);
         orc_fitness(pop, m, 2 * N, 2 * N, kind, F);
