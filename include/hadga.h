@@ -96,7 +96,17 @@ typedef struct {
     int32_t mutation; /* 0: each offspring draws its own columns and rows (methods 2 and 3
                          of Sec. 3.5); 1: method 1 of Sec. 3.5, every offspring of a
                          generation uses the same draws, those of stream index 2N */
+    int32_t selection; /* ga_selection: 0 truncation (Sec. 3.3, the paper's method);
+                          1 probabilistic, probabilities inverse to the fitness (the
+                          variant Sec. 3.3 names): weights floor(2^32 / (F + 1)), each
+                          parent slot p drawn independently with replacement by
+                          t = floor(u W / 2^64), u the 64 bits of Philox
+                          (PSELECT = 5, g, p, 0) words 0 and 1, W the sum of the
+                          weights; the parent is the individual whose cumulative-weight
+                          interval holds t.  Not with the incremental mode. */
 } ga_config;
+
+typedef enum { GA_SEL_TRUNCATION = 0, GA_SEL_PROBABILISTIC = 1 } ga_selection;
 
 typedef struct ga_ctx ga_ctx;
 

@@ -204,6 +204,8 @@ ga_status ga_create(const ga_config *cfg, void *pop_dev, uint32_t *fit_dev, void
         return set_error(nullptr, GA_EINVAL, "traj_cap must be >= 1");
     if (cfg->mutation != 0 && cfg->mutation != 1)
         return set_error(nullptr, GA_EINVAL, "mutation must be 0 (per offspring) or 1 (one draw per generation)");
+    if (cfg->selection != GA_SEL_TRUNCATION && cfg->selection != GA_SEL_PROBABILISTIC)
+        return set_error(nullptr, GA_EINVAL, "selection must be 0 (truncation) or 1 (probabilistic)");
     int path = cfg->path == GA_PATH_AUTO ? auto_path(cfg->storage, cfg->m, cfg->fitness) : cfg->path;
     if (!fitness_path_supported(cfg->storage, cfg->m, path))
         return set_error(nullptr, GA_EINVAL, "Gram path %d does not read storage %d", cfg->path, cfg->storage);
@@ -267,6 +269,11 @@ ga_status ga_create(const ga_config *cfg, void *pop_dev, uint32_t *fit_dev, void
         {(void **)&c->best, 8u},
         {(void **)&c->err, 4u},
     };
+    if (cfg->selection == GA_SEL_PROBABILISTIC) {
+        parts.push_back({(void **)&c->sel.cw, (size_t)tiles * 32u * 8u});
+        parts.push_back({(void **)&c->sel.tex, (size_t)tiles * 8u});
+        parts.push_back({(void **)&c->sel.wtotal, 8u});
+    }
     if ((uint64_t)n_keep > kPermSmemMax) {
         const int nb = perm_global_bits((uint32_t)n_keep);
         parts.push_back({(void **)&c->sel.perm_keys, (size_t)n_keep * 8u});
@@ -379,10 +386,17 @@ ga_status ga_select(ga_ctx *ctx)
         return st;
     const uint32_t g = ctx->gen + 1u;
     ctx->gram_valid = 0;
-    st = cuda_check(ctx,
-                    launch_select(ctx->pop, ctx->fit, ctx->N, ctx->mat_bytes, ctx->cfg.seed, ctx->cfg.pop_id, g,
-                                  ctx->sel, ctx->scratch_pop, ctx->scratch_fit, ctx->stream),
-                    "select");
+    if (ctx->cfg.selection == GA_SEL_PROBABILISTIC)
+        st = cuda_check(ctx,
+                        launch_select_prob(ctx->pop, ctx->fit, ctx->N, ctx->mat_bytes, ctx->cfg.seed,
+                                           ctx->cfg.pop_id, g, ctx->sel, ctx->scratch_pop, ctx->scratch_fit,
+                                           ctx->stream),
+                        "probabilistic select");
+    else
+        st = cuda_check(ctx,
+                        launch_select(ctx->pop, ctx->fit, ctx->N, ctx->mat_bytes, ctx->cfg.seed, ctx->cfg.pop_id, g,
+                                      ctx->sel, ctx->scratch_pop, ctx->scratch_fit, ctx->stream),
+                        "select");
     if (st != GA_OK)
         return st;
     const int64_t n_keep = 2 * ctx->N;
@@ -467,6 +481,10 @@ static ga_status fused_run(ga_ctx *const *ctxs, int n, int32_t generations, int 
     FusedParams prm{};
     memset(&prm, 0, sizeof(prm));
     prm.npop = n;
+    prm.psel = c0->cfg.selection == GA_SEL_PROBABILISTIC ? 1 : 0;
+    for (int i = 1; i < n; ++i)
+        if (ctxs[i]->cfg.selection != c0->cfg.selection)
+            return set_error(c0, GA_EUNSUPPORTED, "one persistent launch runs one selection method");
     uint32_t tiles = 0, tslots = 0, wpairs = 0;
     int max_words = 0;
     for (int i = 0; i < n; ++i) {
@@ -479,6 +497,7 @@ static ga_status fused_run(ga_ctx *const *ctxs, int n, int32_t generations, int 
         p.fit[1] = c->ffit;
         p.state = c->fstate;
         p.tmask = c->ftmask;
+        p.cw = c->sel.cw;
         p.perm = c->fperm;
         p.traj = c->traj;
         p.gen_dev = c->fmisc + 2;
@@ -565,8 +584,10 @@ static ga_status fused_run(ga_ctx *const *ctxs, int n, int32_t generations, int 
                 cudaEventCreate(&ev[1]);
                 cudaEventRecord(ev[0], c0->stream);
             }
-            e = launch_perm_table((uint32_t)(2 * c->N), c->cfg.seed, c->cfg.pop_id, c->gen + 1u, chunk, c->fperm,
-                                  c0->stream, c->fmisc + 2, c->fperm_keys);
+            // the survivor orders of truncation selection (probabilistic selection draws per parent slot)
+            e = prm.psel ? cudaSuccess
+                         : launch_perm_table((uint32_t)(2 * c->N), c->cfg.seed, c->cfg.pop_id, c->gen + 1u, chunk,
+                                             c->fperm, c0->stream, c->fmisc + 2, c->fperm_keys);
             if (c->profiling) {
                 cudaEventRecord(ev[1], c0->stream);
                 c->prof_perm.push_back(ev[0]);
@@ -687,7 +708,7 @@ ga_status ga_step_multi(ga_ctx *const *ctxs, int32_t n, int32_t generations)
             return set_error(nullptr, GA_EINVAL, "context %d is NULL", i);
         if (ctxs[i]->stream != ctxs[0]->stream || ctxs[i]->device != ctxs[0]->device)
             return set_error(nullptr, GA_EINVAL, "contexts must share stream and device");
-        fused = fused && ctxs[i]->fused_ok;
+        fused = fused && ctxs[i]->fused_ok && ctxs[i]->cfg.selection == ctxs[0]->cfg.selection;
         strict = strict || ctxs[i]->strict;
     }
     if (!fused && strict)
@@ -844,6 +865,10 @@ ga_status ga_set_incremental(ga_ctx *ctx, int32_t enable)
     if (ctx->cfg.storage != GA_STORE_BITS || ctx->m <= 32 || ctx->m > 128 || !ctx->fused_ok)
         return set_error(ctx, GA_EUNSUPPORTED,
                          "incremental Gram mode needs BITS storage, 32 < m <= 128 and a fused-capable context");
+    if (ctx->cfg.selection != GA_SEL_TRUNCATION)
+        return set_error(ctx, GA_EUNSUPPORTED,
+                         "incremental Gram mode needs truncation selection (parents and offspring trade Gram "
+                         "buffers one to one; probabilistic selection may draw an individual twice)");
     if (!ctx->gram_mem) {
         const int dpad = gram_tiles(ctx->m) * 64;  // 8 x 8 int8 tiles of the upper triangle
         const size_t gbytes = align_up((size_t)ctx->P * dpad, 256), ibytes = align_up((size_t)ctx->P * 4u, 256);

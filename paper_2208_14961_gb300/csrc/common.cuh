@@ -13,7 +13,7 @@
 
 namespace hadga {
 
-enum : uint32_t { OP_INIT = 0, OP_SELECT = 1, OP_CROSS = 2, OP_MUTATE = 3 };
+enum : uint32_t { OP_INIT = 0, OP_SELECT = 1, OP_CROSS = 2, OP_MUTATE = 3, OP_PSELECT = 5 };
 enum : uint32_t { ERR_TIMEOUT = 1u, ERR_INTERNAL = 2u };
 enum { FIT_SQ = 0, FIT_ABS = 1, FIT_NNZ = 2 };
 enum { ST_INT8 = 0, ST_BITS = 1, ST_E4M3 = 2, ST_BF16 = 3 };
@@ -72,6 +72,80 @@ __device__ __forceinline__ int cut_point(uint32_t seed, uint32_t pop_id, uint32_
 {
     const uint4 b = philox_block(seed, pop_id, OP_CROSS, gen, k, 0u, 0u);
     return (int)uniform_int(b.x, 1u, (uint32_t)(m - 1));
+}
+
+// ---------------------------------------------------------------------------
+// Probabilistic selection (the Sec. 3.3 variant: probabilities inverse to the
+// fitness).  Weight w = floor(2^32 / (F + 1)); parent slot p draws the 64-bit
+// u of words 0, 1 of Philox (PSELECT, gen, p, 0) and takes the individual
+// whose cumulative-weight interval holds t = floor(u W / 2^64).
+// ---------------------------------------------------------------------------
+// floor(2^32 / d) for d = f + 1 in 32-bit arithmetic: floor((2^32 - 1) / d),
+// plus one when d divides 2^32 (d a power of two); 2^32 for f = 0.
+__device__ __forceinline__ unsigned long long psel_weight(uint32_t f)
+{
+    if (f == 0u)
+        return 1ull << 32;
+    const uint32_t d = f + 1u;
+    if (d == 0u)  // f = 2^32 - 1 (never a fitness value): 2^32 / 2^32
+        return 1ull;
+    return (unsigned long long)(0xFFFFFFFFu / d + ((d & (d - 1u)) == 0u ? 1u : 0u));
+}
+
+__device__ __forceinline__ unsigned long long psel_draw(uint32_t seed, uint32_t pop_id, uint32_t gen, uint32_t p)
+{
+    const uint4 b = philox_block(seed, pop_id, OP_PSELECT, gen, p, 0u, 0u);
+    return ((unsigned long long)b.x << 32) | (unsigned long long)b.y;
+}
+
+// Whole warp, one tile of 32 slots (lane = slot - 32 t): stores the inclusive
+// prefix of the tile's weights at cw_tile[lane] (slots past the population
+// weigh 0, so their entries equal the tile sum) and returns the tile's sum.
+__device__ __forceinline__ unsigned long long psel_tile(uint32_t f, bool valid, unsigned long long *cw_tile, int lane)
+{
+    unsigned long long w = valid ? psel_weight(f) : 0ull;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(0xFFFFFFFFu, w, o);
+        if (lane >= o)
+            w += t;
+    }
+    cw_tile[lane] = w;
+    return __shfl_sync(0xFFFFFFFFu, w, 31);
+}
+
+// Slot drawn by u: t = base + floor(u W / 2^64); the tile j is the last with
+// ex_at(j) <= t (ex_at: exclusive prefix of the tile sums, from base), the
+// slot inside it the first whose inclusive in-tile prefix exceeds t - ex_at(j).
+template <class ExAt>
+__device__ __forceinline__ uint32_t psel_lookup(unsigned long long u, ExAt ex_at, uint32_t ntiles,
+                                                unsigned long long base, unsigned long long W,
+                                                const unsigned long long *cw, uint32_t P, uint32_t *err)
+{
+    const unsigned long long t = base + __umul64hi(u, W);
+    uint32_t lo = 0, hi = ntiles - 1u;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1u) >> 1;
+        if (ex_at(mid) <= t)
+            lo = mid;
+        else
+            hi = mid - 1u;
+    }
+    const unsigned long long r = t - ex_at(lo);
+    const uint4 *c4 = reinterpret_cast<const uint4 *>(cw + (size_t)lo * 32u);
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int v = 0; v < 16; ++v) {
+        const uint4 x = __ldcg(c4 + v);
+        const unsigned long long a = ((unsigned long long)x.y << 32) | x.x, b = ((unsigned long long)x.w << 32) | x.z;
+        cnt += (a <= r ? 1u : 0u) + (b <= r ? 1u : 0u);
+    }
+    const uint32_t slot = lo * 32u + cnt;
+    if (cnt >= 32u || slot >= P) {  // only if the prefixes were inconsistent
+        atomicOr(err, ERR_INTERNAL);
+        return P - 1u;
+    }
+    return slot;
 }
 
 // ---------------------------------------------------------------------------

@@ -50,6 +50,8 @@ struct PopSel {
     uint32_t gen0;          // generation of the population before this launch
     uint32_t bor;           // block OR of the new fitness values
     unsigned long long bbest;  // block minimum of the new best keys
+    uint32_t psel;          // probabilistic selection (no threshold, no histograms)
+    unsigned long long pbase, pW;  // probabilistic selection: joint prefix before the first tile, total weight
 };
 
 __device__ __forceinline__ uint32_t ldcg32(const uint32_t *p) { return __ldcg(p); }
@@ -264,6 +266,17 @@ __device__ __forceinline__ uint32_t nonsurvivor_of(uint32_t o, const FusedPop &p
     return 32u * lo + (uint32_t)nth_set_bit(mask, (int)r);
 }
 
+// Slot drawn by the probabilistic selection for a parent whose draw is u:
+// the tile sums' exclusive prefix ex (joint tile space, shared memory) from
+// the population's first tile, then the in-tile weight prefixes.
+__device__ __forceinline__ uint32_t psel_slot_of(unsigned long long u, const FusedPop &p, const PopSel &S,
+                                                 const Surv &sv, uint32_t *err)
+{
+    const unsigned long long *ex = sv.ex + p.tile_base;
+    return psel_lookup(u, [&](uint32_t j) { return ex[j]; }, p.ntiles, S.pbase, S.pW, p.cw, (uint32_t)(4 * p.N),
+                       err);
+}
+
 // Stream index of the mutation draws of offspring o: o itself, or 2N for
 // every offspring under method 1 of Sec. 3.5 (one draw per generation).
 __device__ __forceinline__ uint32_t mut_stream(const FusedPop &p, uint32_t o)
@@ -275,13 +288,20 @@ __device__ __forceinline__ uint32_t mut_stream(const FusedPop &p, uint32_t o)
 // number d, cut point c and (for NC = NR = 1) the mutated column and rows.
 struct Pre {
     uint32_t d, c, cc, ra, rb;
+    unsigned long long u;  // probabilistic selection: the parent's 64-bit draw
 };
 
-__device__ __forceinline__ Pre make_pre(const FusedPop &p, uint32_t gen, uint32_t tch, uint32_t k, int half)
+__device__ __forceinline__ Pre make_pre(const FusedPop &p, uint32_t gen, uint32_t tch, uint32_t k, int half,
+                                        bool psel)
 {
     const uint32_t N = (uint32_t)p.N;
     Pre r;
-    r.d = __ldg(p.perm + (size_t)tch * 2u * N + k + (half ? N : 0u));
+    r.d = 0u;
+    r.u = 0ull;
+    if (psel)
+        r.u = psel_draw(p.seed, p.pop_id, gen, k + (half ? N : 0u));
+    else
+        r.d = __ldg(p.perm + (size_t)tch * 2u * N + k + (half ? N : 0u));
     r.c = (uint32_t)cut_point(p.seed, p.pop_id, gen, k, p.m);
     r.cc = r.ra = r.rb = 0u;
     if (p.NC == 1 && p.NR == 1) {
@@ -343,7 +363,7 @@ __device__ __forceinline__ void pair_thread(const FusedPop &p, const PopSel &S, 
     const uint32_t N = (uint32_t)p.N;
     uint32_t s_mine = 0;
     if (valid)
-        s_mine = survivor_of(pre.d, p, S, sv, err);
+        s_mine = S.psel ? psel_slot_of(pre.u, p, S, sv, err) : survivor_of(pre.d, p, S, sv, err);
     const uint32_t s_other = __shfl_xor_sync(FULL, s_mine, 2);
     const uint32_t *src_pop = p.pop[src];
     uint32_t *dst_pop = p.pop[src ^ 1];
@@ -720,7 +740,8 @@ __device__ void offspring_warp(const FusedPop &p, PopSel &S, int src, uint32_t g
     uint32_t look = 0, lf = 0, lg = 0;
     if (lane < (inc ? 3 : 2)) {
         if (lane < 2)
-            look = survivor_of(__ldg(p.perm + (size_t)tch * 2u * N + k + (lane ? N : 0u)), p, S, sv, err);
+            look = S.psel ? psel_slot_of(psel_draw(p.seed, p.pop_id, gen, k + (lane ? N : 0u)), p, S, sv, err)
+                          : survivor_of(__ldg(p.perm + (size_t)tch * 2u * N + k + (lane ? N : 0u)), p, S, sv, err);
         else
             look = nonsurvivor_of(k + oh, p, S, sv, err);
         // fitness and Gram index of the slot in one round trip
@@ -862,7 +883,7 @@ __device__ void offspring_warp(const FusedPop &p, PopSel &S, int src, uint32_t g
         unsigned long long bk = ~0ull;
         uint32_t orr = 0;
         for (int i = 0; i < 2; ++i) {
-            if (fv[i] <= S.capn)
+            if (!S.psel && fv[i] <= S.capn)
                 atomicAdd((S.boff != 0xFFFFFFFFu ? bhist + S.boff : hist_next) + (fv[i] >> S.shiftn), 1u);
             orr |= fv[i];
             const unsigned long long key = ((unsigned long long)fv[i] << 32) | slots[i];
@@ -974,10 +995,16 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
     auto tile_base = [&](int i) { return prm.p[i].tile_base; };
 
     // ---- pre-pass: max and OR of the current fitness of every population -----
-    {
+    // (truncation selection only: probabilistic selection keeps no histograms)
+    const bool psel = prm.psel != 0;
+    if (tid < npop) {
+        S[tid].gen0 = ldcg32(prm.p[tid].gen_dev);
+        S[tid].psel = psel ? 1u : 0u;
+        S[tid].boff = 0xFFFFFFFFu;
+    }
+    __syncthreads();
+    if (!psel) {
         const int par0 = 0;  // buffers alternate with the generation index inside the launch
-        if (tid < npop)
-            S[tid].gen0 = ldcg32(prm.p[tid].gen_dev);
         for (int i = 0; i < npop; ++i) {
             const FusedPop &p = prm.p[i];
             const uint32_t P = (uint32_t)(4 * p.N);
@@ -1030,10 +1057,10 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
         // first group's histogram buckets (populations [0, g1) whose buckets
         // fit the staging area), held in registers while the
         // selection-independent draws are computed
-        const uint32_t vload = tid < npop ? ldcg32(stat_of(prm.p[tid]) + 1 + par) : 0u;
+        const uint32_t vload = (!psel && tid < npop) ? ldcg32(stat_of(prm.p[tid]) + 1 + par) : 0u;
         int g1 = 0;
         uint32_t goff = 0;
-        while (g1 < npop) {
+        while (!psel && g1 < npop) {
             const uint32_t nb = (S[g1].cap >> S[g1].shift) + 1u;
             if (g1 > 0 && goff + nb > kHistSmem)
                 break;
@@ -1067,7 +1094,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             f_pre = q < (uint32_t)(4 * p.N) ? ldcg32(p.fit[src] + q) : 0u;
         }
         // selection-independent draws of this warp's first build item
-        Pre pre0{0u, 1u, 1u, 0u, 0u};
+        Pre pre0{0u, 1u, 1u, 0u, 0u, 0ull};
         const uint32_t nwork_t = prm.thread_slots >> 5;
         if (gwarp < nwork_t) {
             const uint32_t u = gwarp * 32u + (uint32_t)lane;
@@ -1079,10 +1106,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                 const FusedPop &p = prm.p[i];
                 const uint32_t local = u - p.work_base, k = local >> 2;
                 if (k < (uint32_t)p.N)
-                    pre0 = make_pre(p, S[i].gen0 + 1u + (uint32_t)t, (uint32_t)t, k, (int)((local >> 1) & 1u));
+                    pre0 = make_pre(p, S[i].gen0 + 1u + (uint32_t)t, (uint32_t)t, k, (int)((local >> 1) & 1u),
+                                    psel);
             }
         }
-        for (int i = 0; i < npop; ++i) {
+        for (int i = 0; i < npop && !psel; ++i) {
             uint32_t *hn = hist_of(prm.p[i], par ^ 1);
             for (uint32_t e = gtid; e < (uint32_t)kHistR; e += gthreads)
                 hn[e] = 0u;
@@ -1097,7 +1125,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
         // histograms staged in shared memory (groups of populations that
         // fit); one warp per population finds the crossing of 2N and, when
         // its bucket holds a single value, fixes the threshold right away
-        for (int i0 = 0; i0 < npop;) {
+        for (int i0 = 0; i0 < npop && !psel;) {
             uint32_t off = 0;
             int i1 = i0;
             while (i1 < npop) {
@@ -1172,7 +1200,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             i0 = i1;
         }
         // refinement passes while a candidate bucket may hold several values
-        if (s_flag) {
+        // (s_flag was last written before a block barrier of the staging loop,
+        // which probabilistic selection skips: it never reads it)
+        if (!psel && s_flag) {
             while (s_flag) {
                 const int rl = (int)(ref_level % 3u), rz = (int)((ref_level + 1u) % 3u);
                 for (int i = 0; i < npop; ++i) {
@@ -1237,6 +1267,13 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             const uint32_t P = (uint32_t)(4 * p.N), T = S[i].T;
             const uint32_t q = (tl - p.tile_base) * 32u + lane;
             const uint32_t f = tl == gwarp ? f_pre : (q < P ? ldcg32(p.fit[src] + q) : 0u);
+            if (psel) {
+                // probabilistic selection: in-tile weight prefixes and the tile's weight
+                const unsigned long long sum = psel_tile(f, q < P, p.cw + (size_t)(tl - p.tile_base) * 32u, lane);
+                if (lane == 0)
+                    p.tmask[tl - p.tile_base] = sum;
+                continue;
+            }
             const uint32_t lt = __ballot_sync(FULL, q < P && f < T);
             const uint32_t eq = __ballot_sync(FULL, q < P && f == T);
             if (lane == 0)
@@ -1244,7 +1281,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
         }
         // block-local histogram offsets of the next generation (read after
         // the barrier's bar.sync)
-        if (tid == 0) {
+        if (tid == 0 && !psel) {
             uint32_t off = 0;
             for (int i = 0; i < npop; ++i) {
                 const uint32_t nb = (S[i].capn >> S[i].shiftn) + 1u;
@@ -1283,10 +1320,22 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             TT,
             [&](uint32_t e) {
                 const unsigned long long v = tm[e];
+                if (psel)
+                    return v;  // the tile's weight
                 return ((unsigned long long)__popc((uint32_t)v) << 32) | (unsigned long long)__popc((uint32_t)(v >> 32));
             },
             ex, s_tmp64);
-        if (tid < npop) {
+        if (tid < npop && psel) {
+            const FusedPop &p = prm.p[tid];
+            PopSel &s = S[tid];
+            const uint32_t last = p.tile_base + p.ntiles - 1u;
+            s.pbase = ex[p.tile_base];
+            s.pW = ex[last] + tm[last] - s.pbase;
+            s.bor = 0u;
+            s.bbest = ~0ull;
+            if (s.pW == 0ull)
+                atomicOr(err, ERR_INTERNAL);
+        } else if (tid < npop) {
             const FusedPop &p = prm.p[tid];
             PopSel &s = S[tid];
             const unsigned long long e0 = ex[p.tile_base];
@@ -1316,7 +1365,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             const uint32_t gen = S[i < 0 ? 0 : i].gen0 + 1u + (uint32_t)t;
             Pre pre = pre0;
             if (w != gwarp && valid)
-                pre = make_pre(p, gen, (uint32_t)t, k, half);
+                pre = make_pre(p, gen, (uint32_t)t, k, half, psel);
             uint32_t fv = 0, sl = 0;
             const PopSel &s = S[i < 0 ? 0 : i];
             switch (p.m) {
@@ -1329,7 +1378,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             default:
                 break;
             }
-            if (s.boff != 0xFFFFFFFFu) {
+            if (psel) {
+                // no histogram: the next selection weighs every individual
+            } else if (s.boff != 0xFFFFFFFFu) {
                 if (valid && fv <= s.capn)
                     atomicAdd(bhist + s.boff + (fv >> s.shiftn), 1u);
             } else {

@@ -360,6 +360,119 @@ __global__ void __launch_bounds__(256) k_sel_gather(const uint8_t *__restrict__ 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Probabilistic selection (the Sec. 3.3 variant, weights inverse to F): one
+// warp per tile writes the in-tile weight prefixes and the tile sum; one
+// block scans the tile sums; one warp per parent slot draws and gathers.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_psel_tiles(const uint32_t *__restrict__ fit, int64_t P,
+                                                    unsigned long long *cw, unsigned long long *tsum)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t tiles = (P + 31) >> 5;
+    for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < tiles;
+         t += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t q = t * 32 + lane;
+        const uint32_t f = q < P ? fit[q] : 0u;
+        const unsigned long long sum = psel_tile(f, q < P, cw + (size_t)t * 32u, lane);
+        if (lane == 0)
+            tsum[t] = sum;
+    }
+}
+
+// One block: exclusive prefix of the tile sums and their total.
+__global__ void __launch_bounds__(1024) k_psel_scan(const unsigned long long *__restrict__ tsum, int64_t tiles,
+                                                    unsigned long long *tex, unsigned long long *total)
+{
+    __shared__ unsigned long long s_w[32];
+    __shared__ unsigned long long s_tot;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned long long carry = 0;
+    for (int64_t base = 0; base < tiles; base += blockDim.x) {
+        const int64_t t = base + threadIdx.x;
+        const unsigned long long v = t < tiles ? tsum[t] : 0ull;
+        unsigned long long inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+            if (lane >= o)
+                inc += y;
+        }
+        if (lane == 31)
+            s_w[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            const unsigned long long x = lane < nw ? s_w[lane] : 0ull;
+            unsigned long long xi = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, xi, o);
+                if (lane >= o)
+                    xi += y;
+            }
+            if (lane < nw)
+                s_w[lane] = xi - x;  // exclusive prefix of the warp totals
+        }
+        __syncthreads();
+        const unsigned long long ex = carry + s_w[warp] + inc - v;
+        if (t < tiles)
+            tex[t] = ex;
+        // the chunk's total: the last thread's inclusive value
+        if (threadIdx.x == blockDim.x - 1)
+            s_tot = ex + v;
+        __syncthreads();
+        carry = s_tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        *total = carry;
+}
+
+__global__ void __launch_bounds__(256) k_psel_gather(const uint8_t *__restrict__ pop,
+                                                     const uint32_t *__restrict__ fit, size_t mat_bytes,
+                                                     int64_t n_keep, const unsigned long long *tex,
+                                                     const unsigned long long *cw, const unsigned long long *total,
+                                                     int64_t tiles, int64_t P, uint32_t seed, uint32_t pop_id,
+                                                     uint32_t gen, uint8_t *out_pop, uint32_t *out_fit, uint32_t *err)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned long long W = *total;
+    for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < n_keep;
+         p += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        uint32_t src = 0;
+        if (lane == 0) {
+            const unsigned long long u = psel_draw(seed, pop_id, gen, (uint32_t)p);
+            src = psel_lookup(u, [&](uint32_t j) { return tex[j]; }, (uint32_t)tiles, 0ull, W, cw, (uint32_t)P, err);
+            out_fit[p] = fit[src];
+        }
+        src = __shfl_sync(0xFFFFFFFFu, src, 0);
+        const uint4 *a = reinterpret_cast<const uint4 *>(pop + (size_t)src * mat_bytes);
+        uint4 *b = reinterpret_cast<uint4 *>(out_pop + (size_t)p * mat_bytes);
+        for (size_t e = lane; e < mat_bytes / 16; e += 32)
+            b[e] = a[e];
+    }
+}
+
+cudaError_t launch_select_prob(const void *pop, const uint32_t *fit, int64_t N, size_t mat_bytes, uint32_t seed,
+                               uint32_t pop_id, uint32_t gen, const SelWork &w, void *scratch_pop,
+                               uint32_t *scratch_fit, cudaStream_t s)
+{
+    const int64_t P = 4 * N, n_keep = 2 * N, tiles = (P + 31) / 32;
+    int64_t tg = (tiles * 32 + 255) / 256;
+    if (tg > 4096)
+        tg = 4096;
+    k_psel_tiles<<<(unsigned)tg, 256, 0, s>>>(fit, P, w.cw, w.tmask);
+    k_psel_scan<<<1, 1024, 0, s>>>(w.tmask, tiles, w.tex, w.wtotal);
+    int64_t gg = (n_keep * 32 + 255) / 256;
+    if (gg > 8192)
+        gg = 8192;
+    k_psel_gather<<<(unsigned)gg, 256, 0, s>>>((const uint8_t *)pop, fit, mat_bytes, n_keep, w.tex, w.cw, w.wtotal,
+                                               tiles, P, seed, pop_id, gen, (uint8_t *)scratch_pop, scratch_fit,
+                                               w.err);
+    note_launches(3);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_select(const void *pop, const uint32_t *fit, int64_t N, size_t mat_bytes, uint32_t seed,
                           uint32_t pop_id, uint32_t gen, const SelWork &w, void *scratch_pop, uint32_t *scratch_fit,
                           cudaStream_t s)

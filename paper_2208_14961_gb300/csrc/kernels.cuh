@@ -87,12 +87,22 @@ struct SelWork {
     unsigned long long *perm_keys;  // [2N] when 2N > kPermSmemMax
     uint32_t *perm_cnt;       // [2 * buckets] when 2N > kPermSmemMax
     uint32_t *err;
+    // probabilistic selection: in-tile inclusive weight prefixes [tiles][32],
+    // exclusive prefix of the tile sums [tiles], total weight [1] (the tile
+    // sums themselves go to tmask)
+    unsigned long long *cw, *tex, *wtotal;
 };
 // Selection of generation `gen`: leaves in scratch_pop[0, 2N) / scratch_fit the
 // parents in placement order (matrix bytes per slot = mat_bytes).
 cudaError_t launch_select(const void *pop, const uint32_t *fit, int64_t N, size_t mat_bytes, uint32_t seed,
                           uint32_t pop_id, uint32_t gen, const SelWork &w, void *scratch_pop, uint32_t *scratch_fit,
                           cudaStream_t s);
+// Probabilistic selection of generation `gen` (weights inverse to F): the 2N
+// drawn parents into scratch_pop[0, 2N) / scratch_fit.  Needs w.cw, w.tex,
+// w.wtotal and w.tmask.
+cudaError_t launch_select_prob(const void *pop, const uint32_t *fit, int64_t N, size_t mat_bytes, uint32_t seed,
+                               uint32_t pop_id, uint32_t gen, const SelWork &w, void *scratch_pop,
+                               uint32_t *scratch_fit, cudaStream_t s);
 // Survivor orders pi of `ngen` consecutive generations into out[ngen][n],
 // one block per generation.  The first generation is gen0, or *gen_dev + 1
 // when gen_dev is not null (a device-side counter, so that a captured launch
@@ -128,6 +138,7 @@ struct FusedPop {
     uint32_t *gen_dev;         // generation counter: read at start, advanced at exit
     int8_t *gram;              // incremental mode: [P][dpad] tiled half-Gram (common.cuh), or null
     uint32_t *gidx[2];         // incremental mode: slot -> Gram buffer, ping-pong with pop
+    unsigned long long *cw;    // probabilistic selection: in-tile weight prefixes [ntiles][32]
     int32_t dpad;              // bytes per Gram buffer (64 per tile)
     int32_t m, W, NC, NR, kind, traj_cap;
     int32_t nch;                 // chunks per column of the warp-level Gram (warp_gram_chunks)
@@ -149,6 +160,7 @@ struct FusedParams {
     int32_t src;             // ping-pong buffer holding the current population
     int32_t warp_buf_words;  // shared words per warp for m > 32 populations
     int32_t inc_ring;        // 16-byte slots per warp of the incremental copy ring (0: no incremental population)
+    int32_t psel;            // probabilistic selection (every population), else truncation
     uint32_t *bar;           // grid-barrier counter (zeroed before the launch)
     uint32_t *err;           // device error word
     int32_t *done;           // generations completed

@@ -21,6 +21,7 @@ FIT_SQ, FIT_ABS, FIT_NNZ = 0, 1, 2
 STORE_INT8, STORE_BITS, STORE_E4M3, STORE_BF16 = 0, 1, 2, 3
 PATH_AUTO, PATH_INT32, PATH_IMMA, PATH_FP8, PATH_BF16, PATH_POPC, PATH_FP8_WARP = range(7)
 GA_REAL_F32, GA_REAL_F64 = 0, 1
+SEL_TRUNCATION, SEL_PROBABILISTIC = 0, 1
 
 _STATUS_NAMES = {0: "GA_OK", 1: "GA_EINVAL", 2: "GA_ENOMEM", 3: "GA_ECUDA", 4: "GA_ETIMEOUT",
                  5: "GA_EUNSUPPORTED"}
@@ -45,6 +46,7 @@ class ga_config(ctypes.Structure):
         ("path", ctypes.c_int32),
         ("traj_cap", ctypes.c_int32),
         ("mutation", ctypes.c_int32),
+        ("selection", ctypes.c_int32),
     ]
 
 
@@ -218,7 +220,8 @@ class Population:
 
     def __init__(self, m: int, N: int, seed: int = 0, pop_id: int = 0, NC: int = 1, NR: int = 1,
                  fitness: int = FIT_SQ, storage: int = STORE_BITS, path: int = PATH_AUTO,
-                 traj_cap: int = 1024, device="cuda", stream=None, mutation: int = 0):
+                 traj_cap: int = 1024, device="cuda", stream=None, mutation: int = 0,
+                 selection: int = SEL_TRUNCATION):
         lib = load()
         self.m, self.N, self.P = m, N, 4 * N
         self.storage = storage
@@ -226,7 +229,8 @@ class Population:
         self.pop = empty_population(storage, m, self.P, device)
         self.fit = torch.zeros(self.P, dtype=torch.int32, device=device)
         self.cfg = ga_config(m=m, NC=NC, N=N, seed=seed, pop_id=pop_id, NR=NR, fitness=fitness,
-                             storage=storage, path=path, traj_cap=traj_cap, mutation=mutation)
+                             storage=storage, path=path, traj_cap=traj_cap, mutation=mutation,
+                             selection=selection)
         ctx = ctypes.c_void_p()
         check(lib.ga_create(ctypes.byref(self.cfg), _ptr(self.pop), _ptr(self.fit),
                             ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(ctx)))

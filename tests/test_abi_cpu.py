@@ -38,8 +38,9 @@ def test_binding_covers_the_header():
 
 def test_config_struct_layout():
     from paper_2208_14961_gb300 import hadga
-    assert ctypes.sizeof(hadga.ga_config) == 48
+    assert ctypes.sizeof(hadga.ga_config) == 56
     assert hadga.ga_config.N.offset == 8
+    assert hadga.ga_config.selection.offset == 48
 
 
 def test_version_and_storage_bytes(lib):
@@ -56,7 +57,7 @@ def test_version_and_storage_bytes(lib):
 
 @pytest.mark.parametrize("field,value", [("m", 18), ("m", 0), ("m", 260), ("N", 0), ("NC", 0), ("NR", 65),
                                          ("fitness", 3), ("storage", 2), ("traj_cap", 0), ("mutation", 2), ("mutation", -1),
-                                         ("path", 3)])
+                                         ("path", 3), ("selection", 2), ("selection", -1)])
 def test_create_rejects_bad_config_without_gpu(lib, field, value):
     from paper_2208_14961_gb300 import hadga
     cfg = hadga.ga_config(m=20, NC=1, N=10, seed=0, pop_id=0, NR=1, fitness=0, storage=1, path=0,
