@@ -216,8 +216,19 @@ ga_status ga_step_multi_graph(ga_ctx *const *ctxs, int32_t n, int32_t generation
  * current population; ga_init_population, ga_set_slot and the one-kernel-
  * per-operator calls mark it stale and the next ga_step rebuilds it.  After
  * writing the population buffer directly, enable again.  enable = 0 frees
- * the Gram storage. */
+ * the Gram storage.  enable = 2 (AUTO) chooses by measurement: from the
+ * current population it runs 4 + 32 generations of the fused path with full
+ * recomputation and the same with the stored Gram, timing the last 32 of
+ * each with CUDA events, restores the population, fitness, generation and
+ * trajectory, and keeps the faster mode (the times are reported by
+ * ga_get_incremental).  Synchronises; allocates a copy of the state for the
+ * duration of the call. */
 ga_status ga_set_incremental(ga_ctx *ctx, int32_t enable);
+
+/* Whether incremental mode is on, and the milliseconds per generation the
+ * last AUTO choice measured with full recomputation and with the stored
+ * Gram (0 if AUTO never ran).  Host only. */
+ga_status ga_get_incremental(const ga_ctx *ctx, int32_t *enabled, float *full_ms_per_gen, float *inc_ms_per_gen);
 
 /* Full recomputation check of the incremental state: recomputes every
  * slot's Gram and fitness from the population and counts the stored

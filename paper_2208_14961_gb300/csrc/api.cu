@@ -74,6 +74,7 @@ struct ga_ctx {
     // incremental Gram-delta mode (BITS, 32 < m <= 128)
     int incremental = 0;
     int gram_valid = 0;
+    float auto_full_ms = 0.f, auto_inc_ms = 0.f;  // ms per generation measured by the AUTO choice
     int dpad = 0;
     void *gram_mem = nullptr;                 // gram | gidx[0] | gidx[1] | counts
     int8_t *gram = nullptr;
@@ -846,11 +847,17 @@ ga_status ga_step_multi_graph(ga_ctx *const *ctxs, int32_t n, int32_t generation
     return GA_OK;
 }
 
+static ga_status incremental_auto(ga_ctx *ctx);
+
 ga_status ga_set_incremental(ga_ctx *ctx, int32_t enable)
 {
     ga_status st = begin(ctx);
     if (st != GA_OK)
         return st;
+    if (enable < 0 || enable > 2)
+        return set_error(ctx, GA_EINVAL, "enable must be 0 (off), 1 (on) or 2 (choose by measurement)");
+    if (enable == 2)
+        return incremental_auto(ctx);
     if (!enable) {
         cudaStreamSynchronize(ctx->stream);
         cudaFree(ctx->gram_mem);
@@ -893,6 +900,107 @@ ga_status ga_set_incremental(ga_ctx *ctx, int32_t enable)
                     "Gram store");
     ctx->gram_valid = st == GA_OK;
     return st;
+}
+
+// GA_INC_AUTO: from the current population, time kAutoGens generations of
+// the fused path with full fitness recomputation and with the stored Gram
+// (after kAutoWarm untimed generations each, the same for both), restore the
+// population, fitness, generation and trajectory, and keep the faster mode.
+static ga_status incremental_auto(ga_ctx *ctx)
+{
+    constexpr int kAutoWarm = 4, kAutoGens = 32;
+    // the same preconditions as enabling (reports GA_EUNSUPPORTED)
+    ga_status st = ga_set_incremental(ctx, 1);
+    if (st != GA_OK)
+        return st;
+    const size_t pop_bytes = (size_t)ctx->P * ctx->mat_bytes, fit_bytes = (size_t)ctx->P * 4u,
+                 traj_bytes = (size_t)ctx->cfg.traj_cap * 8u;
+    void *save = nullptr;
+    cudaError_t e = dev_alloc(&save, pop_bytes + fit_bytes + traj_bytes + 64);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(ctx, e == cudaErrorMemoryAllocation ? GA_ENOMEM : GA_ECUDA,
+                         "incremental AUTO: state copy: %s", cudaGetErrorString(e));
+    }
+    char *sp = (char *)save, *sf = sp + pop_bytes, *st_traj = sf + fit_bytes;
+    const uint32_t g0 = ctx->gen;
+    auto copy = [&](void *dst, const void *src, size_t n) {
+        return cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToDevice, ctx->stream);
+    };
+    e = copy(sp, ctx->pop, pop_bytes);
+    if (e == cudaSuccess)
+        e = copy(sf, ctx->fit, fit_bytes);
+    if (e == cudaSuccess)
+        e = copy(st_traj, ctx->traj, traj_bytes);
+    auto restore = [&]() {
+        cudaError_t r = copy(ctx->pop, sp, pop_bytes);
+        if (r == cudaSuccess)
+            r = copy(ctx->fit, sf, fit_bytes);
+        if (r == cudaSuccess)
+            r = copy(ctx->traj, st_traj, traj_bytes);
+        ctx->gen = g0;
+        ctx->gram_valid = 0;
+        return r;
+    };
+    float ms[2] = {0.f, 0.f};
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (e == cudaSuccess)
+        e = cudaEventCreate(&ev[0]);
+    if (e == cudaSuccess)
+        e = cudaEventCreate(&ev[1]);
+    for (int mode = 0; mode < 2 && e == cudaSuccess && st == GA_OK; ++mode) {
+        ctx->incremental = mode;
+        if (mode == 1) {
+            e = launch_gram_store((const uint32_t *)ctx->pop, ctx->m, ctx->P, ctx->gram, ctx->dpad, ctx->gidx[0],
+                                  ctx->stream);
+            ctx->gram_valid = e == cudaSuccess;
+        }
+        if (e == cudaSuccess)
+            st = fused_run(&ctx, 1, kAutoWarm, 0, nullptr);
+        if (st == GA_OK && e == cudaSuccess)
+            e = cudaEventRecord(ev[0], ctx->stream);
+        if (st == GA_OK && e == cudaSuccess)
+            st = fused_run(&ctx, 1, kAutoGens, 0, nullptr);
+        if (st == GA_OK && e == cudaSuccess)
+            e = cudaEventRecord(ev[1], ctx->stream);
+        if (st == GA_OK && e == cudaSuccess)
+            e = cudaEventSynchronize(ev[1]);
+        if (st == GA_OK && e == cudaSuccess)
+            e = cudaEventElapsedTime(&ms[mode], ev[0], ev[1]);
+        if (st == GA_OK && e == cudaSuccess)
+            st = ga_sync(ctx);
+        const cudaError_t r = restore();
+        if (e == cudaSuccess)
+            e = r;
+    }
+    for (cudaEvent_t x : ev)
+        if (x)
+            cudaEventDestroy(x);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(save);
+    if (st != GA_OK)
+        return st;
+    if (e != cudaSuccess)
+        return cuda_check(ctx, e, "incremental AUTO");
+    ctx->auto_full_ms = ms[0] / kAutoGens;
+    ctx->auto_inc_ms = ms[1] / kAutoGens;
+    if (ms[1] < ms[0]) {
+        ctx->incremental = 1;  // the Gram of the restored population is rebuilt by the next ga_step
+        return GA_OK;
+    }
+    ctx->incremental = 1;
+    return ga_set_incremental(ctx, 0);
+}
+
+ga_status ga_get_incremental(const ga_ctx *ctx, int32_t *enabled, float *full_ms_per_gen, float *inc_ms_per_gen)
+{
+    if (!ctx || !enabled || !full_ms_per_gen || !inc_ms_per_gen)
+        return set_error(nullptr, GA_EINVAL, "NULL argument");
+    *enabled = ctx->incremental;
+    *full_ms_per_gen = ctx->auto_full_ms;
+    *inc_ms_per_gen = ctx->auto_inc_ms;
+    return GA_OK;
 }
 
 ga_status ga_check_incremental(ga_ctx *ctx, uint64_t *entry_mismatch, uint64_t *fit_mismatch)

@@ -72,6 +72,8 @@ SIGNATURES = {
     "ga_set_fused_grid": (_i32, [_vp, _i32]),
     "ga_set_incremental": (_i32, [_vp, _i32]),
     "ga_check_incremental": (_i32, [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
+    "ga_get_incremental": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_float),
+                                   ctypes.POINTER(ctypes.c_float)]),
     "ga_get_gram": (_i32, [_vp, _i64, _vp]),
     "ga_best": (_i32, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_u32)]),
     "ga_trajectory": (_i32, [_vp, _vp, _vp, _i32, ctypes.POINTER(_i32)]),
@@ -294,10 +296,19 @@ class Population:
         self._chk(load().ga_profile_read(self.ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)))
         return float(a.value), float(b.value), int(n.value)
 
-    def set_incremental(self, enable: bool):
-        """a7: keep each individual's Gram and update it by deltas in ga_step."""
-        self._chk(load().ga_set_incremental(self.ctx, int(enable)))
-        self.incremental = bool(enable)
+    def set_incremental(self, enable):
+        """a7: keep each individual's Gram and update it by deltas in ga_step.
+        enable: True / False, or "auto" to keep whichever of the two modes a
+        short timed run from the current population finds faster."""
+        mode = 2 if enable == "auto" else int(bool(enable))
+        self._chk(load().ga_set_incremental(self.ctx, mode))
+        self.incremental = self.incremental_choice()[0]
+
+    def incremental_choice(self):
+        """(incremental on, full ms/generation, incremental ms/generation) of the last AUTO choice."""
+        en, a, b = ctypes.c_int32(), ctypes.c_float(), ctypes.c_float()
+        self._chk(load().ga_get_incremental(self.ctx, ctypes.byref(en), ctypes.byref(a), ctypes.byref(b)))
+        return bool(en.value), float(a.value), float(b.value)
 
     def check_incremental(self):
         """Full recomputation check: (mismatched Gram entries, mismatched fitness words)."""

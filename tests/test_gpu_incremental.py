@@ -132,3 +132,35 @@ def test_incremental_with_mutation_method1():
     assert np.array_equal(pop.fitness_host(), F)
     assert pop.check_incremental() == (0, 0)
     pop.close()
+
+
+@pytest.mark.parametrize("m,N", [(64, 600), (100, 300)])
+def test_auto_choice_measures_both_and_leaves_the_state(m, N):
+    """ga_set_incremental(AUTO) times both modes from the current population,
+    keeps the faster, and leaves population, fitness, generation and
+    trajectory as they were; the run that follows matches the oracle."""
+    h = need_gpu()
+    gens0, gens = 5, 8
+    pop = h.Population(m, N, seed=6, storage=h.STORE_BITS, traj_cap=64)
+    pop.init_population()
+    pop.fitness()
+    pop.step(gens0)
+    pop.sync()
+    before = pop.as_int8(), pop.fitness_host(), pop.trajectory(), pop.generation()
+    pop.set_incremental("auto")
+    on, full_ms, inc_ms = pop.incremental_choice()
+    assert full_ms > 0 and inc_ms > 0
+    assert on == (inc_ms < full_ms)
+    after = pop.as_int8(), pop.fitness_host(), pop.trajectory(), pop.generation()
+    assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
+    assert np.array_equal(before[2][0], after[2][0]) and np.array_equal(before[2][1], after[2][1])
+    assert before[3] == after[3] == gens0
+    pop.step(gens)
+    pop.sync()
+    ref = oracle.init_population(m, 4 * N, 6)
+    F = oracle.fitness(ref, oracle.FIT_SQ)
+    oracle.run(ref, F, N, 1, 1, oracle.FIT_SQ, 6, 0, 0, gens0 + gens)
+    assert np.array_equal(pop.as_int8(), ref) and np.array_equal(pop.fitness_host(), F)
+    if on:
+        assert pop.check_incremental() == (0, 0)
+    pop.close()
