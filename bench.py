@@ -669,6 +669,60 @@ def search_workload(args):
             print(json.dumps(line), flush=True)
 
 
+# Sec. 4.3, Tables 4 and 5 of the paper (the tables numbered 3 and 4 in its
+# source): mean generations to a Hadamard matrix of order 12 and 16, F2,
+# 10 runs per cell, rows NR = 1..4, columns NC = 1..4 (the order-16 cells
+# NR = 1, NC = 2..4 are those where most runs found none).
+PAPER_TABLE4_M12 = [[34.2, 35.8, 37.4, 35.8], [32.3, 38.8, 40.5, 43.4], [35.2, 42.6, 47.5, 50.7],
+                    [36.3, 46.0, 49.9, 65.7]]
+PAPER_TABLE5_M16 = [[130.1, 119.4, 116.0, 115.5], [121.0, 181.3, 135.0, 168.7], [120.0, 158.1, 165.9, 202.7],
+                    [120.2, 166.2, 236.2, 301.6]]
+
+
+def table45_workload(args):
+    """The convergence statistics of Sec. 4.3 (Tables 4 and 5): for m = 12
+    and 16, F2, N = 1000 (the listing's default population, P = 4,000), every
+    NC, NR in 1..4, `--t45-seeds` seeded runs of the fused path with
+    stop_at_zero, capped at `--t45-cap` generations.  One JSON line per
+    (m, NC, NR): runs that found a Hadamard matrix (each checked Q^T Q = m I
+    on the host), the mean and median generations of those runs, and the
+    paper's mean for the cell (a plausibility band: the paper's random
+    streams and its int64/int32 index reading differ from this build's)."""
+    import numpy as np
+
+    from paper_2208_14961_gb300.build import build
+    build()
+    from paper_2208_14961_gb300 import hadga as h
+
+    tables = {12: PAPER_TABLE4_M12, 16: PAPER_TABLE5_M16}
+    for m in [int(x) for x in args.t45_ms.split(",")]:
+        for NR in range(1, 5):
+            for NC in range(1, 5):
+                gens_found, verified = [], True
+                t0 = time.perf_counter()
+                for seed in range(args.t45_seeds):
+                    pop = h.Population(m, 1000, seed=1000 + seed, NC=NC, NR=NR, fitness=h.FIT_NNZ,
+                                       storage=h.STORE_BITS, traj_cap=args.t45_cap)
+                    pop.set_strict(True)
+                    pop.init_population()
+                    pop.fitness()
+                    done = pop.step(args.t45_cap, stop_at_zero=True)
+                    slot, best = pop.best()
+                    if best == 0:
+                        Q = pop.get_slot(slot).astype(np.int64)
+                        verified = verified and bool(np.array_equal(Q.T @ Q, m * np.eye(m, dtype=np.int64)))
+                        gens_found.append(done)
+                    pop.close()
+                line = {"workload": "paper Sec. 4.3 convergence (Tables 4-5)", "m": m, "NC": NC, "NR": NR,
+                        "fitness": "F2", "P": 4000, "runs": args.t45_seeds, "cap": args.t45_cap,
+                        "found": len(gens_found), "verified_QtQ_eq_mI": verified,
+                        "mean_generations_found": float(np.mean(gens_found)) if gens_found else None,
+                        "median_generations_found": float(np.median(gens_found)) if gens_found else None,
+                        "paper_mean_generations": tables[m][NR - 1][NC - 1] if m in tables else None,
+                        "seconds": time.perf_counter() - t0}
+                print(json.dumps(line), flush=True)
+
+
 def incremental_workload(args):
     """Incremental Gram-delta fitness (a7) on m=100, P=20,000 bit-packed
     balanced matrices (seed 4, F_sq, NC = NR = 1) for `--inc-gens`
@@ -1063,6 +1117,10 @@ def main():
     ap.add_argument("--search-seeds", type=int, default=3)
     ap.add_argument("--search-seconds", type=float, default=60.0)
     ap.add_argument("--search-chunk", type=int, default=2048)
+    ap.add_argument("--table45", action="store_true", help="the paper's convergence tables (Sec. 4.3)")
+    ap.add_argument("--t45-ms", default="12,16")
+    ap.add_argument("--t45-seeds", type=int, default=20)
+    ap.add_argument("--t45-cap", type=int, default=4000)
     ap.add_argument("--case", default="", help="one named small workload for ncu (see PROFILE_CASES)")
     ap.add_argument("--case-gens", type=int, default=8)
     args = ap.parse_args()
@@ -1089,6 +1147,9 @@ def main():
         return
     if args.table1:
         table1_workload(args)
+        return
+    if args.table45:
+        table45_workload(args)
         return
     args.warmup = max(args.warmup, 3)
 
