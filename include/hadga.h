@@ -244,6 +244,21 @@ ga_status ga_get_gram(ga_ctx *ctx, int64_t slot, int32_t *host_G);
  * (0 = one per SM, the default).  Chosen by the autotuner. */
 ga_status ga_set_fused_grid(ga_ctx *ctx, int32_t blocks);
 
+/* Launch shape of this population in the persistent kernel (chosen by the
+ * autotuner per order; results are identical for every shape).  tpp:
+ * threads per pair of the m <= 32 build, 2 (each thread computes a whole
+ * offspring) or 4 (each half of its terms); 0 = default 4.  nch: chunks per
+ * column of the warp-level Gram of m > 32 (the m * nch work units of a
+ * warp; 1 <= nch <= min(16, m/2)); 0 = the built-in cost model.  Host only;
+ * applies from the next ga_step. */
+ga_status ga_set_fused_shape(ga_ctx *ctx, int32_t tpp, int32_t nch);
+
+/* Process-wide override of GA_PATH_AUTO for (storage, m, kind): the Gram
+ * path the autotuner measured fastest on this GPU (GA_PATH_AUTO clears the
+ * override and restores the built-in choice).  GA_EINVAL when the path
+ * cannot compute that fitness of that storage at that order.  Host only. */
+ga_status ga_set_auto_path(int32_t storage, int32_t m, int32_t kind, int32_t path);
+
 /* 1 if ga_step runs the fused kernel for this context, 0 if it falls back. */
 int32_t ga_step_is_fused(const ga_ctx *ctx);
 

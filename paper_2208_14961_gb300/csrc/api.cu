@@ -65,6 +65,8 @@ struct ga_ctx {
     uint32_t *fstate = nullptr;               // kFusedStateWords selection state
     uint32_t *fmisc = nullptr;                // [0] grid-barrier counter, [1] generations done, [2] generation
     int fused_blocks = 0;                     // persistent blocks (0: one per SM)
+    int shape_tpp = 0;                        // m <= 32: threads per pair (0: default 4)
+    int shape_nch = 0;                        // m > 32: warp Gram chunks per column (0: cost model)
     unsigned long long *ftmask = nullptr;
     uint32_t *fperm = nullptr;                // [chunk][2N] survivor orders
     unsigned long long *fperm_keys = nullptr; // [chunk][2N] sort keys when 2N > kPermSmemMax
@@ -147,8 +149,17 @@ constexpr int kChunk = 64;
 // storage takes the tcgen05 path for F_sq at m = 128 and 256 and the
 // warp-level FP8 MMA otherwise (HBM-bound at m <= 64; F1 / F2; orders the
 // tcgen05 kernel does not tile); bf16 storage takes tcgen05.
+// Measured overrides of GA_PATH_AUTO (ga_set_auto_path, set by the
+// autotuner), by storage, order / 4 and fitness kind; 0 = none.
+std::atomic<int> g_auto_override[4][kMaxM / 4 + 1][3];
+
 int auto_path(int storage, int m, int kind)
 {
+    if (storage >= 0 && storage < 4 && m >= 4 && m <= kMaxM && (m & 3) == 0 && kind >= 0 && kind < 3) {
+        const int o = g_auto_override[storage][m / 4][kind].load(std::memory_order_relaxed);
+        if (o != 0)
+            return o;
+    }
     if (storage == GA_STORE_E4M3)
         return (kind == GA_FIT_SQ && (m == 128 || m == 256)) ? GA_PATH_FP8 : GA_PATH_FP8_WARP;
     if (storage == GA_STORE_BF16)
@@ -504,7 +515,8 @@ static ga_status fused_run(ga_ctx *const *ctxs, int n, int32_t generations, int 
         p.gen_dev = c->fmisc + 2;
         p.m = c->m;
         p.W = c->W;
-        p.nch = warp_gram_chunks(c->m);
+        p.nch = c->shape_nch > 0 ? c->shape_nch : warp_gram_chunks(c->m);
+        p.tpp = c->shape_tpp == 2 ? 2 : 4;
         p.shared_mut = c->cfg.mutation;
         p.NC = c->cfg.NC;
         p.NR = c->cfg.NR;
@@ -518,7 +530,7 @@ static ga_status fused_run(ga_ctx *const *ctxs, int n, int32_t generations, int 
         tiles += p.ntiles;
         if (c->m <= 32) {
             p.work_base = tslots;
-            tslots += (uint32_t)((4 * c->N + 31) / 32 * 32);
+            tslots += (uint32_t)(((int64_t)p.tpp * c->N + 31) / 32 * 32);
         } else {
             p.work_base = wpairs;
             wpairs += (uint32_t)(2 * c->N);  // one warp item per offspring
@@ -1059,6 +1071,42 @@ ga_status ga_get_gram(ga_ctx *ctx, int64_t slot, int32_t *host_G)
             host_G[i * m + j] = host_G[j * m + i] = 2 * (int32_t)h[(size_t)t * 64 + (i & 7) * 8 + (j & 7)];
         }
     }
+    return GA_OK;
+}
+
+ga_status ga_set_fused_shape(ga_ctx *ctx, int32_t tpp, int32_t nch)
+{
+    if (!ctx)
+        return set_error(nullptr, GA_EINVAL, "ctx is NULL");
+    if (tpp != 0 && tpp != 2 && tpp != 4)
+        return set_error(ctx, GA_EINVAL, "threads per pair must be 0 (default), 2 or 4");
+    if (nch < 0 || nch > 16 || (nch > 0 && nch > ctx->m / 2))
+        return set_error(ctx, GA_EINVAL, "nch=%d must be 0 (cost model) or in [1, min(16, m/2)]", nch);
+    ctx->shape_tpp = tpp;
+    ctx->shape_nch = nch;
+    return GA_OK;
+}
+
+ga_status ga_set_auto_path(int32_t storage, int32_t m, int32_t kind, int32_t path)
+{
+    ga_status st = check_storage_m(nullptr, storage, m);
+    if (st != GA_OK)
+        return st;
+    if (kind < GA_FIT_SQ || kind > GA_FIT_NNZ)
+        return set_error(nullptr, GA_EINVAL, "unknown fitness %d", kind);
+    if (path < GA_PATH_AUTO || path > GA_PATH_FP8_WARP)
+        return set_error(nullptr, GA_EINVAL, "unknown path %d", path);
+    if (path != GA_PATH_AUTO) {
+        const bool tc = path == GA_PATH_FP8 || path == GA_PATH_BF16;
+        const bool ok = tc ? ((path == GA_PATH_FP8) == (storage == GA_STORE_E4M3) &&
+                              (path == GA_PATH_BF16) == (storage == GA_STORE_BF16) && kind == GA_FIT_SQ &&
+                              fitness_tc_supported(storage, m))
+                           : fitness_path_supported(storage, m, path);
+        if (!ok)
+            return set_error(nullptr, GA_EINVAL, "path %d cannot compute fitness %d of storage %d at m=%d", path, kind,
+                             storage, m);
+    }
+    g_auto_override[storage][m / 4][kind].store(path, std::memory_order_relaxed);
     return GA_OK;
 }
 

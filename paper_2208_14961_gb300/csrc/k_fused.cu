@@ -350,21 +350,27 @@ __device__ __forceinline__ uint32_t fitness_half_regs(const uint32_t (&c)[M])
 }
 
 // ---------------------------------------------------------------------------
-// m <= 32: four threads per pair (lanes 4j .. 4j + 3): `half` selects the
-// offspring O_{1 + half} (and the parent P_{1 + half} it carries over), `sub`
-// splits its fitness terms; thread sub = 1 places the parent, sub = 0 the
-// offspring.  Each thread returns the one (fitness, slot) it placed.
+// m <= 32, TPP = 4: four threads per pair (lanes 4j .. 4j + 3): `half`
+// selects the offspring O_{1 + half} (and the parent P_{1 + half} it carries
+// over), `sub` splits its fitness terms; thread sub = 1 places the parent,
+// sub = 0 the offspring.  Each thread returns the one (fitness, slot) it
+// placed in f_out[0], slot_out[0].
+// TPP = 2: two threads per pair (lanes 2j, 2j + 1 = half), each computing
+// all fitness terms of its offspring and placing both the parent it
+// carries over (f_out[0], slot_out[0]) and the offspring (f_out[1],
+// slot_out[1]).  The autotuner picks TPP per order.
 // ---------------------------------------------------------------------------
-template <int M>
+template <int M, int TPP>
 __device__ __forceinline__ void pair_thread(const FusedPop &p, const PopSel &S, int src, uint32_t gen, const Pre &pre,
                                             uint32_t k, int half, int sub, bool valid, const Surv &sv, uint32_t *err,
-                                            uint32_t &f_out, uint32_t &slot_out)
+                                            uint32_t (&f_out)[2], uint32_t (&slot_out)[2])
 {
+    static_assert(TPP == 2 || TPP == 4, "two or four threads per pair");
     const uint32_t N = (uint32_t)p.N;
     uint32_t s_mine = 0;
     if (valid)
         s_mine = S.psel ? psel_slot_of(pre.u, p, S, sv, err) : survivor_of(pre.d, p, S, sv, err);
-    const uint32_t s_other = __shfl_xor_sync(FULL, s_mine, 2);
+    const uint32_t s_other = __shfl_xor_sync(FULL, s_mine, TPP == 4 ? 2 : 1);
     const uint32_t *src_pop = p.pop[src];
     uint32_t *dst_pop = p.pop[src ^ 1];
     const uint32_t s1 = half ? s_other : s_mine, s2 = half ? s_mine : s_other;
@@ -383,17 +389,17 @@ __device__ __forceinline__ void pair_thread(const FusedPop &p, const PopSel &S, 
         for (int j = 0; j < M; ++j)
             p1[j] = p2[j] = 0u;
     }
-    if (valid && sub) {
+    if (valid && (TPP == 2 || sub)) {
         // the parent this half carries over keeps its slot order k / k + N
-        f_out = ldcg32(p.fit[src] + s_mine);
-        slot_out = half ? k + N : k;
-        uint4 *d = reinterpret_cast<uint4 *>(dst_pop + (size_t)slot_out * M);
+        f_out[0] = ldcg32(p.fit[src] + s_mine);
+        slot_out[0] = half ? k + N : k;
+        uint4 *d = reinterpret_cast<uint4 *>(dst_pop + (size_t)slot_out[0] * M);
 #pragma unroll
         for (int v = 0; v < M / 4; ++v) {
             const uint32_t *q = half ? p2 : p1;
             d[v] = make_uint4(q[4 * v], q[4 * v + 1], q[4 * v + 2], q[4 * v + 3]);
         }
-        p.fit[src ^ 1][slot_out] = f_out;
+        p.fit[src ^ 1][slot_out[0]] = f_out[0];
     }
     // crossover (Sec. 3.4): O1 = P1[:, :c] | P2[:, c:], O2 = P2[:, :c] | P1[:, c:]
     const int c = (int)pre.c;
@@ -439,27 +445,38 @@ __device__ __forceinline__ void pair_thread(const FusedPop &p, const PopSel &S, 
             }
         }
     }
-    // fitness: this thread's half of the terms (columns rotated by one for sub 1)
+    // fitness: this thread's half of the terms (columns rotated by one for
+    // sub 1), or both halves with two threads per pair
     uint32_t cr[M];
 #pragma unroll
     for (int j = 0; j < M; ++j)
-        cr[j] = sub ? o[(j + 1) % M] : o[j];
+        cr[j] = (TPP == 2 || sub) ? o[(j + 1) % M] : o[j];
     uint32_t part;
     switch (p.kind) {
     case FIT_SQ: part = fitness_half_regs<M, FIT_SQ>(cr); break;
     case FIT_ABS: part = fitness_half_regs<M, FIT_ABS>(cr); break;
     default: part = fitness_half_regs<M, FIT_NNZ>(cr); break;
     }
-    const uint32_t sum = part + __shfl_xor_sync(FULL, part, 1);
+    uint32_t sum;
+    if constexpr (TPP == 4) {
+        sum = part + __shfl_xor_sync(FULL, part, 1);
+    } else {
+        switch (p.kind) {
+        case FIT_SQ: sum = part + fitness_half_regs<M, FIT_SQ>(o); break;
+        case FIT_ABS: sum = part + fitness_half_regs<M, FIT_ABS>(o); break;
+        default: sum = part + fitness_half_regs<M, FIT_NNZ>(o); break;
+        }
+    }
     const uint32_t f = p.kind == FIT_SQ ? fit_finish<FIT_SQ>(sum) : fit_finish<FIT_ABS>(sum);
-    if (valid && !sub) {
-        slot_out = 2u * N + k + (half ? N : 0u);
-        uint4 *d = reinterpret_cast<uint4 *>(dst_pop + (size_t)slot_out * M);
+    const int oi = TPP == 4 ? 0 : 1;  // output entry of the offspring
+    if (valid && (TPP == 2 || !sub)) {
+        slot_out[oi] = 2u * N + k + (half ? N : 0u);
+        uint4 *d = reinterpret_cast<uint4 *>(dst_pop + (size_t)slot_out[oi] * M);
 #pragma unroll
         for (int v = 0; v < M / 4; ++v)
             d[v] = make_uint4(o[4 * v], o[4 * v + 1], o[4 * v + 2], o[4 * v + 3]);
-        p.fit[src ^ 1][slot_out] = f;
-        f_out = f;
+        p.fit[src ^ 1][slot_out[oi]] = f;
+        f_out[oi] = f;
     }
 }
 
@@ -958,6 +975,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
 {
     extern __shared__ __align__(16) uint32_t dyn[];
     __shared__ PopSel S[kMaxPops];
+    // the populations' parameters, copied once from the kernel argument: read
+    // with population indices computed at run time, the argument would be
+    // served by the constant cache, whose misses cost L2 round trips on the
+    // dependent chains of the build phase
+    __shared__ __align__(16) FusedPop PP[kMaxPops];
     __shared__ unsigned long long s_tmp64[32];
     __shared__ uint32_t hoff[kMaxPops];
     __shared__ int s_flag;
@@ -966,6 +988,14 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
 
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
     const int npop = prm.npop;
+    {
+        static_assert(sizeof(FusedPop) % 4 == 0, "FusedPop copies word by word");
+        const uint32_t *from = reinterpret_cast<const uint32_t *>(prm.p);
+        uint32_t *to = reinterpret_cast<uint32_t *>(PP);
+        for (uint32_t e = tid; e < (uint32_t)npop * (uint32_t)(sizeof(FusedPop) / 4); e += blockDim.x)
+            to[e] = from[e];
+        __syncthreads();
+    }
     const uint32_t nblocks = gridDim.x;
     const uint32_t gtid = blockIdx.x * blockDim.x + tid, gthreads = nblocks * blockDim.x;
     // warps enumerated across blocks first, so consecutive work items land on
@@ -992,13 +1022,13 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
     }
     int src = prm.src;
     int done = 0;
-    auto tile_base = [&](int i) { return prm.p[i].tile_base; };
+    auto tile_base = [&](int i) { return PP[i].tile_base; };
 
     // ---- pre-pass: max and OR of the current fitness of every population -----
     // (truncation selection only: probabilistic selection keeps no histograms)
     const bool psel = prm.psel != 0;
     if (tid < npop) {
-        S[tid].gen0 = ldcg32(prm.p[tid].gen_dev);
+        S[tid].gen0 = ldcg32(PP[tid].gen_dev);
         S[tid].psel = psel ? 1u : 0u;
         S[tid].boff = 0xFFFFFFFFu;
     }
@@ -1006,7 +1036,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
     if (!psel) {
         const int par0 = 0;  // buffers alternate with the generation index inside the launch
         for (int i = 0; i < npop; ++i) {
-            const FusedPop &p = prm.p[i];
+            const FusedPop &p = PP[i];
             const uint32_t P = (uint32_t)(4 * p.N);
             uint32_t mx = 0, orr = 0;
             for (uint32_t q = gtid; q < P; q += gthreads) {
@@ -1024,7 +1054,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
         if (!grid_barrier(prm.bar, nblocks, epoch, err))
             return;
         if (tid < npop) {
-            const FusedPop &p = prm.p[tid];
+            const FusedPop &p = PP[tid];
             const uint32_t cap = ldcg32(stat_of(p) + 0);
             const uint32_t v = ctz_or(ldcg32(stat_of(p) + 1 + par0));
             S[tid].cap = cap;
@@ -1032,7 +1062,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
         }
         __syncthreads();
         for (int i = 0; i < npop; ++i) {
-            const FusedPop &p = prm.p[i];
+            const FusedPop &p = PP[i];
             const uint32_t P = (uint32_t)(4 * p.N);
             uint32_t *h = hist_of(p, par0);
             const uint32_t cap = S[i].cap, sh = S[i].shift;
@@ -1057,7 +1087,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
         // first group's histogram buckets (populations [0, g1) whose buckets
         // fit the staging area), held in registers while the
         // selection-independent draws are computed
-        const uint32_t vload = (!psel && tid < npop) ? ldcg32(stat_of(prm.p[tid]) + 1 + par) : 0u;
+        const uint32_t vload = (!psel && tid < npop) ? ldcg32(stat_of(PP[tid]) + 1 + par) : 0u;
         int g1 = 0;
         uint32_t goff = 0;
         while (!psel && g1 < npop) {
@@ -1081,7 +1111,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                     ++i;
                     nb = (S[i].cap >> S[i].shift) + 1u;
                 }
-                hv[r] = ldcg32(hist_of(prm.p[i], par) + (e - base));
+                hv[r] = ldcg32(hist_of(PP[i], par) + (e - base));
             }
         }
         // first tile of this warp: its fitness is loaded now, with the histograms
@@ -1089,7 +1119,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
         int i_pre = 0;
         if (gwarp < TT) {
             i_pre = owner_of(gwarp, npop, tile_base);
-            const FusedPop &p = prm.p[i_pre];
+            const FusedPop &p = PP[i_pre];
             const uint32_t q = (gwarp - p.tile_base) * 32u + lane;
             f_pre = q < (uint32_t)(4 * p.N) ? ldcg32(p.fit[src] + q) : 0u;
         }
@@ -1100,23 +1130,24 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             const uint32_t u = gwarp * 32u + (uint32_t)lane;
             int i = -1;
             for (int j = 0; j < npop; ++j)
-                if (prm.p[j].m <= 32 && u >= prm.p[j].work_base)
-                    i = (i < 0 || prm.p[j].work_base >= prm.p[i].work_base) ? j : i;
+                if (PP[j].m <= 32 && u >= PP[j].work_base)
+                    i = (i < 0 || PP[j].work_base >= PP[i].work_base) ? j : i;
             if (i >= 0) {
-                const FusedPop &p = prm.p[i];
-                const uint32_t local = u - p.work_base, k = local >> 2;
+                const FusedPop &p = PP[i];
+                const uint32_t local = u - p.work_base;
+                const uint32_t k = p.tpp == 2 ? local >> 1 : local >> 2;
+                const int half = (int)(p.tpp == 2 ? (local & 1u) : ((local >> 1) & 1u));
                 if (k < (uint32_t)p.N)
-                    pre0 = make_pre(p, S[i].gen0 + 1u + (uint32_t)t, (uint32_t)t, k, (int)((local >> 1) & 1u),
-                                    psel);
+                    pre0 = make_pre(p, S[i].gen0 + 1u + (uint32_t)t, (uint32_t)t, k, half, psel);
             }
         }
         for (int i = 0; i < npop && !psel; ++i) {
-            uint32_t *hn = hist_of(prm.p[i], par ^ 1);
+            uint32_t *hn = hist_of(PP[i], par ^ 1);
             for (uint32_t e = gtid; e < (uint32_t)kHistR; e += gthreads)
                 hn[e] = 0u;
         }
         if (blockIdx.x == 0 && tid < npop) {
-            const FusedPop &p = prm.p[tid];
+            const FusedPop &p = PP[tid];
             stat_of(p)[1 + (par ^ 1)] = 0u;
             p.traj[(S[tid].gen0 + (uint32_t)t) % (uint32_t)p.traj_cap] = ~0ull;
         }
@@ -1154,7 +1185,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                     int i = 0;
                     while (i + 1 < i1 && e >= hoff[i + 1])
                         ++i;
-                    hcnt[e] = ldcg32(hist_of(prm.p[i], par) + (e - hoff[i]));
+                    hcnt[e] = ldcg32(hist_of(PP[i], par) + (e - hoff[i]));
                 }
             } else {
                 __syncthreads();
@@ -1162,7 +1193,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                     int i = i0;
                     while (i + 1 < i1 && e >= hoff[i + 1])
                         ++i;
-                    hcnt[e] = ldcg32(hist_of(prm.p[i], par) + (e - hoff[i]));
+                    hcnt[e] = ldcg32(hist_of(PP[i], par) + (e - hoff[i]));
                 }
             }
             __syncthreads();
@@ -1170,7 +1201,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                 const int i = i0 + wib;
                 PopSel &s = S[i];
                 const uint32_t nb = (s.cap >> s.shift) + 1u;
-                const uint32_t need2 = (uint32_t)(2 * prm.p[i].N);
+                const uint32_t need2 = (uint32_t)(2 * PP[i].N);
                 uint32_t b = 0, before = 0;
                 const bool found = warp_find_crossing_smem(hcnt + hoff[i], nb, need2, b, before);
                 if (lane == 0) {
@@ -1206,7 +1237,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             while (s_flag) {
                 const int rl = (int)(ref_level % 3u), rz = (int)((ref_level + 1u) % 3u);
                 for (int i = 0; i < npop; ++i) {
-                    const FusedPop &p = prm.p[i];
+                    const FusedPop &p = PP[i];
                     uint32_t *hz = ref_of(p, rz);
                     for (uint32_t e = gtid; e < (uint32_t)kHistR; e += gthreads)
                         hz[e] = 0u;
@@ -1227,7 +1258,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                 if (!grid_barrier(prm.bar, nblocks, epoch, err))
                     return;
                 if (wib < npop && !S[wib].exact) {
-                    const FusedPop &p = prm.p[wib];
+                    const FusedPop &p = PP[wib];
                     PopSel &s = S[wib];
                     const uint32_t sn = max(s.v, s.sr > 12u ? s.sr - 12u : 0u);
                     uint32_t b, before;
@@ -1263,7 +1294,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
         // tile masks: F < T and F == T per 32 slots
         for (uint32_t tl = gwarp; tl < TT; tl += gwarps) {
             const int i = tl == gwarp ? i_pre : owner_of(tl, npop, tile_base);
-            const FusedPop &p = prm.p[i];
+            const FusedPop &p = PP[i];
             const uint32_t P = (uint32_t)(4 * p.N), T = S[i].T;
             const uint32_t q = (tl - p.tile_base) * 32u + lane;
             const uint32_t f = tl == gwarp ? f_pre : (q < P ? ldcg32(p.fit[src] + q) : 0u);
@@ -1301,7 +1332,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                 const uint32_t tt = t0 + (uint32_t)r * blockDim.x;
                 if (tt < TT) {
                     const int i = owner_of(tt, npop, tile_base);
-                    v[r] = ldcg64(prm.p[i].tmask + (tt - prm.p[i].tile_base));
+                    v[r] = ldcg64(PP[i].tmask + (tt - PP[i].tile_base));
                 }
             }
 #pragma unroll
@@ -1326,7 +1357,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             },
             ex, s_tmp64);
         if (tid < npop && psel) {
-            const FusedPop &p = prm.p[tid];
+            const FusedPop &p = PP[tid];
             PopSel &s = S[tid];
             const uint32_t last = p.tile_base + p.ntiles - 1u;
             s.pbase = ex[p.tile_base];
@@ -1336,7 +1367,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             if (s.pW == 0ull)
                 atomicOr(err, ERR_INTERNAL);
         } else if (tid < npop) {
-            const FusedPop &p = prm.p[tid];
+            const FusedPop &p = PP[tid];
             PopSel &s = S[tid];
             const unsigned long long e0 = ex[p.tile_base];
             s.lb = (uint32_t)(e0 >> 32);
@@ -1349,45 +1380,55 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                 atomicOr(err, ERR_INTERNAL);
         }
         __syncthreads();
-        // m <= 32: four threads per pair
+        // m <= 32: two or four threads per pair (FusedPop::tpp)
         for (uint32_t w = gwarp; w < nwork_t; w += gwarps) {
             const uint32_t u = w * 32u;
             // the population whose (32-aligned) thread range holds this warp
             int i = -1;
             for (int j = 0; j < npop; ++j)
-                if (prm.p[j].m <= 32 && u >= prm.p[j].work_base)
-                    i = (i < 0 || prm.p[j].work_base >= prm.p[i].work_base) ? j : i;
-            const FusedPop &p = prm.p[i < 0 ? 0 : i];
+                if (PP[j].m <= 32 && u >= PP[j].work_base)
+                    i = (i < 0 || PP[j].work_base >= PP[i].work_base) ? j : i;
+            const FusedPop &p = PP[i < 0 ? 0 : i];
+            const bool two = p.tpp == 2;
             const uint32_t local = u + (uint32_t)lane - p.work_base;
-            const uint32_t k = local >> 2;
-            const int half = (int)((local >> 1) & 1u), sub = (int)(local & 1u);
+            const uint32_t k = two ? local >> 1 : local >> 2;
+            const int half = (int)(two ? (local & 1u) : ((local >> 1) & 1u)), sub = (int)(local & 1u);
             const bool valid = i >= 0 && k < (uint32_t)p.N;
             const uint32_t gen = S[i < 0 ? 0 : i].gen0 + 1u + (uint32_t)t;
             Pre pre = pre0;
             if (w != gwarp && valid)
                 pre = make_pre(p, gen, (uint32_t)t, k, half, psel);
-            uint32_t fv = 0, sl = 0;
+            uint32_t fv[2] = {0u, 0u}, sl[2] = {0u, 0u};
             const PopSel &s = S[i < 0 ? 0 : i];
             switch (p.m) {
 #define HADGA_PT(MM)                                                                                        \
     case MM:                                                                                                \
-        pair_thread<MM>(p, s, src, gen, pre, k, half, sub, valid, sv, err, fv, sl);                         \
+        if (two)                                                                                            \
+            pair_thread<MM, 2>(p, s, src, gen, pre, k, half, sub, valid, sv, err, fv, sl);                  \
+        else                                                                                                \
+            pair_thread<MM, 4>(p, s, src, gen, pre, k, half, sub, valid, sv, err, fv, sl);                  \
         break;
                 HADGA_PT(4) HADGA_PT(8) HADGA_PT(12) HADGA_PT(16) HADGA_PT(20) HADGA_PT(24) HADGA_PT(28) HADGA_PT(32)
 #undef HADGA_PT
             default:
                 break;
             }
-            if (psel) {
-                // no histogram: the next selection weighs every individual
-            } else if (s.boff != 0xFFFFFFFFu) {
-                if (valid && fv <= s.capn)
-                    atomicAdd(bhist + s.boff + (fv >> s.shiftn), 1u);
-            } else {
-                warp_hist_add(hist_of(p, par ^ 1), valid && fv <= s.capn, fv >> s.shiftn);
+            uint32_t orr = 0;
+            unsigned long long key = ~0ull;
+            for (int e = 0; e < (two ? 2 : 1); ++e) {
+                if (psel) {
+                    // no histogram: the next selection weighs every individual
+                } else if (s.boff != 0xFFFFFFFFu) {
+                    if (valid && fv[e] <= s.capn)
+                        atomicAdd(bhist + s.boff + (fv[e] >> s.shiftn), 1u);
+                } else {
+                    warp_hist_add(hist_of(p, par ^ 1), valid && fv[e] <= s.capn, fv[e] >> s.shiftn);
+                }
+                orr |= valid ? fv[e] : 0u;
+                const unsigned long long ke = valid ? (((unsigned long long)fv[e] << 32) | sl[e]) : ~0ull;
+                key = ke < key ? ke : key;
             }
-            const uint32_t orr = warp_or(valid ? fv : 0u);
-            unsigned long long key = valid ? (((unsigned long long)fv << 32) | sl) : ~0ull;
+            orr = warp_or(orr);
             key = warp_min_u64(key);
             if (lane == 0 && i >= 0) {
                 atomicOr(&S[i].bor, orr);
@@ -1409,12 +1450,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                 break;
             int i = -1;
             for (int j = 0; j < npop; ++j)
-                if (prm.p[j].m > 32 && it >= prm.p[j].work_base &&
-                    it < prm.p[j].work_base + 2u * (uint32_t)prm.p[j].N)
+                if (PP[j].m > 32 && it >= PP[j].work_base &&
+                    it < PP[j].work_base + 2u * (uint32_t)PP[j].N)
                     i = j;
             if (i < 0)
                 continue;
-            const FusedPop &p = prm.p[i];
+            const FusedPop &p = PP[i];
             const uint32_t item = it - p.work_base, k = item >> 1;
             const int half = (int)(item & 1u);
             uint32_t *hn = hist_of(p, par ^ 1);
@@ -1433,7 +1474,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             if (bo == 0xFFFFFFFFu)
                 continue;
             const uint32_t nb = (S[i].capn >> S[i].shiftn) + 1u;
-            uint32_t *hn = hist_of(prm.p[i], par ^ 1);
+            uint32_t *hn = hist_of(PP[i], par ^ 1);
             for (uint32_t e = tid; e < nb; e += blockDim.x) {
                 const uint32_t c = bhist[bo + e];
                 if (c)
@@ -1441,7 +1482,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             }
         }
         if (tid < npop) {
-            const FusedPop &p = prm.p[tid];
+            const FusedPop &p = PP[tid];
             if (S[tid].bor)
                 atomicOr(stat_of(p) + 1 + (par ^ 1), S[tid].bor);
             if (S[tid].bbest != ~0ull)
@@ -1456,7 +1497,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
         }
         done = t + 1;
         if (prm.stop_at_zero) {
-            const FusedPop &p = prm.p[0];
+            const FusedPop &p = PP[0];
             const unsigned long long key = ldcg64(p.traj + (S[0].gen0 + (uint32_t)t) % (uint32_t)p.traj_cap);
             if ((key >> 32) == 0ull)
                 break;
@@ -1466,7 +1507,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
     if (blockIdx.x == 0 && tid == 0)
         *prm.done = done;
     if (blockIdx.x == 0 && tid < npop)
-        *prm.p[tid].gen_dev = S[tid].gen0 + (uint32_t)done;
+        *PP[tid].gen_dev = S[tid].gen0 + (uint32_t)done;
 }
 
 size_t fused_smem_bytes(const FusedParams &p)

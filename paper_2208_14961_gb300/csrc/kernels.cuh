@@ -141,7 +141,8 @@ struct FusedPop {
     unsigned long long *cw;    // probabilistic selection: in-tile weight prefixes [ntiles][32]
     int32_t dpad;              // bytes per Gram buffer (64 per tile)
     int32_t m, W, NC, NR, kind, traj_cap;
-    int32_t nch;                 // chunks per column of the warp-level Gram (warp_gram_chunks)
+    int32_t nch;                 // chunks per column of the warp-level Gram (m > 32; autotuned)
+    int32_t tpp;                 // threads per pair of the m <= 32 build, 2 or 4 (autotuned)
     int32_t shared_mut;          // mutation method 1: every offspring draws from stream index 2N
     int64_t N;
     uint32_t seed, pop_id;

@@ -70,6 +70,8 @@ SIGNATURES = {
     "ga_set_strict": (_i32, [_vp, _i32]),
     "ga_step_multi_graph": (_i32, [ctypes.POINTER(_vp), _i32, _i32, _i32]),
     "ga_set_fused_grid": (_i32, [_vp, _i32]),
+    "ga_set_fused_shape": (_i32, [_vp, _i32, _i32]),
+    "ga_set_auto_path": (_i32, [_i32, _i32, _i32, _i32]),
     "ga_set_incremental": (_i32, [_vp, _i32]),
     "ga_check_incremental": (_i32, [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
     "ga_get_incremental": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_float),
@@ -398,3 +400,13 @@ def step_multi_graph(pops, generations: int, chunk: int = 50):
 
 def set_fused_grid(pop, blocks: int):
     check(load().ga_set_fused_grid(pop.ctx, blocks))
+
+
+def set_fused_shape(pop, tpp: int = 0, nch: int = 0):
+    """Per-population launch shape of the persistent kernel (see ga_set_fused_shape)."""
+    check(load().ga_set_fused_shape(pop.ctx, tpp, nch), pop.ctx)
+
+
+def set_auto_path(storage: int, m: int, kind: int, path: int):
+    """Process-wide GA_PATH_AUTO override for (storage, m, kind)."""
+    check(load().ga_set_auto_path(storage, m, kind, path))

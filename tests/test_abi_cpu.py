@@ -177,3 +177,14 @@ def test_out_of_memory_hook_in_create_without_gpu(lib):
     assert st == hadga.GA_ENOMEM
     assert not ctx.value
     assert "allocation" in hadga.last_error()
+
+
+def test_shape_and_auto_path_setters_validate_without_gpu(lib):
+    from paper_2208_14961_gb300 import hadga
+    assert lib.ga_set_fused_shape(None, 2, 0) == hadga.GA_EINVAL
+    # a path that does not read the storage is refused; a valid one is kept and cleared
+    assert lib.ga_set_auto_path(hadga.STORE_BITS, 20, hadga.FIT_SQ, hadga.PATH_IMMA) == hadga.GA_EINVAL
+    assert lib.ga_set_auto_path(hadga.STORE_BITS, 20, hadga.FIT_SQ, 9) == hadga.GA_EINVAL
+    assert lib.ga_set_auto_path(hadga.STORE_BITS, 18, hadga.FIT_SQ, hadga.PATH_POPC) == hadga.GA_EINVAL
+    assert lib.ga_set_auto_path(hadga.STORE_BITS, 20, hadga.FIT_SQ, hadga.PATH_POPC) == hadga.GA_OK
+    assert lib.ga_set_auto_path(hadga.STORE_BITS, 20, hadga.FIT_SQ, hadga.PATH_AUTO) == hadga.GA_OK

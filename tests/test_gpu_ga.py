@@ -269,3 +269,58 @@ def test_strict_mode_reports_instead_of_falling_back():
     pop.sync()
     assert pop.generation() == 2
     pop.close()
+
+
+@pytest.mark.parametrize("m,N,tpp,nch", [(4, 5, 2, 0), (12, 250, 2, 0), (20, 501, 2, 0), (32, 300, 2, 0), (24, 97, 4, 0),
+                                         (40, 200, 0, 1), (64, 150, 0, 7), (100, 60, 0, 16), (128, 40, 0, 3)])
+def test_fused_launch_shapes_give_identical_results(m, N, tpp, nch):
+    """Every launch shape the autotuner may pick (two or four threads per
+    pair at m <= 32; any warp-Gram chunking at m > 32) computes the same
+    generations as the oracle."""
+    h = need_gpu()
+    gens = 9
+    pop = h.Population(m, N, seed=21, storage=h.STORE_BITS, traj_cap=gens, NC=2, NR=2, fitness=2)
+    h.set_fused_shape(pop, tpp, nch)
+    pop.set_strict(True)
+    pop.init_population()
+    pop.fitness()
+    pop.step(gens)
+    pop.sync()
+    gpu = pop.as_int8(), pop.fitness_host(), pop.trajectory()
+    pop.close()
+    _assert_same(gpu, _run_oracle(m, N, 21, gens, 2, 2, 2))
+
+
+def test_mixed_orders_with_tuned_shapes_in_one_launch():
+    h = need_gpu()
+    specs = [(8, 300, 2, 0), (20, 211, 4, 0), (28, 150, 2, 0), (36, 90, 0, 5), (96, 30, 0, 11)]
+    gens = 7
+    pops = []
+    for i, (m, N, tpp, nch) in enumerate(specs):
+        p = h.Population(m, N, seed=8, pop_id=i, storage=h.STORE_BITS, traj_cap=gens)
+        h.set_fused_shape(p, tpp, nch)
+        p.set_strict(True)
+        p.init_population()
+        p.fitness()
+        pops.append(p)
+    h.step_multi(pops, gens)
+    for i, ((m, N, _, _), p) in enumerate(zip(specs, pops)):
+        p.sync()
+        _assert_same((p.as_int8(), p.fitness_host(), p.trajectory()), _run_oracle(m, N, 8, gens, pop_id=i))
+        p.close()
+
+
+def test_auto_path_override_picks_the_measured_path():
+    h = need_gpu()
+    import torch
+    m, P = 32, 4096
+    pop = h.empty_population(h.STORE_INT8, m, P)
+    h.ga_init_batch(pop, h.STORE_INT8, m, P, 5)
+    ref = torch.zeros(P, dtype=torch.int32, device="cuda")
+    h.ga_fitness_batch(pop, h.STORE_INT8, m, P, h.FIT_SQ, h.PATH_INT32, ref)
+    for path in (h.PATH_POPC, h.PATH_IMMA, h.PATH_INT32):
+        h.set_auto_path(h.STORE_INT8, m, h.FIT_SQ, path)
+        got = torch.zeros(P, dtype=torch.int32, device="cuda")
+        h.ga_fitness_batch(pop, h.STORE_INT8, m, P, h.FIT_SQ, h.PATH_AUTO, got)
+        assert torch.equal(got, ref)
+    h.set_auto_path(h.STORE_INT8, m, h.FIT_SQ, h.PATH_AUTO)
