@@ -480,6 +480,35 @@ def table1_workload(args):
 MIXED_ORDERS = (12, 16, 20, 24, 28, 32, 36)
 
 
+def _mixed_rate(h, specs, stream, gens, tuned):
+    """Generations/s of the mixed-order launch as CUDA-graph replays of
+    50-generation chunks, with the tuned shapes or (tuned None) the
+    defaults (four threads per pair, the cost model's chunking, one block
+    per SM)."""
+    import torch
+
+    from paper_2208_14961_gb300 import autotune
+    pops = []
+    for i, (m, N) in enumerate(specs):
+        p = h.Population(m, N, seed=3, pop_id=i, fitness=h.FIT_SQ, storage=h.STORE_BITS, traj_cap=512,
+                         stream=stream)
+        p.init_population()
+        p.fitness()
+        pops.append(p)
+    if tuned:
+        autotune.apply_fused(pops, tuned)
+    h.step_multi_graph(pops, 50, 50)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    h.step_multi_graph(pops, gens, 50)
+    e1.record(stream)
+    e1.synchronize()
+    for p in pops:
+        p.close()
+    return gens / (e0.elapsed_time(e1) / 1e3)
+
+
 def mixed_workload(args):
     """Batched mixed orders in one persistent launch: one population per
     order m in {12, ..., 36}, P = 4(500 + U[0, 4500]) each (Philox stream
@@ -496,7 +525,10 @@ def mixed_workload(args):
 
     specs = [(m, oracle.mixed_N(3, i)) for i, m in enumerate(MIXED_ORDERS)]
     stream = torch.cuda.Stream()
-    blocks = autotune.tune_fused_grid(specs, stream=stream)
+    tuned = autotune.tune_fused(specs, stream=stream)
+    default_gps = None
+    if args.mixed_compare_default:
+        default_gps = _mixed_rate(h, specs, stream, args.mixed_gens, None)
 
     def fresh():
         pops = []
@@ -506,7 +538,7 @@ def mixed_workload(args):
             p.init_population()
             p.fitness()
             pops.append(p)
-        h.set_fused_grid(pops[0], blocks)
+        autotune.apply_fused(pops, tuned)
         return pops
 
     gens, chunk = args.mixed_gens, 50
@@ -531,9 +563,13 @@ def mixed_workload(args):
             oracle.run(ref, F, N, 1, 1, oracle.FIT_SQ, 3, i, 0, gens)
             exact = exact and bool((p.as_int8() == ref).all()) and bool((p.fitness_host() == F).all())
     line = {"workload": "mixed orders 12..36 in one persistent launch", "orders": list(MIXED_ORDERS),
-            "P": [4 * N for _, N in specs], "generations": gens, "graph_chunk": chunk, "autotuned_blocks": blocks,
+            "P": [4 * N for _, N in specs], "generations": gens, "graph_chunk": chunk,
+            "autotuned_blocks": tuned["blocks"],
+            "autotuned_shapes": {str(m): {"threads_per_pair" if m <= 32 else "warp_gram_chunks":
+                                          (t if m <= 32 else n)} for (m, _), (t, n) in zip(specs, tuned["shapes"])},
             "ms": ms, "generations_per_s": gens / (ms / 1e3),
-            "evals_per_s": gens * (total_P // 2) / (ms / 1e3), "exact_vs_oracle": exact}
+            "evals_per_s": gens * (total_P // 2) / (ms / 1e3), "exact_vs_oracle": exact,
+            "default_shapes_generations_per_s": default_gps}
     for p in pops:
         p.close()
     print(json.dumps(line), flush=True)
@@ -923,9 +959,12 @@ def m32_gram_report(hbm, popc_rate, e4m3_warp_rate, fp8_rate, gib=8.0, reps=5):
 
     import oracle
     from paper_2208_14961_gb300 import hadga as h
+    from paper_2208_14961_gb300 import autotune
     rng = np.random.default_rng(7)
     out = []
     for m in M32_GRAM_ORDERS:
+        # GA_PATH_AUTO on e4m3 storage takes the path the autotuner measured fastest here
+        tuned_e4m3 = autotune.tune_gram_path(h.STORE_E4M3, m, h.FIT_SQ)
         P = int(gib * (1 << 30)) // (m * m)
         macs, popcs = gram_algorithmic_work(m)
         idx_np = np.sort(rng.choice(P, size=256, replace=False))
@@ -950,11 +989,14 @@ def m32_gram_report(hbm, popc_rate, e4m3_warp_rate, fp8_rate, gib=8.0, reps=5):
             t_mem = nbytes / (hbm * 1e9)
             if storage == h.STORE_BITS:
                 ops, peak, unit = P * popcs, popc_rate, "popc32"
-            elif m >= 128:   # AUTO on e4m3: tcgen05
+            elif tuned_e4m3["path"] == h.PATH_FP8:   # AUTO on e4m3 resolved to tcgen05
                 ops, peak, unit = P * macs, fp8_rate, "e4m3 MAC (tcgen05)"
-            else:            # AUTO on e4m3: warp-level FP8 MMA
+            else:                                     # AUTO on e4m3 resolved to the warp-level FP8 MMA
                 ops, peak, unit = P * macs, e4m3_warp_rate, "e4m3 MAC (mma.sync)"
             row = {"path": name, "ms": sec * 1e3, "matrices_per_s": P / sec, "exact_256_sampled": exact}
+            if storage == h.STORE_E4M3:
+                row["auto_resolved_to"] = {3: "tcgen05 FP8", 6: "FP8 mma.sync"}.get(tuned_e4m3["path"],
+                                                                                 str(tuned_e4m3["path"]))
             row.update(_roof_entry(sec, t_mem, ops / peak, unit, peak, ops, nbytes, hbm))
             rows.append(row)
             del pop, fit
@@ -1101,6 +1143,8 @@ def main():
     ap.add_argument("--mixed", action="store_true", help="mixed-order multi-population workload")
     ap.add_argument("--mixed-gens", type=int, default=500)
     ap.add_argument("--mixed-check", action="store_true")
+    ap.add_argument("--mixed-compare-default", action="store_true",
+                    help="also time the mixed workload with the default launch shapes")
     ap.add_argument("--incremental", action="store_true", help="incremental Gram-delta workload (m=100)")
     ap.add_argument("--inc-gens", type=int, default=10000)
     ap.add_argument("--table3", action="store_true", help="the paper's fitness-comparison workload (Sec. 4.2)")

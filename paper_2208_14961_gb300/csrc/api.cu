@@ -573,6 +573,7 @@ static ga_status fused_run(ga_ctx *const *ctxs, int n, int32_t generations, int 
     prm.done = (int32_t *)(c0->fmisc + 1);
     prm.err = c0->err;
     fused_plan_ring(prm);
+    fused_plan_list(prm);
     const size_t smem = fused_smem_bytes(prm);
     if (smem > fused_smem_limit())
         return set_error(c0, GA_EUNSUPPORTED,

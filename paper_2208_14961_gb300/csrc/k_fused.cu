@@ -201,6 +201,7 @@ __device__ __forceinline__ uint32_t warp_max(uint32_t v)
 // mask is lt | the lowest (take - eq_before) bits of eq.
 struct Surv {
     const unsigned long long *tm, *ex;
+    const uint32_t *list;  // survivors' slots in slot order (per population from list_base), or null
 };
 
 __device__ __forceinline__ uint32_t surv_before(const Surv &sv, uint32_t tt, const PopSel &S)
@@ -215,6 +216,14 @@ __device__ __forceinline__ uint32_t surv_before(const Surv &sv, uint32_t tt, con
 __device__ __forceinline__ uint32_t survivor_of(uint32_t d, const FusedPop &p, const PopSel &S, const Surv &sv,
                                                 uint32_t *err)
 {
+    if (sv.list) {
+        // the block expanded every survivor's slot into shared memory
+        if (d >= (uint32_t)(2 * p.N)) {
+            atomicOr(err, ERR_INTERNAL);
+            return (uint32_t)(4 * p.N) - 1u;
+        }
+        return sv.list[p.list_base + d];
+    }
     const uint32_t tb = p.tile_base;
     uint32_t lo = 0, hi = p.ntiles - 1;
     while (lo < hi) {
@@ -1012,7 +1021,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
     uint4 *ring = reinterpret_cast<uint4 *>(dyn + 4u * TT) + wib * prm.inc_ring;
     uint32_t *bhist = dyn + r1;  // block-local histograms of the next generation
     uint32_t *wbuf = bhist + kHistSmem + wib * prm.warp_buf_words;
-    const Surv sv{tm, ex};
+    // survivors' slots, when the launch's shared-memory plan holds them
+    uint32_t *slist = prm.list_words ? bhist + kHistSmem + (kFusedThreads / 32) * prm.warp_buf_words : nullptr;
+    const Surv sv{tm, ex, slist};
     uint32_t *err = prm.err;
     uint32_t epoch = 0;
     uint32_t inc_parity = 0;  // phase of this warp's bulk-copy barrier
@@ -1197,8 +1208,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                 }
             }
             __syncthreads();
-            if (wib < i1 - i0) {
-                const int i = i0 + wib;
+            // the block's last warps search: at small orders the first warps
+            // are still drawing their first build item's random numbers
+            const int nwb = kFusedThreads / 32;
+            if (wib >= nwb - (i1 - i0)) {
+                const int i = i0 + (nwb - 1 - wib);
                 PopSel &s = S[i];
                 const uint32_t nb = (s.cap >> s.shift) + 1u;
                 const uint32_t need2 = (uint32_t)(2 * PP[i].N);
@@ -1380,6 +1394,26 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                 atomicOr(err, ERR_INTERNAL);
         }
         __syncthreads();
+        if (slist && !psel) {
+            // expand the survivors of every tile into the slot list (all warps
+            // of the block take part; a lookup is then one shared-memory read)
+            for (uint32_t e = tid; e < TT; e += blockDim.x) {
+                const int i = owner_of(e, npop, tile_base);
+                const FusedPop &p = PP[i];
+                const PopSel &s = S[i];
+                const unsigned long long m64 = tm[e];
+                const uint32_t eqb = min((uint32_t)ex[e] - s.eb, s.take);
+                uint32_t mask = (uint32_t)m64 | lowest_set_bits((uint32_t)(m64 >> 32), (int)(s.take - eqb));
+                uint32_t at = p.list_base + surv_before(sv, e, s);
+                const uint32_t slot0 = (e - p.tile_base) * 32u;
+                while (mask) {
+                    const int b = __ffs(mask) - 1;
+                    slist[at++] = slot0 + (uint32_t)b;
+                    mask &= mask - 1u;
+                }
+            }
+            __syncthreads();
+        }
         // m <= 32: two or four threads per pair (FusedPop::tpp)
         for (uint32_t w = gwarp; w < nwork_t; w += gwarps) {
             const uint32_t u = w * 32u;
@@ -1517,7 +1551,24 @@ size_t fused_smem_bytes(const FusedParams &p)
         inc = inc || p.p[i].gram != nullptr;
     const size_t ring_words = inc ? (size_t)(kFusedThreads / 32) * (size_t)p.inc_ring * 4u : 0u;
     const size_t r1 = std::max((size_t)4 * p.total_tiles + ring_words, (size_t)2 * kHistSmem);
-    return (r1 + kHistSmem + (size_t)(kFusedThreads / 32) * p.warp_buf_words) * 4u;
+    return (r1 + kHistSmem + (size_t)(kFusedThreads / 32) * p.warp_buf_words + (size_t)p.list_words) * 4u;
+}
+
+void fused_plan_list(FusedParams &p)
+{
+    // the survivors' slot list of truncation selection (sum of 2N words),
+    // when it fits beside the rest of the block's plan
+    p.list_words = 0;
+    if (p.psel)
+        return;
+    uint32_t words = 0;
+    for (int i = 0; i < p.npop; ++i) {
+        p.p[i].list_base = words;
+        words += (uint32_t)(2 * p.p[i].N);
+    }
+    p.list_words = words;
+    if (fused_smem_bytes(p) > fused_smem_limit())
+        p.list_words = 0;
 }
 
 size_t fused_smem_limit()
