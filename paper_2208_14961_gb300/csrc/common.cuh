@@ -612,6 +612,48 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32
 // data written by other blocks through L2 (ld.global.cg or atomics).
 constexpr unsigned long long kBarrierBudgetNs = 2000000000ull;
 
+// Split form of the grid barrier: grid_arrive after the block's writes,
+// work that needs nothing from other blocks, then grid_wait.
+__device__ __forceinline__ void grid_arrive(uint32_t *bar)
+{
+    __syncthreads();
+    // the block's writes precede this release through the bar.sync above
+    if (threadIdx.x == 0)
+        red_release_gpu_add(bar, 1u);
+}
+
+__device__ __forceinline__ bool grid_wait(uint32_t *bar, uint32_t nblocks, uint32_t &epoch, uint32_t *err,
+                                          unsigned long long budget_ns = kBarrierBudgetNs)
+{
+    __shared__ int s_ok;
+    epoch += 1u;
+    if (threadIdx.x == 0) {
+        const uint32_t target = epoch * nblocks;
+        int ok = 1;
+        const unsigned long long t0 = global_ns();
+        uint32_t spins = 0;
+        for (;;) {
+            const uint32_t v = ld_acquire_gpu(bar);
+            if ((int32_t)(v - target) >= 0)
+                break;
+            if ((++spins & 63u) == 0u) {
+                if (ld_acquire_gpu(err) != 0u) {
+                    ok = 0;
+                    break;
+                }
+                if (global_ns() - t0 > budget_ns) {
+                    atomicOr(err, ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
 __device__ __forceinline__ bool grid_barrier(uint32_t *bar, uint32_t nblocks, uint32_t &epoch, uint32_t *err,
                                              unsigned long long budget_ns = kBarrierBudgetNs)
 {

@@ -201,8 +201,12 @@ __device__ __forceinline__ uint32_t warp_max(uint32_t v)
 // mask is lt | the lowest (take - eq_before) bits of eq.
 struct Surv {
     const unsigned long long *tm, *ex;
-    const uint32_t *list;  // survivors' slots in slot order (per population from list_base), or null
+    const uint32_t *cidx;  // per population from cidx_base: tile (relative) of survivor 64 j, or null
 };
+
+// Survivors per coarse-index entry: the tile holding survivor number 64 j
+// is recorded, so a lookup searches only the tiles between two entries.
+constexpr uint32_t kCoarse = 64;
 
 __device__ __forceinline__ uint32_t surv_before(const Surv &sv, uint32_t tt, const PopSel &S)
 {
@@ -216,16 +220,14 @@ __device__ __forceinline__ uint32_t surv_before(const Surv &sv, uint32_t tt, con
 __device__ __forceinline__ uint32_t survivor_of(uint32_t d, const FusedPop &p, const PopSel &S, const Surv &sv,
                                                 uint32_t *err)
 {
-    if (sv.list) {
-        // the block expanded every survivor's slot into shared memory
-        if (d >= (uint32_t)(2 * p.N)) {
-            atomicOr(err, ERR_INTERNAL);
-            return (uint32_t)(4 * p.N) - 1u;
-        }
-        return sv.list[p.list_base + d];
-    }
     const uint32_t tb = p.tile_base;
     uint32_t lo = 0, hi = p.ntiles - 1;
+    if (sv.cidx && d < (uint32_t)(2 * p.N)) {
+        // the tiles of survivors 64 j and 64 (j + 1) bound the search
+        const uint32_t j = d / kCoarse, nj = ((uint32_t)(2 * p.N) + kCoarse - 1u) / kCoarse;
+        lo = sv.cidx[p.cidx_base + j];
+        hi = j + 1u < nj ? sv.cidx[p.cidx_base + j + 1u] : p.ntiles - 1u;
+    }
     while (lo < hi) {
         const uint32_t mid = (lo + hi + 1) >> 1;
         if (surv_before(sv, tb + mid, S) <= d)
@@ -1021,9 +1023,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
     uint4 *ring = reinterpret_cast<uint4 *>(dyn + 4u * TT) + wib * prm.inc_ring;
     uint32_t *bhist = dyn + r1;  // block-local histograms of the next generation
     uint32_t *wbuf = bhist + kHistSmem + wib * prm.warp_buf_words;
-    // survivors' slots, when the launch's shared-memory plan holds them
-    uint32_t *slist = prm.list_words ? bhist + kHistSmem + (kFusedThreads / 32) * prm.warp_buf_words : nullptr;
-    const Surv sv{tm, ex, slist};
+    // coarse survivor index (truncation selection)
+    uint32_t *cidx = prm.cidx_words ? bhist + kHistSmem + (kFusedThreads / 32) * prm.warp_buf_words : nullptr;
+    const Surv sv{tm, ex, cidx};
     uint32_t *err = prm.err;
     uint32_t epoch = 0;
     uint32_t inc_parity = 0;  // phase of this warp's bulk-copy barrier
@@ -1089,6 +1091,29 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             return;
     }
 
+    // the selection-independent draws (survivor number or parent draw, cut
+    // point, mutation) of this thread's first m <= 32 build item of
+    // generation tt of the launch
+    auto first_pre = [&](int tt) {
+        Pre r{0u, 1u, 1u, 0u, 0u, 0ull};
+        const uint32_t u = gwarp * 32u + (uint32_t)lane;
+        if (gwarp < (prm.thread_slots >> 5)) {
+            int i = -1;
+            for (int j = 0; j < npop; ++j)
+                if (PP[j].m <= 32 && u >= PP[j].work_base)
+                    i = (i < 0 || PP[j].work_base >= PP[i].work_base) ? j : i;
+            if (i >= 0) {
+                const FusedPop &p = PP[i];
+                const uint32_t local = u - p.work_base;
+                const uint32_t k = p.tpp == 2 ? local >> 1 : local >> 2;
+                const int half = (int)(p.tpp == 2 ? (local & 1u) : ((local >> 1) & 1u));
+                if (k < (uint32_t)p.N)
+                    r = make_pre(p, S[i].gen0 + 1u + (uint32_t)tt, (uint32_t)tt, k, half, psel);
+            }
+        }
+        return r;
+    };
+    Pre pre_next{0u, 1u, 1u, 0u, 0u, 0ull};
     uint32_t ref_level = 0;
     for (int t = 0; t < prm.ngen; ++t) {
         const int par = t & 1;
@@ -1134,24 +1159,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             const uint32_t q = (gwarp - p.tile_base) * 32u + lane;
             f_pre = q < (uint32_t)(4 * p.N) ? ldcg32(p.fit[src] + q) : 0u;
         }
-        // selection-independent draws of this warp's first build item
-        Pre pre0{0u, 1u, 1u, 0u, 0u, 0ull};
+        // selection-independent draws of this warp's first build item: drawn
+        // while the previous generation's closing barrier completed, except in
+        // the launch's first generation
         const uint32_t nwork_t = prm.thread_slots >> 5;
-        if (gwarp < nwork_t) {
-            const uint32_t u = gwarp * 32u + (uint32_t)lane;
-            int i = -1;
-            for (int j = 0; j < npop; ++j)
-                if (PP[j].m <= 32 && u >= PP[j].work_base)
-                    i = (i < 0 || PP[j].work_base >= PP[i].work_base) ? j : i;
-            if (i >= 0) {
-                const FusedPop &p = PP[i];
-                const uint32_t local = u - p.work_base;
-                const uint32_t k = p.tpp == 2 ? local >> 1 : local >> 2;
-                const int half = (int)(p.tpp == 2 ? (local & 1u) : ((local >> 1) & 1u));
-                if (k < (uint32_t)p.N)
-                    pre0 = make_pre(p, S[i].gen0 + 1u + (uint32_t)t, (uint32_t)t, k, half, psel);
-            }
-        }
+        const Pre pre0 = t == 0 ? first_pre(0) : pre_next;
         for (int i = 0; i < npop && !psel; ++i) {
             uint32_t *hn = hist_of(PP[i], par ^ 1);
             for (uint32_t e = gtid; e < (uint32_t)kHistR; e += gthreads)
@@ -1208,11 +1220,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                 }
             }
             __syncthreads();
-            // the block's last warps search: at small orders the first warps
-            // are still drawing their first build item's random numbers
-            const int nwb = kFusedThreads / 32;
-            if (wib >= nwb - (i1 - i0)) {
-                const int i = i0 + (nwb - 1 - wib);
+            if (wib < i1 - i0) {
+                const int i = i0 + wib;
                 PopSel &s = S[i];
                 const uint32_t nb = (s.cap >> s.shift) + 1u;
                 const uint32_t need2 = (uint32_t)(2 * PP[i].N);
@@ -1394,23 +1403,19 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                 atomicOr(err, ERR_INTERNAL);
         }
         __syncthreads();
-        if (slist && !psel) {
-            // expand the survivors of every tile into the slot list (all warps
-            // of the block take part; a lookup is then one shared-memory read)
+        if (cidx && !psel) {
+            // coarse index: a tile holds at most 32 < kCoarse survivors, so at
+            // most one multiple of kCoarse falls among its survivor numbers
             for (uint32_t e = tid; e < TT; e += blockDim.x) {
                 const int i = owner_of(e, npop, tile_base);
                 const FusedPop &p = PP[i];
                 const PopSel &s = S[i];
-                const unsigned long long m64 = tm[e];
-                const uint32_t eqb = min((uint32_t)ex[e] - s.eb, s.take);
-                uint32_t mask = (uint32_t)m64 | lowest_set_bits((uint32_t)(m64 >> 32), (int)(s.take - eqb));
-                uint32_t at = p.list_base + surv_before(sv, e, s);
-                const uint32_t slot0 = (e - p.tile_base) * 32u;
-                while (mask) {
-                    const int b = __ffs(mask) - 1;
-                    slist[at++] = slot0 + (uint32_t)b;
-                    mask &= mask - 1u;
-                }
+                const uint32_t n2 = (uint32_t)(2 * p.N);
+                const uint32_t b = surv_before(sv, e, s);
+                const uint32_t end = e + 1u == p.tile_base + p.ntiles ? n2 : surv_before(sv, e + 1u, s);
+                const uint32_t j = (b + kCoarse - 1u) / kCoarse;
+                if (end > b && j * kCoarse < end)
+                    cidx[p.cidx_base + j] = e - p.tile_base;
             }
             __syncthreads();
         }
@@ -1522,7 +1527,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             if (S[tid].bbest != ~0ull)
                 atomicMin(p.traj + (S[tid].gen0 + (uint32_t)t) % (uint32_t)p.traj_cap, S[tid].bbest);
         }
-        if (!grid_barrier(prm.bar, nblocks, epoch, err))
+        // split barrier: the next generation's first draws overlap its latency
+        grid_arrive(prm.bar);
+        if (t + 1 < prm.ngen)
+            pre_next = first_pre(t + 1);
+        if (!grid_wait(prm.bar, nblocks, epoch, err))
             return;
         src ^= 1;
         if (tid < npop) {
@@ -1551,24 +1560,17 @@ size_t fused_smem_bytes(const FusedParams &p)
         inc = inc || p.p[i].gram != nullptr;
     const size_t ring_words = inc ? (size_t)(kFusedThreads / 32) * (size_t)p.inc_ring * 4u : 0u;
     const size_t r1 = std::max((size_t)4 * p.total_tiles + ring_words, (size_t)2 * kHistSmem);
-    return (r1 + kHistSmem + (size_t)(kFusedThreads / 32) * p.warp_buf_words + (size_t)p.list_words) * 4u;
+    return (r1 + kHistSmem + (size_t)(kFusedThreads / 32) * p.warp_buf_words + (size_t)p.cidx_words) * 4u;
 }
 
-void fused_plan_list(FusedParams &p)
+void fused_plan_cidx(FusedParams &p)
 {
-    // the survivors' slot list of truncation selection (sum of 2N words),
-    // when it fits beside the rest of the block's plan
-    p.list_words = 0;
-    if (p.psel)
-        return;
     uint32_t words = 0;
     for (int i = 0; i < p.npop; ++i) {
-        p.p[i].list_base = words;
-        words += (uint32_t)(2 * p.p[i].N);
+        p.p[i].cidx_base = words;
+        words += (uint32_t)((2 * p.p[i].N + kCoarse - 1) / kCoarse);
     }
-    p.list_words = words;
-    if (fused_smem_bytes(p) > fused_smem_limit())
-        p.list_words = 0;
+    p.cidx_words = p.psel ? 0u : words;
 }
 
 size_t fused_smem_limit()
