@@ -254,8 +254,6 @@ ga_status ga_create(const ga_config *cfg, void *pop_dev, uint32_t *fit_dev, void
         fp.total_tiles = (uint32_t)tiles;
         fp.warp_buf_words = c->m > 32 ? ((2 * c->m * c->W + col_set_words(c->m, c->W) + 3) & ~3) : 0;
         fp.p[0].N = c->N;
-        fp.psel = cfg->selection == GA_SEL_PROBABILISTIC;
-        fused_plan_cidx(fp);
         const size_t need = fused_smem_bytes(fp), have = fused_smem_limit();
         if (need > have) {
             fused_fit = false;
@@ -575,7 +573,6 @@ static ga_status fused_run(ga_ctx *const *ctxs, int n, int32_t generations, int 
     prm.bar = c0->fmisc;
     prm.done = (int32_t *)(c0->fmisc + 1);
     prm.err = c0->err;
-    fused_plan_cidx(prm);
     fused_plan_ring(prm);
     const size_t smem = fused_smem_bytes(prm);
     if (smem > fused_smem_limit())

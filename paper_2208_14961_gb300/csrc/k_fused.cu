@@ -38,7 +38,8 @@ namespace {
 constexpr uint32_t FULL = 0xFFFFFFFFu;
 
 struct PopSel {
-    uint32_t cap, shift;  // histogram of the current generation: f >> shift for f <= cap
+    uint32_t cap, shift;  // histogram of the current generation: bucket hkey(f) for f <= cap
+    uint32_t hlo, hlon;   // window base of the current / next generation's histogram (0: no window)
     uint32_t v;           // every current F is a multiple of 2^v
     uint32_t lo, need;    // candidate bucket [lo, lo + 2^sr) and survivors still to take there
     uint32_t sr;          // width exponent of the candidate bucket
@@ -62,6 +63,38 @@ __device__ __forceinline__ uint32_t shift_for(uint32_t cap)
 {
     const int bl = 32 - __clz(cap);
     return bl > 12 ? (uint32_t)(bl - 12) : 0u;
+}
+
+// Histogram bucket of fitness f (f <= cap) with window base lo and bucket
+// width 2^sh: values below the window share bucket 0.
+__device__ __forceinline__ uint32_t hkey(uint32_t f, uint32_t lo, uint32_t sh)
+{
+    return f >= lo ? (f - lo) >> sh : 0u;
+}
+
+// Buckets of a histogram up to cap.
+__device__ __forceinline__ uint32_t hbuckets(uint32_t cap, uint32_t lo, uint32_t sh)
+{
+    return ((cap - lo) >> sh) + 1u;
+}
+
+// Histogram parameters of the next generation from its cap T (the current
+// threshold, a multiple of 2^v): buckets of width max(v, shift_for(T))
+// from 0 when that width is exact (<= 2^v); otherwise exact buckets of
+// width 2^v over the kHistR - 1 values just below T, everything lower in
+// bucket 0 (the next threshold usually moves less than the window; when it
+// falls below it, the refinement passes find it).
+__device__ __forceinline__ void next_hist(uint32_t T, uint32_t v, uint32_t &lo, uint32_t &sh)
+{
+    sh = max(v, shift_for(T));
+    lo = 0u;
+    if (sh > v && v < 20u) {
+        const uint32_t span = (uint32_t)(kHistR - 1) << v;
+        lo = T > span ? T - span : 0u;
+        sh = v;
+        if (lo == 0u)
+            sh = max(v, shift_for(T));
+    }
 }
 
 __device__ __forceinline__ uint32_t ctz_or(uint32_t orv) { return orv ? (uint32_t)(__ffs(orv) - 1) : 31u; }
@@ -201,12 +234,7 @@ __device__ __forceinline__ uint32_t warp_max(uint32_t v)
 // mask is lt | the lowest (take - eq_before) bits of eq.
 struct Surv {
     const unsigned long long *tm, *ex;
-    const uint32_t *cidx;  // per population from cidx_base: tile (relative) of survivor 64 j, or null
 };
-
-// Survivors per coarse-index entry: the tile holding survivor number 64 j
-// is recorded, so a lookup searches only the tiles between two entries.
-constexpr uint32_t kCoarse = 64;
 
 __device__ __forceinline__ uint32_t surv_before(const Surv &sv, uint32_t tt, const PopSel &S)
 {
@@ -222,12 +250,6 @@ __device__ __forceinline__ uint32_t survivor_of(uint32_t d, const FusedPop &p, c
 {
     const uint32_t tb = p.tile_base;
     uint32_t lo = 0, hi = p.ntiles - 1;
-    if (sv.cidx && d < (uint32_t)(2 * p.N)) {
-        // the tiles of survivors 64 j and 64 (j + 1) bound the search
-        const uint32_t j = d / kCoarse, nj = ((uint32_t)(2 * p.N) + kCoarse - 1u) / kCoarse;
-        lo = sv.cidx[p.cidx_base + j];
-        hi = j + 1u < nj ? sv.cidx[p.cidx_base + j + 1u] : p.ntiles - 1u;
-    }
     while (lo < hi) {
         const uint32_t mid = (lo + hi + 1) >> 1;
         if (surv_before(sv, tb + mid, S) <= d)
@@ -912,7 +934,7 @@ __device__ void offspring_warp(const FusedPop &p, PopSel &S, int src, uint32_t g
         uint32_t orr = 0;
         for (int i = 0; i < 2; ++i) {
             if (!S.psel && fv[i] <= S.capn)
-                atomicAdd((S.boff != 0xFFFFFFFFu ? bhist + S.boff : hist_next) + (fv[i] >> S.shiftn), 1u);
+                atomicAdd((S.boff != 0xFFFFFFFFu ? bhist + S.boff : hist_next) + hkey(fv[i], S.hlon, S.shiftn), 1u);
             orr |= fv[i];
             const unsigned long long key = ((unsigned long long)fv[i] << 32) | slots[i];
             bk = key < bk ? key : bk;
@@ -1023,9 +1045,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
     uint4 *ring = reinterpret_cast<uint4 *>(dyn + 4u * TT) + wib * prm.inc_ring;
     uint32_t *bhist = dyn + r1;  // block-local histograms of the next generation
     uint32_t *wbuf = bhist + kHistSmem + wib * prm.warp_buf_words;
-    // coarse survivor index (truncation selection)
-    uint32_t *cidx = prm.cidx_words ? bhist + kHistSmem + (kFusedThreads / 32) * prm.warp_buf_words : nullptr;
-    const Surv sv{tm, ex, cidx};
+    const Surv sv{tm, ex};
     uint32_t *err = prm.err;
     uint32_t epoch = 0;
     uint32_t inc_parity = 0;  // phase of this warp's bulk-copy barrier
@@ -1044,6 +1064,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
         S[tid].gen0 = ldcg32(PP[tid].gen_dev);
         S[tid].psel = psel ? 1u : 0u;
         S[tid].boff = 0xFFFFFFFFu;
+        S[tid].hlo = 0u;  // the launch's first histogram covers [0, max F] from bucket 0
     }
     __syncthreads();
     if (!psel) {
@@ -1127,7 +1148,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
         int g1 = 0;
         uint32_t goff = 0;
         while (!psel && g1 < npop) {
-            const uint32_t nb = (S[g1].cap >> S[g1].shift) + 1u;
+            const uint32_t nb = hbuckets(S[g1].cap, S[g1].hlo, S[g1].shift);
             if (g1 > 0 && goff + nb > kHistSmem)
                 break;
             goff += nb;
@@ -1141,11 +1162,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             hv[r] = 0u;
             if (e < goff) {
                 int i = 0;
-                uint32_t base = 0, nb = (S[0].cap >> S[0].shift) + 1u;
+                uint32_t base = 0, nb = hbuckets(S[0].cap, S[0].hlo, S[0].shift);
                 while (i + 1 < g1 && e >= base + nb) {
                     base += nb;
                     ++i;
-                    nb = (S[i].cap >> S[i].shift) + 1u;
+                    nb = hbuckets(S[i].cap, S[i].hlo, S[i].shift);
                 }
                 hv[r] = ldcg32(hist_of(PP[i], par) + (e - base));
             }
@@ -1183,7 +1204,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             uint32_t off = 0;
             int i1 = i0;
             while (i1 < npop) {
-                const uint32_t nb = (S[i1].cap >> S[i1].shift) + 1u;
+                const uint32_t nb = hbuckets(S[i1].cap, S[i1].hlo, S[i1].shift);
                 if (i1 > i0 && off + nb > kHistSmem)
                     break;
                 if (tid == 0)
@@ -1223,13 +1244,13 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             if (wib < i1 - i0) {
                 const int i = i0 + wib;
                 PopSel &s = S[i];
-                const uint32_t nb = (s.cap >> s.shift) + 1u;
+                const uint32_t nb = hbuckets(s.cap, s.hlo, s.shift);
                 const uint32_t need2 = (uint32_t)(2 * PP[i].N);
                 uint32_t b = 0, before = 0;
                 const bool found = warp_find_crossing_smem(hcnt + hoff[i], nb, need2, b, before);
                 if (lane == 0) {
                     if (found) {
-                        s.lo = b << s.shift;
+                        s.lo = s.hlo + (b << s.shift);
                         s.need = need2 - before;
                     } else {
                         atomicOr(err, ERR_INTERNAL);
@@ -1238,11 +1259,17 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                     }
                     s.sr = s.shift;
                     s.exact = s.shift <= s.v ? 1u : 0u;
+                    if (found && b == 0u && s.hlo != 0u) {
+                        // the threshold lies below the window: bucket 0 holds [0, hlo + 2^shift)
+                        s.lo = 0u;
+                        s.sr = 32u - (uint32_t)__clz(s.hlo + (1u << s.shift) - 1u);
+                        s.exact = 0u;
+                    }
                     if (s.exact) {
                         s.T = s.lo;
                         s.take = s.need;
                         s.capn = s.T;
-                        s.shiftn = max(s.v, shift_for(s.T));
+                        next_hist(s.T, s.v, s.hlon, s.shiftn);
                         s.bor = 0u;
                         s.bbest = ~0ull;
                     } else {
@@ -1308,7 +1335,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                 s.T = s.lo;
                 s.take = s.need;
                 s.capn = s.T;
-                s.shiftn = max(s.v, shift_for(s.T));
+                next_hist(s.T, s.v, s.hlon, s.shiftn);
                 s.bor = 0u;
                 s.bbest = ~0ull;
             }
@@ -1338,7 +1365,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
         if (tid == 0 && !psel) {
             uint32_t off = 0;
             for (int i = 0; i < npop; ++i) {
-                const uint32_t nb = (S[i].capn >> S[i].shiftn) + 1u;
+                const uint32_t nb = hbuckets(S[i].capn, S[i].hlon, S[i].shiftn);
                 S[i].boff = off + nb <= kHistSmem ? off : 0xFFFFFFFFu;
                 if (off + nb <= kHistSmem)
                     off += nb;
@@ -1403,22 +1430,6 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                 atomicOr(err, ERR_INTERNAL);
         }
         __syncthreads();
-        if (cidx && !psel) {
-            // coarse index: a tile holds at most 32 < kCoarse survivors, so at
-            // most one multiple of kCoarse falls among its survivor numbers
-            for (uint32_t e = tid; e < TT; e += blockDim.x) {
-                const int i = owner_of(e, npop, tile_base);
-                const FusedPop &p = PP[i];
-                const PopSel &s = S[i];
-                const uint32_t n2 = (uint32_t)(2 * p.N);
-                const uint32_t b = surv_before(sv, e, s);
-                const uint32_t end = e + 1u == p.tile_base + p.ntiles ? n2 : surv_before(sv, e + 1u, s);
-                const uint32_t j = (b + kCoarse - 1u) / kCoarse;
-                if (end > b && j * kCoarse < end)
-                    cidx[p.cidx_base + j] = e - p.tile_base;
-            }
-            __syncthreads();
-        }
         // m <= 32: two or four threads per pair (FusedPop::tpp)
         for (uint32_t w = gwarp; w < nwork_t; w += gwarps) {
             const uint32_t u = w * 32u;
@@ -1459,9 +1470,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                     // no histogram: the next selection weighs every individual
                 } else if (s.boff != 0xFFFFFFFFu) {
                     if (valid && fv[e] <= s.capn)
-                        atomicAdd(bhist + s.boff + (fv[e] >> s.shiftn), 1u);
+                        atomicAdd(bhist + s.boff + hkey(fv[e], s.hlon, s.shiftn), 1u);
                 } else {
-                    warp_hist_add(hist_of(p, par ^ 1), valid && fv[e] <= s.capn, fv[e] >> s.shiftn);
+                    warp_hist_add(hist_of(p, par ^ 1), valid && fv[e] <= s.capn, hkey(fv[e], s.hlon, s.shiftn));
                 }
                 orr |= valid ? fv[e] : 0u;
                 const unsigned long long ke = valid ? (((unsigned long long)fv[e] << 32) | sl[e]) : ~0ull;
@@ -1512,7 +1523,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             const uint32_t bo = S[i].boff;
             if (bo == 0xFFFFFFFFu)
                 continue;
-            const uint32_t nb = (S[i].capn >> S[i].shiftn) + 1u;
+            const uint32_t nb = hbuckets(S[i].capn, S[i].hlon, S[i].shiftn);
             uint32_t *hn = hist_of(PP[i], par ^ 1);
             for (uint32_t e = tid; e < nb; e += blockDim.x) {
                 const uint32_t c = bhist[bo + e];
@@ -1537,6 +1548,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
         if (tid < npop) {
             S[tid].cap = S[tid].capn;
             S[tid].shift = S[tid].shiftn;
+            S[tid].hlo = S[tid].hlon;
         }
         done = t + 1;
         if (prm.stop_at_zero) {
@@ -1560,17 +1572,7 @@ size_t fused_smem_bytes(const FusedParams &p)
         inc = inc || p.p[i].gram != nullptr;
     const size_t ring_words = inc ? (size_t)(kFusedThreads / 32) * (size_t)p.inc_ring * 4u : 0u;
     const size_t r1 = std::max((size_t)4 * p.total_tiles + ring_words, (size_t)2 * kHistSmem);
-    return (r1 + kHistSmem + (size_t)(kFusedThreads / 32) * p.warp_buf_words + (size_t)p.cidx_words) * 4u;
-}
-
-void fused_plan_cidx(FusedParams &p)
-{
-    uint32_t words = 0;
-    for (int i = 0; i < p.npop; ++i) {
-        p.p[i].cidx_base = words;
-        words += (uint32_t)((2 * p.p[i].N + kCoarse - 1) / kCoarse);
-    }
-    p.cidx_words = p.psel ? 0u : words;
+    return (r1 + kHistSmem + (size_t)(kFusedThreads / 32) * p.warp_buf_words) * 4u;
 }
 
 size_t fused_smem_limit()

@@ -147,7 +147,6 @@ struct FusedPop {
     int64_t N;
     uint32_t seed, pop_id;
     uint32_t tile_base, ntiles;  // tiles of 32 slots in the joint tile space
-    uint32_t cidx_base;          // first word of this population's coarse survivor index
     uint32_t work_base;          // m <= 32: first thread slot; m > 32: first pair
 };
 
@@ -163,7 +162,6 @@ struct FusedParams {
     int32_t warp_buf_words;  // shared words per warp for m > 32 populations
     int32_t inc_ring;        // 16-byte slots per warp of the incremental copy ring (0: no incremental population)
     int32_t psel;            // probabilistic selection (every population), else truncation
-    uint32_t cidx_words;     // shared words of the coarse survivor index (fused_plan_cidx)
     uint32_t *bar;           // grid-barrier counter (zeroed before the launch)
     uint32_t *err;           // device error word
     int32_t *done;           // generations completed
@@ -173,10 +171,6 @@ size_t fused_smem_bytes(const FusedParams &p);
 // Dynamic shared memory a block of the persistent kernel may take on the
 // current device (opt-in maximum less the kernel's static shared memory).
 size_t fused_smem_limit();
-// Sets every population's cidx_base and p.cidx_words: the coarse survivor
-// index of truncation selection (one word per 64 survivors).  Call before
-// fused_plan_ring, which fits the copy ring into what is left.
-void fused_plan_cidx(FusedParams &p);
 // Sets p.inc_ring: the largest copy ring (up to one offspring's phase-1
 // copies) that keeps the block's shared memory within the device limit.
 void fused_plan_ring(FusedParams &p);

@@ -324,3 +324,35 @@ def test_auto_path_override_picks_the_measured_path():
         h.ga_fitness_batch(pop, h.STORE_INT8, m, P, h.FIT_SQ, h.PATH_AUTO, got)
         assert torch.equal(got, ref)
     h.set_auto_path(h.STORE_INT8, m, h.FIT_SQ, h.PATH_AUTO)
+
+
+@pytest.mark.parametrize("m,N,gens", [(64, 64, 6), (100, 40, 4)])
+def test_threshold_below_the_histogram_window(m, N, gens):
+    """2N - 1 planted Sylvester matrices (F = 0) and random others: the first
+    generation's threshold is a random matrix's F, the next one falls to
+    the planted copies' offspring, far below the window of exact buckets
+    kept under the previous threshold, so the search must take bucket 0 and
+    refine from 0.  Bit-exact with the oracle."""
+    h = need_gpu()
+    from hadamard_fixtures import sylvester
+    H = sylvester(64) if m == 64 else None
+    pop = h.Population(m, N, seed=17, storage=h.STORE_BITS, traj_cap=gens)
+    pop.set_strict(True)
+    pop.init_population()
+    host = pop.as_int8()
+    if H is not None:
+        host[:2 * N - 1] = H
+    else:
+        # m = 100 has no Sylvester matrix: plant copies of the population's best instead
+        F0 = oracle.fitness(host, oracle.FIT_SQ)
+        host[:2 * N - 1] = host[int(np.argmin(F0))]
+    pop.load_int8(host)
+    pop.fitness()
+    pop.step(gens)
+    pop.sync()
+    gpu = pop.as_int8(), pop.fitness_host(), pop.trajectory()
+    pop.close()
+    ref = host.copy()
+    F = oracle.fitness(ref, oracle.FIT_SQ)
+    _, tf, ts = oracle.run(ref, F, N, 1, 1, oracle.FIT_SQ, 17, 0, 0, gens)
+    _assert_same(gpu, (ref, F, tf, ts))
