@@ -13,8 +13,11 @@ differs.
   the populations' tuned shapes applied.
 * Gram path per (storage, m, fitness kind) for GA_PATH_AUTO
   (`tune_gram_path`): every exact path the library accepts is timed on a
-  population of about a quarter GiB (int8 size) and the fastest is set as
-  the process-wide AUTO choice (ga_set_auto_path).
+  population of about 2 GiB (int8 size; well beyond the L2, where the
+  paths' HBM and tail behaviour match large workloads: a quarter GiB picked
+  the tcgen05 path at m = 64, which is slower than the warp-level FP8 MMA at
+  8 GiB) and the fastest is set as the process-wide AUTO choice
+  (ga_set_auto_path).
 """
 from __future__ import annotations
 
@@ -169,7 +172,7 @@ def tune_fused_grid(specs, generations: int = 32, stream=None, use_cache: bool =
 GRAM_PATHS = (h.PATH_INT32, h.PATH_IMMA, h.PATH_POPC, h.PATH_FP8, h.PATH_BF16, h.PATH_FP8_WARP)
 
 
-def tune_gram_path(storage: int, m: int, kind: int, gib: float = 0.25, reps: int = 3, use_cache: bool = True,
+def tune_gram_path(storage: int, m: int, kind: int, gib: float = 2.0, reps: int = 3, use_cache: bool = True,
                    apply: bool = True) -> dict:
     """Fastest exact Gram path for (storage, m, kind) on this GPU; applied as
     the process-wide GA_PATH_AUTO choice unless apply is False."""
