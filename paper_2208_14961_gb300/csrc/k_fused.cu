@@ -1435,37 +1435,57 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                         v[r] = ld_tile_masks(mask_at(tt));
                 }
             }
+            if (psel) {
+#pragma unroll
+                for (int r = 0; r < kMaskBatch; ++r) {
+                    const uint32_t tt = t0 + (uint32_t)r * blockDim.x;
+                    if (tt < TT)
+                        tm[tt] = v[r].x;  // the tile's weight
+                }
+                continue;
+            }
+            // bounded wait for this generation's entries (already there after a
+            // grid barrier): every pending entry is reloaded in the same round,
+            // so the wait is the latest entry plus one round trip
+            uint32_t pending = 0;
 #pragma unroll
             for (int r = 0; r < kMaskBatch; ++r) {
                 const uint32_t tt = t0 + (uint32_t)r * blockDim.x;
-                if (tt >= TT)
-                    continue;
-                if (psel) {
-                    tm[tt] = v[r].x;  // the tile's weight
-                    continue;
-                }
-                // bounded wait for this generation's entry (it is already there
-                // after a grid barrier)
-                unsigned long long since = 0ull;
-                uint32_t spins = 0;
-                while (masks_ok && ((uint32_t)(v[r].x >> 32) != MASK_TAG || (uint32_t)(v[r].y >> 32) != MASK_TAG)) {
-                    if ((++spins & 63u) == 0u) {
-                        if (ld_acquire_gpu(err) != 0u) {
-                            masks_ok = 0;
-                            break;
-                        }
-                        const unsigned long long now = global_ns();
-                        if (since == 0ull)
-                            since = now;
-                        else if (now - since > kBarrierBudgetNs) {
-                            atomicOr(err, ERR_TIMEOUT);
-                            masks_ok = 0;
-                            break;
-                        }
+                if (tt < TT && ((uint32_t)(v[r].x >> 32) != MASK_TAG || (uint32_t)(v[r].y >> 32) != MASK_TAG))
+                    pending |= 1u << r;
+            }
+            unsigned long long since = 0ull;
+            uint32_t spins = 0;
+            while (pending && masks_ok) {
+                if ((++spins & 15u) == 0u) {
+                    if (ld_acquire_gpu(err) != 0u) {
+                        masks_ok = 0;
+                        break;
                     }
-                    v[r] = ld_tile_masks(mask_at(tt));
+                    const unsigned long long now = global_ns();
+                    if (since == 0ull)
+                        since = now;
+                    else if (now - since > kBarrierBudgetNs) {
+                        atomicOr(err, ERR_TIMEOUT);
+                        masks_ok = 0;
+                        break;
+                    }
                 }
-                tm[tt] = (v[r].x & 0xFFFFFFFFull) | (v[r].y << 32);
+#pragma unroll
+                for (int r = 0; r < kMaskBatch; ++r)
+                    if (pending & (1u << r))
+                        v[r] = ld_tile_masks(mask_at(t0 + (uint32_t)r * blockDim.x));
+#pragma unroll
+                for (int r = 0; r < kMaskBatch; ++r)
+                    if ((pending & (1u << r)) && (uint32_t)(v[r].x >> 32) == MASK_TAG &&
+                        (uint32_t)(v[r].y >> 32) == MASK_TAG)
+                        pending &= ~(1u << r);
+            }
+#pragma unroll
+            for (int r = 0; r < kMaskBatch; ++r) {
+                const uint32_t tt = t0 + (uint32_t)r * blockDim.x;
+                if (tt < TT)
+                    tm[tt] = (v[r].x & 0xFFFFFFFFull) | (v[r].y << 32);
             }
         }
         for (uint32_t e = tid; e < kHistSmem; e += blockDim.x)
