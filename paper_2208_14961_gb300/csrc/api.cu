@@ -300,7 +300,7 @@ ga_status ga_create(const ga_config *cfg, void *pop_dev, uint32_t *fit_dev, void
         parts.push_back({(void **)&c->ffit, (size_t)P * 4u});
         parts.push_back({(void **)&c->fstate, kFusedStateWords * 4u});
         parts.push_back({(void **)&c->fmisc, 64u * 4u});
-        parts.push_back({(void **)&c->ftmask, (size_t)tiles * 16u});
+        parts.push_back({(void **)&c->ftmask, (size_t)tiles * 8u});
         parts.push_back({(void **)&c->fperm, (size_t)kChunk * n_keep * 4u});
         if ((uint64_t)n_keep > kPermSmemMax)
             parts.push_back({(void **)&c->fperm_keys, (size_t)kChunk * n_keep * 8u});
@@ -495,13 +495,6 @@ static ga_status fused_run(ga_ctx *const *ctxs, int n, int32_t generations, int 
     memset(&prm, 0, sizeof(prm));
     prm.npop = n;
     prm.psel = c0->cfg.selection == GA_SEL_PROBABILISTIC ? 1 : 0;
-    // one grid barrier per generation: truncation selection (tagged tile
-    // masks) and trajectory rings of at least two entries (a generation's best
-    // key is cleared one generation ahead)
-    prm.one_barrier = prm.psel ? 0 : 1;
-    for (int i = 0; i < n; ++i)
-        if (ctxs[i]->cfg.traj_cap < 2)
-            prm.one_barrier = 0;
     for (int i = 1; i < n; ++i)
         if (ctxs[i]->cfg.selection != c0->cfg.selection)
             return set_error(c0, GA_EUNSUPPORTED, "one persistent launch runs one selection method");
@@ -616,9 +609,6 @@ static ga_status fused_run(ga_ctx *const *ctxs, int n, int32_t generations, int 
             }
             if (e == cudaSuccess)
                 e = cudaMemsetAsync(c->fstate, 0, kFusedStateWords * 4u, c0->stream);
-            // tile masks carry the launch's generation index from 1: none is current before it runs
-            if (e == cudaSuccess)
-                e = cudaMemsetAsync(c->ftmask, 0, (size_t)((c->P + 31) / 32) * 16u, c0->stream);
             if (e != cudaSuccess)
                 return cuda_check(c0, e, "survivor orders");
         }

@@ -99,31 +99,9 @@ __device__ __forceinline__ void next_hist(uint32_t T, uint32_t v, uint32_t &lo, 
 
 __device__ __forceinline__ uint32_t ctz_or(uint32_t orv) { return orv ? (uint32_t)(__ffs(orv) - 1) : 31u; }
 
-// Selection histograms rotate over three buffers: generation t of a launch
-// reads buffer t mod 3 (filled by the previous build), fills (t + 1) mod 3
-// and clears (t + 2) mod 3 for the generation after, so that no reset needs
-// a grid barrier between it and the atomic adds it must precede.  The OR
-// words of the fitness values rotate the same way (stat 1..3).
-__device__ __forceinline__ uint32_t *hist_of(const FusedPop &p, int h) { return p.state + h * kHistR; }
-__device__ __forceinline__ uint32_t *ref_of(const FusedPop &p, int level) { return p.state + (3 + level) * kHistR; }
-__device__ __forceinline__ uint32_t *stat_of(const FusedPop &p) { return p.state + 6 * kHistR; }
-
-// Tile masks carry the generation they belong to: per tile two 8-byte words
-// (tag << 32 | F < T mask) and (tag << 32 | F == T mask), stored and loaded
-// as single-copy-atomic relaxed gpu-scope accesses, so a reader recognises
-// a current entry without a grid barrier between writer and reader.
-__device__ __forceinline__ void st_tile_masks(unsigned long long *p, uint32_t tag, uint32_t lt, uint32_t eq)
-{
-    const unsigned long long a = ((unsigned long long)tag << 32) | lt, b = ((unsigned long long)tag << 32) | eq;
-    asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
-}
-
-__device__ __forceinline__ ulonglong2 ld_tile_masks(const unsigned long long *p)
-{
-    ulonglong2 v;
-    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "l"(p) : "memory");
-    return v;
-}
+__device__ __forceinline__ uint32_t *hist_of(const FusedPop &p, int parity) { return p.state + parity * kHistR; }
+__device__ __forceinline__ uint32_t *ref_of(const FusedPop &p, int level) { return p.state + (2 + level) * kHistR; }
+__device__ __forceinline__ uint32_t *stat_of(const FusedPop &p) { return p.state + 5 * kHistR; }
 
 // Whole warp: bucket b in [0, nb) of h where the running count first reaches
 // `need` (1 <= need <= total), and the count before it.
@@ -1087,11 +1065,6 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
         S[tid].psel = psel ? 1u : 0u;
         S[tid].boff = 0xFFFFFFFFu;
         S[tid].hlo = 0u;  // the launch's first histogram covers [0, max F] from bucket 0
-        // the first generation's best key starts empty (later ones are cleared a
-        // generation ahead); the kernel's first grid barrier orders this before
-        // every block's atomicMin
-        if (blockIdx.x == 0 && prm.one_barrier)
-            PP[tid].traj[S[tid].gen0 % (uint32_t)PP[tid].traj_cap] = ~0ull;
     }
     __syncthreads();
     if (!psel) {
@@ -1164,20 +1137,14 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
     Pre pre_next{0u, 1u, 1u, 0u, 0u, 0ull};
     uint32_t ref_level = 0;
     for (int t = 0; t < prm.ngen; ++t) {
-        // histogram / OR-word buffers: read this generation's, fill the next
-        // one's, clear the one after (see hist_of)
-        // (computed where used, from t: nothing extra stays live through the build)
-#define HCUR (t % 3)
-#define HNXT ((t + 1) % 3)
-#define HCLR ((t + 2) % 3)
-#define MASK_TAG ((uint32_t)t + 1u)  // tile masks of generation t (the buffer is zeroed per launch)
+        const int par = t & 1;
 
         // ---- phase A: threshold of the 2N smallest ---------------------------------
         // loads first: the OR word of the current fitness values and the
         // first group's histogram buckets (populations [0, g1) whose buckets
         // fit the staging area), held in registers while the
         // selection-independent draws are computed
-        const uint32_t vload = (!psel && tid < npop) ? ldcg32(stat_of(PP[tid]) + 1 + HCUR) : 0u;
+        const uint32_t vload = (!psel && tid < npop) ? ldcg32(stat_of(PP[tid]) + 1 + par) : 0u;
         int g1 = 0;
         uint32_t goff = 0;
         while (!psel && g1 < npop) {
@@ -1201,7 +1168,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                     ++i;
                     nb = hbuckets(S[i].cap, S[i].hlo, S[i].shift);
                 }
-                hv[r] = ldcg32(hist_of(PP[i], HCUR) + (e - base));
+                hv[r] = ldcg32(hist_of(PP[i], par) + (e - base));
             }
         }
         // first tile of this warp: its fitness is loaded now, with the histograms
@@ -1219,21 +1186,14 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
         const uint32_t nwork_t = prm.thread_slots >> 5;
         const Pre pre0 = t == 0 ? first_pre(0) : pre_next;
         for (int i = 0; i < npop && !psel; ++i) {
-            uint32_t *hz = hist_of(PP[i], HCLR);
+            uint32_t *hn = hist_of(PP[i], par ^ 1);
             for (uint32_t e = gtid; e < (uint32_t)kHistR; e += gthreads)
-                hz[e] = 0u;
+                hn[e] = 0u;
         }
         if (blockIdx.x == 0 && tid < npop) {
             const FusedPop &p = PP[tid];
-            stat_of(p)[1 + HCLR] = 0u;
-            // the best key of this generation starts empty; with one barrier per
-            // generation it is cleared a generation ahead (the closing barrier
-            // orders the clear before the adds), the slot of generation t + 1
-            // being another than generation t's (traj_cap >= 2)
-            if (!prm.one_barrier)
-                p.traj[(S[tid].gen0 + (uint32_t)t) % (uint32_t)p.traj_cap] = ~0ull;
-            else if (t + 1 < prm.ngen)
-                p.traj[(S[tid].gen0 + (uint32_t)t + 1u) % (uint32_t)p.traj_cap] = ~0ull;
+            stat_of(p)[1 + (par ^ 1)] = 0u;
+            p.traj[(S[tid].gen0 + (uint32_t)t) % (uint32_t)p.traj_cap] = ~0ull;
         }
         if (tid == 0)
             s_flag = 0;
@@ -1269,7 +1229,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                     int i = 0;
                     while (i + 1 < i1 && e >= hoff[i + 1])
                         ++i;
-                    hcnt[e] = ldcg32(hist_of(PP[i], HCUR) + (e - hoff[i]));
+                    hcnt[e] = ldcg32(hist_of(PP[i], par) + (e - hoff[i]));
                 }
             } else {
                 __syncthreads();
@@ -1277,7 +1237,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                     int i = i0;
                     while (i + 1 < i1 && e >= hoff[i + 1])
                         ++i;
-                    hcnt[e] = ldcg32(hist_of(PP[i], HCUR) + (e - hoff[i]));
+                    hcnt[e] = ldcg32(hist_of(PP[i], par) + (e - hoff[i]));
                 }
             }
             __syncthreads();
@@ -1392,13 +1352,13 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                 // probabilistic selection: in-tile weight prefixes and the tile's weight
                 const unsigned long long sum = psel_tile(f, q < P, p.cw + (size_t)(tl - p.tile_base) * 32u, lane);
                 if (lane == 0)
-                    p.tmask[2u * (tl - p.tile_base)] = sum;
+                    p.tmask[tl - p.tile_base] = sum;
                 continue;
             }
             const uint32_t lt = __ballot_sync(FULL, q < P && f < T);
             const uint32_t eq = __ballot_sync(FULL, q < P && f == T);
             if (lane == 0)
-                st_tile_masks(p.tmask + 2u * (tl - p.tile_base), MASK_TAG, lt, eq);
+                p.tmask[tl - p.tile_base] = (unsigned long long)lt | ((unsigned long long)eq << 32);
         }
         // block-local histogram offsets of the next generation (read after
         // the barrier's bar.sync)
@@ -1411,89 +1371,32 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                     off += nb;
             }
         }
-        // with one barrier per generation the tile masks carry their generation
-        // and phase B waits for each entry instead (truncation selection)
-        if (!prm.one_barrier && !grid_barrier(prm.bar, nblocks, epoch, err))
+        if (!grid_barrier(prm.bar, nblocks, epoch, err))
             return;
 
         // ---- phase B: survivors in slot order, then build ------------------------
-        int masks_ok = 1;
-        auto mask_at = [&](uint32_t tt) {
-            const int i = owner_of(tt, npop, tile_base);
-            return PP[i].tmask + 2u * (tt - PP[i].tile_base);
-        };
-        constexpr int kMaskBatch = 3;  // tile-mask loads in flight per thread (P = 40,000: one batch)
-        for (uint32_t t0 = tid; t0 < TT; t0 += kMaskBatch * blockDim.x) {
-            ulonglong2 v[kMaskBatch];
+        for (uint32_t t0 = tid; t0 < TT; t0 += 4u * blockDim.x) {
+            unsigned long long v[4];
 #pragma unroll
-            for (int r = 0; r < kMaskBatch; ++r) {
+            for (int r = 0; r < 4; ++r) {
                 const uint32_t tt = t0 + (uint32_t)r * blockDim.x;
                 if (tt < TT) {
-                    if (psel)
-                        v[r] = make_ulonglong2(ldcg64(mask_at(tt)), 0ull);
-                    else
-                        v[r] = ld_tile_masks(mask_at(tt));
+                    const int i = owner_of(tt, npop, tile_base);
+                    v[r] = ldcg64(PP[i].tmask + (tt - PP[i].tile_base));
                 }
             }
-            if (psel) {
 #pragma unroll
-                for (int r = 0; r < kMaskBatch; ++r) {
-                    const uint32_t tt = t0 + (uint32_t)r * blockDim.x;
-                    if (tt < TT)
-                        tm[tt] = v[r].x;  // the tile's weight
-                }
-                continue;
-            }
-            // bounded wait for this generation's entries (already there after a
-            // grid barrier): every pending entry is reloaded in the same round,
-            // so the wait is the latest entry plus one round trip
-            uint32_t pending = 0;
-#pragma unroll
-            for (int r = 0; r < kMaskBatch; ++r) {
-                const uint32_t tt = t0 + (uint32_t)r * blockDim.x;
-                if (tt < TT && ((uint32_t)(v[r].x >> 32) != MASK_TAG || (uint32_t)(v[r].y >> 32) != MASK_TAG))
-                    pending |= 1u << r;
-            }
-            unsigned long long since = 0ull;
-            uint32_t spins = 0;
-            while (pending && masks_ok) {
-                if ((++spins & 15u) == 0u) {
-                    if (ld_acquire_gpu(err) != 0u) {
-                        masks_ok = 0;
-                        break;
-                    }
-                    const unsigned long long now = global_ns();
-                    if (since == 0ull)
-                        since = now;
-                    else if (now - since > kBarrierBudgetNs) {
-                        atomicOr(err, ERR_TIMEOUT);
-                        masks_ok = 0;
-                        break;
-                    }
-                }
-#pragma unroll
-                for (int r = 0; r < kMaskBatch; ++r)
-                    if (pending & (1u << r))
-                        v[r] = ld_tile_masks(mask_at(t0 + (uint32_t)r * blockDim.x));
-#pragma unroll
-                for (int r = 0; r < kMaskBatch; ++r)
-                    if ((pending & (1u << r)) && (uint32_t)(v[r].x >> 32) == MASK_TAG &&
-                        (uint32_t)(v[r].y >> 32) == MASK_TAG)
-                        pending &= ~(1u << r);
-            }
-#pragma unroll
-            for (int r = 0; r < kMaskBatch; ++r) {
+            for (int r = 0; r < 4; ++r) {
                 const uint32_t tt = t0 + (uint32_t)r * blockDim.x;
                 if (tt < TT)
-                    tm[tt] = (v[r].x & 0xFFFFFFFFull) | (v[r].y << 32);
+                    tm[tt] = v[r];
             }
         }
         for (uint32_t e = tid; e < kHistSmem; e += blockDim.x)
             bhist[e] = 0u;
         if (tid == 0)
             s_next = 0u;
-        if (__syncthreads_or(!masks_ok))
-            return;  // a wait gave up (ERR_TIMEOUT) or another block raised an error
+        __syncthreads();
         block_scan_chunks_u64(
             TT,
             [&](uint32_t e) {
@@ -1569,7 +1472,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
                     if (valid && fv[e] <= s.capn)
                         atomicAdd(bhist + s.boff + hkey(fv[e], s.hlon, s.shiftn), 1u);
                 } else {
-                    warp_hist_add(hist_of(p, HNXT), valid && fv[e] <= s.capn, hkey(fv[e], s.hlon, s.shiftn));
+                    warp_hist_add(hist_of(p, par ^ 1), valid && fv[e] <= s.capn, hkey(fv[e], s.hlon, s.shiftn));
                 }
                 orr |= valid ? fv[e] : 0u;
                 const unsigned long long ke = valid ? (((unsigned long long)fv[e] << 32) | sl[e]) : ~0ull;
@@ -1605,7 +1508,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             const FusedPop &p = PP[i];
             const uint32_t item = it - p.work_base, k = item >> 1;
             const int half = (int)(item & 1u);
-            uint32_t *hn = hist_of(p, HNXT);
+            uint32_t *hn = hist_of(p, par ^ 1);
             const uint32_t gen = S[i].gen0 + 1u + (uint32_t)t;
             switch (p.W) {
             case 2: offspring_warp<2, INC>(p, S[i], src, gen, (uint32_t)t, k, half, sv, err, wbuf, ring, prm.inc_ring, &s_incbar[wib], inc_parity, hn, bhist); break;
@@ -1621,7 +1524,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
             if (bo == 0xFFFFFFFFu)
                 continue;
             const uint32_t nb = hbuckets(S[i].capn, S[i].hlon, S[i].shiftn);
-            uint32_t *hn = hist_of(PP[i], HNXT);
+            uint32_t *hn = hist_of(PP[i], par ^ 1);
             for (uint32_t e = tid; e < nb; e += blockDim.x) {
                 const uint32_t c = bhist[bo + e];
                 if (c)
@@ -1631,7 +1534,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
         if (tid < npop) {
             const FusedPop &p = PP[tid];
             if (S[tid].bor)
-                atomicOr(stat_of(p) + 1 + HNXT, S[tid].bor);
+                atomicOr(stat_of(p) + 1 + (par ^ 1), S[tid].bor);
             if (S[tid].bbest != ~0ull)
                 atomicMin(p.traj + (S[tid].gen0 + (uint32_t)t) % (uint32_t)p.traj_cap, S[tid].bbest);
         }
@@ -1656,10 +1559,6 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
         }
         __syncthreads();
     }
-#undef HCUR
-#undef HNXT
-#undef HCLR
-#undef MASK_TAG
     if (blockIdx.x == 0 && tid == 0)
         *prm.done = done;
     if (blockIdx.x == 0 && tid < npop)

@@ -124,17 +124,15 @@ constexpr int kFusedMaxM = 128;    // orders the fused kernel builds (larger: pl
 constexpr uint32_t kFusedMaxTiles = 8192;   // joint tiles of 32 slots (P <= 262144)
 
 // Per-population state words of the fused kernel (device memory):
-// hist[3][kHistR] selection histograms rotating over generations,
-// ref[3][kHistR] refinement histograms, stat[4] = {max F, OR of F (three
-// rotating words)}.
-constexpr size_t kFusedStateWords = 6 * kHistR + 4;
+// hist[2][kHistR] selection histograms by generation parity, ref[3][kHistR]
+// refinement histograms, stat[4] = {max F, OR of F (parity 0, parity 1), spare}.
+constexpr size_t kFusedStateWords = 5 * kHistR + 4;
 
 struct FusedPop {
     uint32_t *pop[2];          // bit storage, ping-pong
     uint32_t *fit[2];          // fitness, ping-pong
     uint32_t *state;           // kFusedStateWords words, zeroed before each launch
-    unsigned long long *tmask; // [ntiles][2] per tile: (tag << 32 | F < T mask), (tag << 32 | F == T mask);
-                               // probabilistic selection: the tile's weight in word 0.  Zeroed per launch.
+    unsigned long long *tmask; // [ntiles] (F < T) | (F == T) << 32 per tile
     const uint32_t *perm;      // [ngen][2N] survivor orders of the chunk
     unsigned long long *traj;  // [traj_cap] best keys (F << 32 | slot)
     uint32_t *gen_dev;         // generation counter: read at start, advanced at exit
@@ -164,7 +162,6 @@ struct FusedParams {
     int32_t warp_buf_words;  // shared words per warp for m > 32 populations
     int32_t inc_ring;        // 16-byte slots per warp of the incremental copy ring (0: no incremental population)
     int32_t psel;            // probabilistic selection (every population), else truncation
-    int32_t one_barrier;     // one grid barrier per generation (tagged tile masks; truncation, traj_cap >= 2)
     uint32_t *bar;           // grid-barrier counter (zeroed before the launch)
     uint32_t *err;           // device error word
     int32_t *done;           // generations completed
