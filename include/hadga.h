@@ -225,7 +225,8 @@ ga_status ga_step_multi_graph(ga_ctx *const *ctxs, int32_t n, int32_t generation
  * duration of the call. */
 ga_status ga_set_incremental(ga_ctx *ctx, int32_t enable);
 
-/* Whether incremental mode is on, and the milliseconds per generation the
+/* Whether incremental mode (the Gram-delta update of the fitness of Sec. 3.2
+ * under the operators of Sec. 3.4-3.5) is on, and the milliseconds per generation the
  * last AUTO choice measured with full recomputation and with the stored
  * Gram (0 if AUTO never ran).  Host only. */
 ga_status ga_get_incremental(const ga_ctx *ctx, int32_t *enabled, float *full_ms_per_gen, float *inc_ms_per_gen);
@@ -244,7 +245,8 @@ ga_status ga_get_gram(ga_ctx *ctx, int64_t slot, int32_t *host_G);
  * (0 = one per SM, the default).  Chosen by the autotuner. */
 ga_status ga_set_fused_grid(ga_ctx *ctx, int32_t blocks);
 
-/* Launch shape of this population in the persistent kernel (chosen by the
+/* Launch shape of this population in the persistent kernel (an
+ * implementation parameter with no counterpart in the paper, chosen by the
  * autotuner per order; results are identical for every shape).  tpp:
  * threads per pair of the m <= 32 build, 2 (each thread computes a whole
  * offspring) or 4 (each half of its terms); 0 = default 4.  nch: chunks per
@@ -254,7 +256,8 @@ ga_status ga_set_fused_grid(ga_ctx *ctx, int32_t blocks);
 ga_status ga_set_fused_shape(ga_ctx *ctx, int32_t tpp, int32_t nch);
 
 /* Process-wide override of GA_PATH_AUTO for (storage, m, kind): the Gram
- * path the autotuner measured fastest on this GPU (GA_PATH_AUTO clears the
+ * path (of the fitness of Sec. 3.2, Eq. (3)-(5)) the autotuner measured
+ * fastest on this GPU (GA_PATH_AUTO clears the
  * override and restores the built-in choice).  GA_EINVAL when the path
  * cannot compute that fitness of that storage at that order.  Host only. */
 ga_status ga_set_auto_path(int32_t storage, int32_t m, int32_t kind, int32_t path);
@@ -262,7 +265,8 @@ ga_status ga_set_auto_path(int32_t storage, int32_t m, int32_t kind, int32_t pat
 /* 1 if ga_step runs the fused kernel for this context, 0 if it falls back. */
 int32_t ga_step_is_fused(const ga_ctx *ctx);
 
-/* strict != 0: ga_step and ga_step_multi never fall back to the one-kernel-
+/* Execution policy (no counterpart in the paper).
+ * strict != 0: ga_step and ga_step_multi never fall back to the one-kernel-
  * per-operator path; a population the persistent kernel cannot run makes
  * them return GA_EUNSUPPORTED (reason in ga_last_error).  Returns
  * GA_EUNSUPPORTED at once when setting strict mode on such a context (the

@@ -207,18 +207,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
     if (warp == 0) {
         // ---- TMA producer ----------------------------------------------------
         if (lane == 0) {
-            int pos[2] = {0, 0};          // next stage of each ring half (relative)
-            uint32_t sph[2] = {0u, 0u};   // parity of that stage's current use
-            uint32_t used[2] = {0u, 0u};  // stage uses issued in each half
-            int who = 0;                  // issuer (ring half) of the next job
+            // per ring half (issuer) 0 / 1, kept in registers: next stage
+            // (relative), parity of its current use, uses issued so far
+            int pos0 = 0, pos1 = 0;
+            uint32_t sph0 = 0u, sph1 = 0u, used0 = 0u, used1 = 0u;
+            int who = 0;  // issuer (ring half) of the next job
             bool ok = true;
             for (int64_t j = blockIdx.x; j < prm.jobs && ok; j += gridDim.x) {
-                const int r = who;
+                const bool second = who == 1;
                 if (++who == nis)
                     who = 0;
+                int pos = second ? pos1 : pos0;
+                uint32_t sph = second ? sph1 : sph0;
+                const int s0 = second ? SR : 0;
+                int issued = 0;
                 for (int c = 0; c < nch; ++c) {
-                    const int st = r * SR + pos[r];
-                    if (!mbar_wait(&empty[st], sph[r] ^ 1u, err)) {
+                    const int st = s0 + pos;
+                    if (!mbar_wait(&empty[st], sph ^ 1u, err)) {
                         ok = false;
                         break;
                     }
@@ -227,20 +232,30 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
                     for (int h = 0; h < rows / 128; ++h)
                         tma_load_2d(stages + (size_t)st * sbytes + (size_t)h * 128 * kb, &map, x,
                                     (int32_t)(j * rows + h * 128), &full[st]);
-                    ++used[r];
-                    if (++pos[r] == SR) {
-                        pos[r] = 0;
-                        sph[r] ^= 1u;
+                    ++issued;
+                    if (++pos == SR) {
+                        pos = 0;
+                        sph ^= 1u;
                     }
+                }
+                if (second) {
+                    pos1 = pos;
+                    sph1 = sph;
+                    used1 += (uint32_t)issued;
+                } else {
+                    pos0 = pos;
+                    sph0 = sph;
+                    used0 += (uint32_t)issued;
                 }
             }
             if (!ok) {
                 // drain: let copies already in flight land before the block exits
                 // (the last min(used, SR) uses of each half)
                 for (int r = 0; r < nis; ++r) {
-                    const uint32_t n = used[r] < (uint32_t)SR ? used[r] : (uint32_t)SR;
+                    const uint32_t used = r ? used1 : used0;
+                    const uint32_t n = used < (uint32_t)SR ? used : (uint32_t)SR;
                     for (uint32_t q = 0; q < n; ++q) {
-                        const uint32_t u = used[r] - 1u - q;
+                        const uint32_t u = used - 1u - q;
                         mbar_wait(&full[r * SR + (int)(u % (uint32_t)SR)], (u / (uint32_t)SR) & 1u, err);
                     }
                 }

@@ -356,3 +356,32 @@ def test_threshold_below_the_histogram_window(m, N, gens):
     F = oracle.fitness(ref, oracle.FIT_SQ)
     _, tf, ts = oracle.run(ref, F, N, 1, 1, oracle.FIT_SQ, 17, 0, 0, gens)
     _assert_same(gpu, (ref, F, tf, ts))
+
+
+def test_config4_full_sizes_graph_prefix():
+    """Config 4 at its real sizes: orders 12..36 with P = 4 (500 + U[0, 4500])
+    from the CONFIG stream (seed 3), one persistent launch per CUDA-graph
+    chunk of 10 generations, 20 generations, every population equal to its
+    own oracle run."""
+    h = need_gpu()
+    orders = [12, 16, 20, 24, 28, 32, 36]
+    gens = 20
+    stream = torch.cuda.Stream()
+    pops, refs = [], []
+    for idx, m in enumerate(orders):
+        N = oracle.mixed_N(3, idx)
+        p = h.Population(m, N, seed=3, pop_id=idx, fitness=0, storage=1, traj_cap=64, stream=stream)
+        p.set_strict(True)
+        p.init_population()
+        p.fitness()
+        pops.append(p)
+        r = oracle.init_population(m, 4 * N, 3, idx)
+        F = oracle.fitness(r, 0)
+        _, tf, ts = oracle.run(r, F, N, 1, 1, 0, 3, idx, 0, gens)
+        refs.append((r, F, tf, ts))
+    h.step_multi_graph(pops, gens, 10)
+    for p, ref in zip(pops, refs):
+        p.sync()
+        assert p.generation() == gens
+        _assert_same((p.as_int8(), p.fitness_host(), p.trajectory()), ref)
+        p.close()

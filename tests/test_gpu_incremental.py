@@ -164,3 +164,30 @@ def test_auto_choice_measures_both_and_leaves_the_state(m, N):
     if on:
         assert pop.check_incremental() == (0, 0)
     pop.close()
+
+
+@pytest.mark.parametrize("incremental", [False, True])
+def test_config5_full_size_prefix(incremental):
+    """Config 5 at its real size (m = 100, P = 20,000, bit storage, F_sq,
+    NC = NR = 1, seed 4): 20 generations of the fused path, with full
+    recomputation or the incremental Gram-delta fitness, equal to the oracle;
+    the incremental state passes a GPU full recheck."""
+    h = need_gpu()
+    m, N, gens = 100, 5000, 20
+    pop = h.Population(m, N, seed=4, storage=h.STORE_BITS, traj_cap=gens)
+    pop.set_strict(True)
+    pop.init_population()
+    pop.fitness()
+    if incremental:
+        pop.set_incremental(True)
+    pop.step(gens)
+    pop.sync()
+    ref = oracle.init_population(m, 4 * N, 4)
+    F = oracle.fitness(ref, oracle.FIT_SQ)
+    _, tf, ts = oracle.run(ref, F, N, 1, 1, oracle.FIT_SQ, 4, 0, 0, gens)
+    assert np.array_equal(pop.as_int8(), ref) and np.array_equal(pop.fitness_host(), F)
+    gtf, gts = pop.trajectory()
+    assert np.array_equal(gtf.astype(np.uint64), tf) and np.array_equal(gts, ts)
+    if incremental:
+        assert pop.check_incremental() == (0, 0)
+    pop.close()
