@@ -1,7 +1,10 @@
 """ga_select_static: the selection step for callers that cannot allocate
 device memory while it runs (its scratch is a fixed array inside the
 library).  Checked against the context-based ga_select and the oracle's
-selection, bit for bit, on two calls in a row.  Named to be collected last."""
+selection, bit for bit, on two calls in a row.  The step's internal
+consistency checks (survivor counts, masks) have no output of their own: any
+inconsistency they could see would put a wrong parent into the outputs,
+which the comparison with the oracle catches.  Named to be collected last."""
 import numpy as np
 import pytest
 import torch
