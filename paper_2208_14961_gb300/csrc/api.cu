@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "hadga.h"
 #include "common.cuh"
 #include "kernels.cuh"
@@ -36,6 +38,16 @@ constexpr int32_t kVersion = 1 * 10000 + 0 * 100 + 0;
 constexpr int64_t kMaxP = int64_t(1) << 31;
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Host-side NVTX range for the duration of a scope: calls and chunks of the
+// library appear by name in tools that record NVTX (ncu --nvtx, Nsight
+// Systems); without such a tool attached the calls do nothing.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 } // namespace
 
@@ -363,6 +375,7 @@ static ga_status begin(ga_ctx *ctx)
 
 ga_status ga_init_population(ga_ctx *ctx)
 {
+    NvtxRange nvtx("ga_init_population");
     ga_status st = begin(ctx);
     if (st != GA_OK)
         return st;
@@ -380,6 +393,7 @@ ga_status ga_init_population(ga_ctx *ctx)
 
 ga_status ga_fitness(ga_ctx *ctx, int64_t first, int64_t count)
 {
+    NvtxRange nvtx("ga_fitness");
     ga_status st = begin(ctx);
     if (st != GA_OK)
         return st;
@@ -394,6 +408,7 @@ ga_status ga_fitness(ga_ctx *ctx, int64_t first, int64_t count)
 
 ga_status ga_select(ga_ctx *ctx)
 {
+    NvtxRange nvtx("ga_select");
     ga_status st = begin(ctx);
     if (st != GA_OK)
         return st;
@@ -425,6 +440,7 @@ ga_status ga_select(ga_ctx *ctx)
 
 ga_status ga_crossover(ga_ctx *ctx)
 {
+    NvtxRange nvtx("ga_crossover");
     ga_status st = begin(ctx);
     if (st != GA_OK)
         return st;
@@ -437,6 +453,7 @@ ga_status ga_crossover(ga_ctx *ctx)
 
 ga_status ga_mutate(ga_ctx *ctx)
 {
+    NvtxRange nvtx("ga_mutate");
     ga_status st = begin(ctx);
     if (st != GA_OK)
         return st;
@@ -460,6 +477,7 @@ ga_status ga_record_best(ga_ctx *ctx)
 
 ga_status ga_step_plain(ga_ctx *ctx, int32_t generations)
 {
+    NvtxRange nvtx("ga_step_plain");
     ga_status st = begin(ctx);
     if (st != GA_OK)
         return st;
@@ -590,6 +608,7 @@ static ga_status fused_run(ga_ctx *const *ctxs, int n, int32_t generations, int 
     int32_t total_done = 0;
     for (int32_t left = generations; left > 0;) {
         const int chunk = left < kChunk ? left : kChunk;
+        NvtxRange nvtx_chunk("persistent chunk");
         for (int i = 0; i < n; ++i) {
             ga_ctx *c = ctxs[i];
             cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -674,6 +693,7 @@ static ga_status fused_run(ga_ctx *const *ctxs, int n, int32_t generations, int 
 
 ga_status ga_step(ga_ctx *ctx, int32_t generations, int32_t stop_at_zero, int32_t *done)
 {
+    NvtxRange nvtx("ga_step");
     ga_status st = begin(ctx);
     if (st != GA_OK)
         return st;
@@ -712,6 +732,7 @@ ga_status ga_step(ga_ctx *ctx, int32_t generations, int32_t stop_at_zero, int32_
 
 ga_status ga_step_multi(ga_ctx *const *ctxs, int32_t n, int32_t generations)
 {
+    NvtxRange nvtx("ga_step_multi");
     if (!ctxs || n < 1)
         return set_error(nullptr, GA_EINVAL, "ctxs must hold n >= 1 contexts");
     if (generations < 0)
@@ -786,6 +807,7 @@ ga_status ga_profile_read(ga_ctx *ctx, float *perm_ms, float *fused_ms, int32_t 
 
 ga_status ga_step_multi_graph(ga_ctx *const *ctxs, int32_t n, int32_t generations, int32_t chunk)
 {
+    NvtxRange nvtx("ga_step_multi_graph");
     if (!ctxs || n < 1 || n > kMaxPops)
         return set_error(nullptr, GA_EINVAL, "ctxs must hold 1..%d contexts", kMaxPops);
     if (generations < 0 || chunk < 2 || chunk > kChunk || (chunk & 1))
