@@ -33,8 +33,13 @@
  *
  * Randomness: Philox4x32-10 (Salmon et al., SC'11), key (seed, pop_id),
  * counter (op, generation, index, (sub << 16) | block); op INIT = 0,
- * SELECT = 1, CROSS = 2, MUTATE = 3.  A word w gives an integer in [lo, hi]
- * as lo + floor(w * (hi - lo + 1) / 2^32).
+ * SELECT = 1, CROSS = 2, MUTATE = 3, CONFIG = 4 (mixed-order sizes),
+ * PSELECT = 5 (probabilistic selection: words 0, 1 of (PSELECT, g, p, 0)
+ * form the 64-bit draw of parent slot p).  A word w gives an integer in
+ * [lo, hi] as lo + floor(w * (hi - lo + 1) / 2^32).
+ *
+ * Tracing: every host call, and each chunk of the persistent kernel, is an
+ * NVTX range named after the call ("ga_step", "persistent chunk", ...).
  */
 #ifndef HADGA_H
 #define HADGA_H
