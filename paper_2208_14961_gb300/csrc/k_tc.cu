@@ -150,7 +150,11 @@ __device__ __forceinline__ float sq_cols(uint32_t taddr)
 
 } // namespace
 
-template <bool BF16>
+// SPLIT: m <= 128, two MMA issuers, each with its own half of the stage ring
+// (four accumulators); otherwise m = 256, one issuer on the whole ring and one
+// accumulator. The two are separate instantiations so that neither carries the
+// other's loops or epilogue.
+template <bool BF16, bool SPLIT>
 __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant__ CUtensorMap map,
                                                           const __grid_constant__ TcParams prm)
 {
@@ -166,8 +170,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m = prm.m, rows = prm.rows, nch = prm.nchunks, kb = prm.kb, S = prm.nstages;
     const uint32_t sbytes = (uint32_t)rows * (uint32_t)kb;  // bytes of one stage
-    const int nacc = (m == 256) ? 1 : 4;
-    const int ngroups = (m == 256) ? 1 : 2;
+    constexpr int nacc = SPLIT ? 4 : 1;
+    constexpr int ngroups = SPLIT ? 2 : 1;
     const uint32_t tmem_cols = 512u;
     uint32_t *err = prm.err ? prm.err : &g_tc_err;
 
@@ -202,11 +206,44 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
 
     // MMA issuers and the stage ring halves they own (one ring of S stages
     // with a single issuer; two halves of SR stages with two)
-    const int nis = nacc > 1 ? 2 : 1;
+    constexpr int nis = SPLIT ? 2 : 1;
     const int SR = S / nis;
     if (warp == 0) {
         // ---- TMA producer ----------------------------------------------------
-        if (lane == 0) {
+        if (!SPLIT && lane == 0) {
+            // one issuer, one ring (m = 256)
+            uint32_t it = 0;
+            int issued = 0;
+            int st = 0;         // stage of copy `it`
+            uint32_t sph = 0u;  // parity of that stage's current use
+            bool ok = true;
+            for (int64_t j = blockIdx.x; j < prm.jobs && ok; j += gridDim.x) {
+                for (int c = 0; c < nch; ++c, ++it) {
+                    if (!mbar_wait(&empty[st], sph ^ 1u, err)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&full[st], sbytes);
+                    const int32_t x = c * (kb / prm.esize);
+                    for (int h = 0; h < rows / 128; ++h)
+                        tma_load_2d(stages + (size_t)st * sbytes + (size_t)h * 128 * kb, &map, x,
+                                    (int32_t)(j * rows + h * 128), &full[st]);
+                    issued = issued < S ? issued + 1 : S;
+                    if (++st == S) {
+                        st = 0;
+                        sph ^= 1u;
+                    }
+                }
+            }
+            if (!ok) {
+                // drain: let copies already in flight land before the block exits
+                for (int q = 0; q < issued; ++q) {
+                    const uint32_t itq = it - 1u - (uint32_t)q;
+                    mbar_wait(&full[itq % (uint32_t)S], (itq / (uint32_t)S) & 1u, err);
+                }
+            }
+        } else if (SPLIT && lane == 0) {
+            // two issuers, two ring halves (m <= 128)
             // per ring half (issuer) 0 / 1, kept in registers: next stage
             // (relative), parity of its current use, uses issued so far
             int pos0 = 0, pos1 = 0;
@@ -274,7 +311,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
             constexpr bool TWO = decltype(two)::value;
             const uint32_t sbo = 8u * (uint32_t)kb;
             // ring positions kept as counters: no division in the issue loop
-            const int s0 = me * SR;  // first stage of this issuer's ring half
+            // first stage and length of this issuer's ring (half of the ring with two issuers)
+            const int s0 = TWO ? me * SR : 0, sr = TWO ? SR : S;
             int st = s0, b = 0, who = 0;
             uint32_t sph = 0u, aph = 0u;  // parities of the stage's and accumulator's current use
             bool ok = true;
@@ -307,8 +345,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
                     for (int ks = 0; ks < kb / 32; ++ks) {
                         const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
                         const uint32_t koff = (uint32_t)ks * 32u;
-                        if (m == 256) {
-                            // upper blocks: rows 0..127 x cols 0..255, rows 128..255 x cols 128..255
+                        if constexpr (!SPLIT) {
+                            // m = 256, upper blocks: rows 0..127 x cols 0..255, rows 128..255 x cols 128..255
                             const uint64_t a0 = smem_desc(base + koff, sbo, prm.layout);
                             const uint64_t a1 = smem_desc(base + 128u * (uint32_t)kb + koff, sbo, prm.layout);
                             mma<BF16>(tbase, a0, a0, prm.idesc_n256, acc);
@@ -319,7 +357,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
                         }
                     }
                     mma_commit(&empty[st]);  // the stage is free once these MMAs have read it
-                    if (++st == s0 + SR) {
+                    if (++st == s0 + sr) {
                         st = s0;
                         sph ^= 1u;
                     }
@@ -339,7 +377,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
             }
         };
         if (lane == 0 && me < nis) {
-            if (nis == 2)
+            if constexpr (SPLIT)
                 issue(std::true_type{});
             else
                 issue(std::false_type{});
@@ -374,8 +412,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t lane_addr = tbase + ((uint32_t)(q * 32) << 16);
                 float sum_a = 0.f, sum_b = 0.f;
-                if (m == 256) {
-                    // row t of the first block: columns 0..127 count once, 128..255 twice
+                if constexpr (!SPLIT) {
+                    // m = 256: row t of the first block: columns 0..127 count once, 128..255 twice
                     // (their mirror images below the diagonal are not computed); row
                     // 128 + t of the second block: its 128 columns once
                     sum_a = sq_cols<4>(lane_addr);
@@ -396,7 +434,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
                 for (int o = 16; o > 0; o >>= 1)
                     tot += __shfl_xor_sync(0xFFFFFFFFu, tot, o);
                 const unsigned long long m3 = (unsigned long long)m * m * m;
-                if (m <= 32) {
+                if (SPLIT && m <= 32) {
                     // one warp per matrix
                     const int64_t mat = (j * rows + (int64_t)q * 32) / m;
                     if (lane == 0 && mat < prm.P)
@@ -529,7 +567,8 @@ cudaError_t launch_fitness_tc(const void *pop, int storage, int m, int64_t first
         prm.nstages = (int32_t)(ns > (uint32_t)kMaxStages ? kMaxStages : ns);
     }
     const size_t smem = (size_t)prm.nstages * prm.rows * prm.kb + 1024;
-    auto kern = bf16 ? k_fsq_tc<true> : k_fsq_tc<false>;
+    auto kern = bf16 ? (m == 256 ? k_fsq_tc<true, false> : k_fsq_tc<true, true>)
+                     : (m == 256 ? k_fsq_tc<false, false> : k_fsq_tc<false, true>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
