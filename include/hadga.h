@@ -379,10 +379,22 @@ ga_status ga_fitness_batch(const void *pop_dev, int32_t storage, int32_t m, int6
  * that must start at zero are cleared by each call), so calls that overlap
  * on the GPU -- on different streams, or from different threads -- race.
  * Stream-ordered; argument errors are reported through ga_last_error(NULL);
- * device-side consistency checks are not reported. */
+ * the device-side consistency checks (survivor counts and masks) raise bits
+ * in the array's error word, which this call clears first and does not read:
+ * ga_select_static_error reads it. */
 ga_status ga_select_static(const void *pop_in, const uint32_t *fit_in, void *parents_out, uint32_t *parent_fit_out,
                            int32_t storage, int32_t m, int64_t N, uint32_t seed, uint32_t pop_id, uint32_t gen,
                            void *stream);
+
+/* The error word of the last ga_select_static call on the current device
+ * whose work is ordered before `stream`: copied into *err_out (host memory)
+ * after `stream` has been synchronised.  0 when every consistency check
+ * held; bit 1 (value 2) when the survivor counts or masks disagreed (a
+ * parent was then clamped to the last slot and the outputs are wrong).
+ * A diagnostic for tests and debugging: it synchronises, and its pageable
+ * copy may take host staging memory.  GA_EINVAL for a NULL err_out,
+ * GA_ECUDA for a CUDA error (message in ga_last_error(NULL)). */
+ga_status ga_select_static_error(uint32_t *err_out, void *stream);
 
 /* Element type of ga_gram_real_batch. */
 typedef enum {

@@ -29,11 +29,13 @@ namespace {
 
 // Largest N the allocation-free selection accepts (P = 4N <= 32768).
 constexpr int64_t kStaticMaxN = 8192;
-// Scratch layout (bytes): histogram 2048 words, selection state, per tile
-// (P/32 tiles) an 8-byte mask pair and two 4-byte words, the survivor order
-// (2N words), and the device error word.
+// Scratch layout (bytes): histogram 2048 words, selection state, the device
+// error word (in a 256-byte block of its own, at a fixed offset), then per tile
+// (P/32 tiles) an 8-byte mask pair and two 4-byte words and the survivor order
+// (2N words).
 constexpr size_t kStaticHistBytes = 2048 * 4;
 constexpr size_t kStaticStateBytes = 256;
+constexpr size_t kStaticErrOff = kStaticHistBytes + kStaticStateBytes;
 constexpr size_t kStaticTiles = (size_t)(4 * kStaticMaxN) / 32;
 constexpr size_t kStaticScratchBytes =
     kStaticHistBytes + kStaticStateBytes + kStaticTiles * (8 + 4 + 4) + (size_t)(2 * kStaticMaxN) * 4 + 256;
@@ -48,6 +50,26 @@ ga_status fail(ga_status st, const char *msg)
 {
     set_thread_error(msg);  // reported by ga_last_error(NULL)
     return st;
+}
+
+// The current device's address of the scratch array (its host-side name is
+// only a stand-in), looked up once per device with that device current.
+ga_status scratch_base(const char *who, unsigned char **base)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return fail(GA_ECUDA, (std::string(who) + ": no usable current device").c_str());
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (!g_scratch_addr[dev]) {
+        void *ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_select_scratch);
+        if (e != cudaSuccess || !ptr)
+            return fail(GA_ECUDA, (std::string(who) + ": cudaGetSymbolAddress of the scratch array failed").c_str());
+        g_scratch_addr[dev] = ptr;
+    }
+    *base = (unsigned char *)g_scratch_addr[dev];
+    return GA_OK;
 }
 
 } // namespace
@@ -91,24 +113,10 @@ extern "C" ga_status ga_select_static(const void *pop_in, const uint32_t *fit_in
     if (overlap(out[0], out[1]))
         return fail(GA_EINVAL, "ga_select_static: parents_out must not overlap parent_fit_out");
 
-    // set-up, once per device, with that device current: the device address
-    // of the scratch array (its host-side name is only a stand-in)
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-        return fail(GA_ECUDA, "ga_select_static: no usable current device");
     unsigned char *base = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_mutex);
-        if (!g_scratch_addr[dev]) {
-            void *ptr = nullptr;
-            e = cudaGetSymbolAddress(&ptr, g_select_scratch);
-            if (e != cudaSuccess || !ptr)
-                return fail(GA_ECUDA, "ga_select_static: cudaGetSymbolAddress of the scratch array failed");
-            g_scratch_addr[dev] = ptr;
-        }
-        base = (unsigned char *)g_scratch_addr[dev];
-    }
+    const ga_status st = scratch_base("ga_select_static", &base);
+    if (st != GA_OK)
+        return st;
 
     const int64_t tiles = (4 * N + 31) / 32;
     SelWork w{};
@@ -117,6 +125,8 @@ extern "C" ga_status ga_select_static(const void *pop_in, const uint32_t *fit_in
     off += kStaticHistBytes;
     w.state = (SelState *)(base + off);
     off += kStaticStateBytes;
+    w.err = (uint32_t *)(base + off);
+    off += 256;
     w.tmask = (unsigned long long *)(base + off);
     off += (size_t)tiles * 8;
     w.survmask = (uint32_t *)(base + off);
@@ -125,19 +135,36 @@ extern "C" ga_status ga_select_static(const void *pop_in, const uint32_t *fit_in
     off += (size_t)tiles * 4;
     w.perm = (uint32_t *)(base + off);
     off += (size_t)(2 * N) * 4;
-    off = (off + 255) & ~(size_t)255;
-    w.err = (uint32_t *)(base + off);
     w.perm_keys = nullptr;  // 2N <= 16384 always takes the shared-memory sort
     w.perm_cnt = nullptr;
 
     cudaStream_t s = (cudaStream_t)stream;
     // the array keeps the previous call's contents: clear what must start at 0
-    e = cudaMemsetAsync(w.hist, 0, kStaticHistBytes + kStaticStateBytes, s);
+    cudaError_t e = cudaMemsetAsync(w.hist, 0, kStaticHistBytes + kStaticStateBytes, s);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(w.err, 0, 4, s);
     if (e == cudaSuccess)
         e = launch_select(pop_in, fit_in, N, mat, seed, pop_id, gen, w, parents_out, parent_fit_out, s);
     if (e != cudaSuccess)
         return fail(GA_ECUDA, cudaGetErrorString(e));
+    return GA_OK;
+}
+
+extern "C" ga_status ga_select_static_error(uint32_t *err_out, void *stream)
+{
+    if (!err_out)
+        return fail(GA_EINVAL, "ga_select_static_error: NULL err_out");
+    unsigned char *base = nullptr;
+    const ga_status st = scratch_base("ga_select_static_error", &base);
+    if (st != GA_OK)
+        return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t word = 0;
+    cudaError_t e = cudaMemcpyAsync(&word, base + kStaticErrOff, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess)
+        return fail(GA_ECUDA, cudaGetErrorString(e));
+    *err_out = word;
     return GA_OK;
 }

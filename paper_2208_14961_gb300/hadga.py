@@ -94,6 +94,7 @@ SIGNATURES = {
     "ga_convert": (_i32, [_vp, _i32, _vp, _i32, _i32, _i64, _vp]),
     "ga_gram_real_batch": (_i32, [_vp, _vp, _i32, _i32, _i64, _vp]),
     "ga_select_static": (_i32, [_vp, _vp, _vp, _vp, _i32, _i32, _i64, _u32, _u32, _u32, _vp]),
+    "ga_select_static_error": (_i32, [ctypes.POINTER(_u32), _vp]),
     "ga_debug_wait_timeout": (_i32, [_i32, _u32, ctypes.POINTER(_u32), _vp]),
     "ga_debug_fail_allocations": (_i32, [_i32]),
 }
@@ -201,6 +202,14 @@ def ga_select_static(pop_in: torch.Tensor, fit_in: torch.Tensor, parents_out: to
     allocation (the scratch is a fixed array inside the library)."""
     check(load().ga_select_static(_ptr(pop_in), _ptr(fit_in), _ptr(parents_out), _ptr(parent_fit_out), storage, m,
                                   N, seed, pop_id, gen, _stream(stream)))
+
+
+def ga_select_static_error(stream=None) -> int:
+    """Error word of the last ga_select_static call ordered before `stream`
+    (synchronises it): 0 when its consistency checks held."""
+    w = ctypes.c_uint32(0)
+    check(load().ga_select_static_error(ctypes.byref(w), _stream(stream)))
+    return int(w.value)
 
 
 def debug_wait_timeout(which: int, budget_us: int, stream=None):

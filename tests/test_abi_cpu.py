@@ -158,6 +158,12 @@ def test_select_static_rejects_every_overlap(lib, par, pfit, what):
     assert what in hadga.last_error()
 
 
+def test_select_static_error_rejects_null(lib):
+    """The error-word accessor validates its output pointer before any device call."""
+    from paper_2208_14961_gb300 import hadga
+    assert lib.ga_select_static_error(None, None) == hadga.GA_EINVAL
+    assert "NULL err_out" in hadga.last_error()
+
 
 def test_out_of_memory_hook_in_create_without_gpu(lib):
     """The allocation-failure hook makes ga_create fail with GA_ENOMEM before

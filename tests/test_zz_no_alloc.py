@@ -1,10 +1,9 @@
 """ga_select_static: the selection step for callers that cannot allocate
 device memory while it runs (its scratch is a fixed array inside the
 library).  Checked against the context-based ga_select and the oracle's
-selection, bit for bit, on two calls in a row.  The step's internal
-consistency checks (survivor counts, masks) have no output of their own: any
-inconsistency they could see would put a wrong parent into the outputs,
-which the comparison with the oracle catches.  Named to be collected last."""
+selection, bit for bit, on two calls in a row, with the step's device error
+word (its survivor-count and mask consistency checks) read back as zero
+after each call.  Named to be collected last."""
 import numpy as np
 import pytest
 import torch
@@ -41,6 +40,7 @@ def test_select_static_matches_ga_select(storage, m, N):
         pfit = torch.empty(2 * N, dtype=torch.int32, device="cuda")
         h.ga_select_static(pop_in, fit_in, parents, pfit, storage, m, N, seed, pop_id, gen,
                            stream=torch.cuda.current_stream())
+        assert h.ga_select_static_error(stream=torch.cuda.current_stream()) == 0
         ref.select()            # the existing entry point, generation `gen`
         torch.cuda.synchronize()
         assert ref.generation() == gen
