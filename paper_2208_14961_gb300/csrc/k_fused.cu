@@ -851,6 +851,17 @@ __device__ void offspring_warp(const FusedPop &p, PopSel &S, int src, uint32_t g
             }
         }
     }
+    // mutation draws (Sec. 3.5) in lane 0, while the parents are in flight
+    uint8_t cols[64], r1[64], r2[64];
+    if (lane == 0) {
+        Draws dr(p.seed, p.pop_id, gen, mut_stream(p, k + oh));
+        for (int jc = 0; jc < p.NC; ++jc)
+            cols[jc] = (uint8_t)uniform_int(dr.next(), 1u, (uint32_t)(m - 1));
+        for (int ir = 0; ir < p.NR; ++ir)
+            r1[ir] = (uint8_t)uniform_int(dr.next(), 0u, (uint32_t)(m - 1));
+        for (int ir = 0; ir < p.NR; ++ir)
+            r2[ir] = (uint8_t)uniform_int(dr.next(), 0u, (uint32_t)(m - 1));
+    }
     // the parents have landed once at most the Gram group (if any) is pending
     if (gram_group)
         cp_async_wait_group<1>();
@@ -874,14 +885,6 @@ __device__ void offspring_warp(const FusedPop &p, PopSel &S, int src, uint32_t g
     // columns where a flip happened
     uint32_t mut[4] = {0u, 0u, 0u, 0u};
     if (lane == 0) {
-        Draws dr(p.seed, p.pop_id, gen, mut_stream(p, k + oh));
-        uint8_t cols[64], r1[64], r2[64];
-        for (int jc = 0; jc < p.NC; ++jc)
-            cols[jc] = (uint8_t)uniform_int(dr.next(), 1u, (uint32_t)(m - 1));
-        for (int ir = 0; ir < p.NR; ++ir)
-            r1[ir] = (uint8_t)uniform_int(dr.next(), 0u, (uint32_t)(m - 1));
-        for (int ir = 0; ir < p.NR; ++ir)
-            r2[ir] = (uint8_t)uniform_int(dr.next(), 0u, (uint32_t)(m - 1));
         for (int jc = 0; jc < p.NC; ++jc) {
             const int cc = cols[jc];
             uint32_t *col = bo + cc * W;
