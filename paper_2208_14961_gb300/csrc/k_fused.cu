@@ -784,6 +784,7 @@ __device__ void offspring_warp(const FusedPop &p, PopSel &S, int src, uint32_t g
     const uint32_t N = (uint32_t)p.N, words = (uint32_t)(m * W);
     const uint32_t oh = half ? N : 0u;  // slot offset of this half: parent k + oh, offspring 2N + k + oh
     const bool inc = INC && p.gram != nullptr;
+    const int c = cut_point(p.seed, p.pop_id, gen, k, m);
     // lanes 0, 1: slots of the parents (survivors pi(k), pi(k + N)) and
     // their fitness; lane 2 (incremental mode): slot of non-survivor k + oh,
     // whose Gram buffer the offspring takes over
@@ -805,19 +806,57 @@ __device__ void offspring_warp(const FusedPop &p, PopSel &S, int src, uint32_t g
     const uint32_t *sp = p.pop[src];
     uint32_t *dp = p.pop[src ^ 1];
     const uint32_t w4 = words >> 2;  // words is a multiple of 4
-    {
+    // the parent giving columns [0, c) (the one this half carries over) and
+    // the one giving [c, m)
+    const uint32_t st = half ? s2 : s1, sb = half ? s1 : s2;
+    const uint4 *pt = reinterpret_cast<const uint4 *>(sp) + (size_t)st * w4;
+    const uint4 *pb = reinterpret_cast<const uint4 *>(sp) + (size_t)sb * w4;
+    if (inc) {
         // both parents as 16-byte cp.async copies (one commit group, waited
         // for below while the incremental Gram copies stay in flight)
-        const uint4 *pa = reinterpret_cast<const uint4 *>(sp) + (size_t)s1 * w4;
-        const uint4 *pb = reinterpret_cast<const uint4 *>(sp) + (size_t)s2 * w4;
         for (uint32_t e = lane; e < w4; e += 32) {
-            cp_async16(reinterpret_cast<uint4 *>(b1) + e, pa + e);
-            cp_async16(reinterpret_cast<uint4 *>(b2) + e, pb + e);
+            cp_async16(reinterpret_cast<uint4 *>(half ? b2 : b1) + e, pt + e);
+            cp_async16(reinterpret_cast<uint4 *>(half ? b1 : b2) + e, pb + e);
         }
-        cp_async_commit();
+    } else {
+        // full recomputation: the carried-over parent into b1, and the
+        // offspring's column set assembled by the copies themselves (Sec. 3.4:
+        // columns [0, c) of P_t, [c, m) of P_b, then again columns
+        // 0 .. m/2 - 2 for the warp-level Gram).  A 16-byte unit holds words
+        // of at most two columns (W >= 2): the one source unit g that the cut
+        // splits (its copies in both runs) is merged from both parents through
+        // registers by every lane that meets it.
+        const uint32_t ext = (uint32_t)(((m >> 1) - 1) * W);
+        const uint32_t units = (words + ext + 3u) >> 2;
+        uint32_t split = 0xFFFFFFFFu;  // the source unit cut by c, when this lane meets it
+        for (uint32_t e = lane; e < w4; e += 32)
+            cp_async16(reinterpret_cast<uint4 *>(b1) + e, pt + e);
+        for (uint32_t u = lane; u < units; u += 32) {
+            const uint32_t g = u < w4 ? u : u - w4;  // unit of the source matrix
+            const int j0 = (int)(4u * g) / W, j1 = (int)(4u * g + 3u) / W;
+            if (j1 < c)
+                cp_async16(reinterpret_cast<uint4 *>(bo) + u, pt + g);
+            else if (j0 >= c)
+                cp_async16(reinterpret_cast<uint4 *>(bo) + u, pb + g);
+            else
+                split = g;
+        }
+        if (split != 0xFFFFFFFFu) {
+            // word-wise merge of the cut unit (read through L2, like the copies)
+            const uint4 a = __ldcg(pt + split), b = __ldcg(pb + split);
+            const uint32_t wa[4] = {a.x, a.y, a.z, a.w}, wb[4] = {b.x, b.y, b.z, b.w};
+            uint32_t o[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                o[i] = ((int)(4u * split + (uint32_t)i) / W < c) ? wa[i] : wb[i];
+            const uint4 v = make_uint4(o[0], o[1], o[2], o[3]);
+            reinterpret_cast<uint4 *>(bo)[split] = v;
+            if (w4 + split < units)
+                reinterpret_cast<uint4 *>(bo)[w4 + split] = v;
+        }
     }
+    cp_async_commit();
     const uint32_t Fp = __shfl_sync(FULL, lf, half);  // fitness of the parent this half carries over
-    const int c = cut_point(p.seed, p.pop_id, gen, k, m);
     // incremental mode: parents keep their Gram buffers, offspring take the
     // buffers of the non-survivors
     uint32_t gb1 = 0, gb2 = 0, go = 0;
@@ -870,7 +909,7 @@ __device__ void offspring_warp(const FusedPop &p, PopSel &S, int src, uint32_t g
     __syncwarp();
     {
         // this half's parent keeps its place k + oh in the next population
-        const uint4 *bp = reinterpret_cast<const uint4 *>(half ? b2 : b1);
+        const uint4 *bp = reinterpret_cast<const uint4 *>(inc && half ? b2 : b1);
         uint4 *d4 = reinterpret_cast<uint4 *>(dp) + (size_t)(k + oh) * w4;
         for (uint32_t e = lane; e < w4; e += 32)
             d4[e] = bp[e];
@@ -878,9 +917,12 @@ __device__ void offspring_warp(const FusedPop &p, PopSel &S, int src, uint32_t g
     if (lane == 0)
         p.fit[src ^ 1][k + oh] = Fp;
     // crossover (Sec. 3.4): O1 = P1[:, :c] | P2[:, c:], O2 = P2[:, :c] | P1[:, c:]
-    for (uint32_t e = lane; e < words; e += 32)
-        bo[e] = (((int)(e / W) < c) != (half != 0)) ? b1[e] : b2[e];
-    __syncwarp();
+    // (full recomputation: already assembled by the copies)
+    if (inc) {
+        for (uint32_t e = lane; e < words; e += 32)
+            bo[e] = (((int)(e / W) < c) != (half != 0)) ? b1[e] : b2[e];
+        __syncwarp();
+    }
     // mutation (Sec. 3.5) in lane 0, sequential semantics; mut marks the
     // columns where a flip happened
     uint32_t mut[4] = {0u, 0u, 0u, 0u};
@@ -888,12 +930,19 @@ __device__ void offspring_warp(const FusedPop &p, PopSel &S, int src, uint32_t g
         for (int jc = 0; jc < p.NC; ++jc) {
             const int cc = cols[jc];
             uint32_t *col = bo + cc * W;
+            // full recomputation: the copy of column cc after column m - 1
+            // (columns 0 .. m/2 - 2) takes the same flips
+            uint32_t *mir = (!inc && cc < (m >> 1) - 1) ? bo + (m + cc) * W : nullptr;
             for (int ir = 0; ir < p.NR; ++ir) {
                 const int ra = r1[ir], rb = r2[ir];
                 const uint32_t ba = (col[ra >> 5] >> (ra & 31)) & 1u, bb = (col[rb >> 5] >> (rb & 31)) & 1u;
                 if (ba != bb) {
                     col[ra >> 5] ^= 1u << (ra & 31);
                     col[rb >> 5] ^= 1u << (rb & 31);
+                    if (mir) {
+                        mir[ra >> 5] ^= 1u << (ra & 31);
+                        mir[rb >> 5] ^= 1u << (rb & 31);
+                    }
                     mut[cc >> 5] |= 1u << (cc & 31);
                 }
             }
@@ -916,10 +965,8 @@ __device__ void offspring_warp(const FusedPop &p, PopSel &S, int src, uint32_t g
         }
     }
     if (!inc) {
-        // the warp-level Gram reads copies of columns 0 .. m/2 - 2 after column m - 1
-        for (int e = lane; e < ((m >> 1) - 1) * W; e += 32)
-            bo[words + e] = bo[e];
-        __syncwarp();
+        // the warp-level Gram reads the copies of columns 0 .. m/2 - 2 after
+        // column m - 1 (made by the copies and the mutation above)
         switch (p.kind) {
         case FIT_SQ: f = warp_fitness_cols<W, FIT_SQ>(bo, m, lane, p.nch); break;
         case FIT_ABS: f = warp_fitness_cols<W, FIT_ABS>(bo, m, lane, p.nch); break;
