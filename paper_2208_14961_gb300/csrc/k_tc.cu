@@ -28,10 +28,13 @@
 //            stage follows a use by the same issuer and a parity wait on its
 //            "full" barrier can never pass on the phase of an earlier lap
 //            that the other issuer has not consumed yet
-//   warps 2-9  two epilogue groups of four warps taking alternate jobs: wait
-//            for the accumulator, read it with tcgen05.ld (warp w reads TMEM
-//            lanes 32(w%4)..32(w%4)+31 = tile rows), free it, then square,
-//            sum and write the fitness
+//   warps 2-9  two epilogue groups of four warps, taking alternate jobs with
+//            four accumulators, or both on every job at m = 256 (group 0
+//            reads columns 0..191, group 1 columns 192..383, so the single
+//            accumulator is free again after half the reads): wait for the
+//            accumulator, read it with tcgen05.ld (warp w reads TMEM lanes
+//            32(w%4)..32(w%4)+31 = tile rows), free it, then square, sum and
+//            write the fitness
 // Every mbarrier wait is bounded (about two seconds); on a timeout the block
 // records ERR_TIMEOUT, drains its outstanding copies with bounded waits,
 // frees its TMEM and returns.
@@ -171,7 +174,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
     const int m = prm.m, rows = prm.rows, nch = prm.nchunks, kb = prm.kb, S = prm.nstages;
     const uint32_t sbytes = (uint32_t)rows * (uint32_t)kb;  // bytes of one stage
     constexpr int nacc = SPLIT ? 4 : 1;
-    constexpr int ngroups = SPLIT ? 2 : 1;
+    // epilogue groups: with four accumulators (m <= 128) they take alternate
+    // jobs; at m = 256 both read every job, each half of its 384 columns
+    constexpr int ngroups = 2;
     const uint32_t tmem_cols = 512u;
     uint32_t *err = prm.err ? prm.err : &g_tc_err;
 
@@ -182,7 +187,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
         }
         for (int b = 0; b < 4; ++b) {
             mbar_init(&acc_full[b], 1);
-            mbar_init(&acc_empty[b], 128);
+            mbar_init(&acc_empty[b], SPLIT ? 128 : 256);
             for (int g = 0; g < 2; ++g)
                 for (int u = 0; u < 2; ++u) {
                     part_sum[b][g][u] = 0ull;
@@ -396,7 +401,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
             int gsel = 0, bn = 0;
             uint32_t aph = 0u;
             for (int64_t j = blockIdx.x; j < prm.jobs; j += gridDim.x) {
-                const bool mine = gsel == grp;
+                const bool mine = !SPLIT || gsel == grp;
                 const int b = bn;
                 const uint32_t ph = aph;
                 if (++gsel == ngroups)
@@ -415,10 +420,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
                 if constexpr (!SPLIT) {
                     // m = 256: row t of the first block: columns 0..127 count once, 128..255 twice
                     // (their mirror images below the diagonal are not computed); row
-                    // 128 + t of the second block: its 128 columns once
-                    sum_a = sq_cols<4>(lane_addr);
-                    sum_b = sq_cols<4>(lane_addr + 128u);
-                    sum_a += sq_cols<4>(lane_addr + 256u);
+                    // 128 + t of the second block: its 128 columns once.  Group 0 reads
+                    // columns 0..191, group 1 columns 192..383.
+                    if (grp == 0) {
+                        sum_a = sq_cols<4>(lane_addr);
+                        sum_b = sq_cols<2>(lane_addr + 128u);
+                    } else {
+                        sum_b = sq_cols<2>(lane_addr + 192u);
+                        sum_a = sq_cols<4>(lane_addr + 256u);
+                    }
                 } else {
                     const int g = t / m;
                     const uint32_t col0 = lane_addr + (uint32_t)b * 128u + (uint32_t)(g * m);
@@ -440,9 +450,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
                     if (lane == 0 && mat < prm.P)
                         prm.fit[mat] = (uint32_t)((tot - m3) >> 1);
                 } else if (lane == 0) {
-                    // m = 64: warps of sub-partitions 2g, 2g+1 hold matrix g; m >= 128: all four
+                    // m = 64: warps of sub-partitions 2g, 2g+1 hold matrix g; m = 128: all
+                    // four of the group; m = 256: all eight of both groups
                     const int g = (m == 64) ? (q >> 1) : 0;
-                    const uint32_t need = (m == 64) ? 2u : 4u;
+                    const uint32_t need = !SPLIT ? 8u : (m == 64) ? 2u : 4u;
                     atomicAdd(&part_sum[b][g][use], tot);
                     __threadfence_block();
                     if (atomicAdd(&part_cnt[b][g][use], 1u) + 1u == need) {
@@ -454,9 +465,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fsq_tc(const __grid_constant_
                     }
                 }
                 // The combining slot of use parity u is taken again by the job two
-                // uses later on this accumulator, whose MMA waits for every thread of
-                // the group to have read the use in between, i.e. to have finished
-                // this job's combination first.
+                // uses later on this accumulator, whose MMA waits for every thread
+                // reading the accumulator (the group, or both groups at m = 256) to
+                // have read the use in between, i.e. to have finished this job's
+                // combination first.
                 __syncwarp();
             }
         }
